@@ -1,0 +1,185 @@
+/*
+ * rmq.h -- C ABI of the GB300 batched range-minimum-query library
+ * (librmq_gb300.so, CUDA for sm_103a).
+ *
+ * Method: the block-based sparse table (BbST) of S. Grabowski and
+ * T. Kowalski, "Faster batched range minimum queries" (arXiv:1706.06940),
+ * in its two forms:
+ *   - plain BbST (Sec. 3.2): blocks of k cells over A, a sparse table over
+ *     the block minima (Sec. 3.1 step 3), and query answering with two table
+ *     lookups plus speculative reads of the two end blocks (Sec. 3.1 step 4);
+ *   - contracted BbST_CON (Sec. 3.1): sort the 2q query endpoints (step 1),
+ *     contract A to the minima between consecutive endpoints (step 2), then
+ *     steps 3 and 4 over the contracted array A_Q.
+ *
+ * Problem (Sec. 1): for an int32 array A[0..n) and queries [l_i, r_i],
+ * out_i = the position of the minimum of A[l_i .. r_i].  This library uses
+ * 0-based inclusive ranges and always returns the LEFTMOST minimum position,
+ * so every valid answer is unique and bit-exact, independent of k, of the
+ * form used and of batching.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named A, l, r, out, T, P, ... are DEVICE pointers owned by the
+ *     caller unless a name ends in _host.  Nothing is retained after return
+ *     except where a handle says so (rmq_build borrows A).
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Device work is enqueued on it and the call returns without
+ *     waiting, except rmq_batch_host and rmq_stream_status, which wait.
+ *   - Host-detectable errors (null pointer with a non-zero size, n <= 0,
+ *     n or q too large, a bad block size) return immediately and enqueue
+ *     nothing.  A failed CUDA call returns RMQ_ERR_CUDA; workspace exhaustion
+ *     returns RMQ_ERR_OOM.
+ *   - A query with l < 0, r >= n or l > r is invalid: its out entry is set
+ *     to -1 on the device and a sticky device error word is raised, which
+ *     rmq_stream_status reports as RMQ_ERR_QUERY_RANGE.  l and r are never
+ *     swapped.
+ *   - Sizes: 1 <= n <= 2^31 - 1, 0 <= q <= 2^30 (q == 0 is a no-op).
+ *   - A is int32; arrays that are 16-byte aligned are read with 128-bit
+ *     loads, others with 32-bit loads (same results).
+ *   - Workspace comes from the device's stream-ordered memory pool
+ *     (cudaMallocAsync on `stream`), so calls can be captured in a CUDA graph.
+ *   - Calls are thread-safe on distinct handles and buffers.
+ *
+ * Packed keys: tables produced by the step-level entry points hold uint64
+ *   key(i) = ((uint64)((uint32)A[i] ^ 0x80000000) << 32) | (uint32)i
+ * whose unsigned order is (value, position) order, so the minimum key is the
+ * leftmost minimum and its low 32 bits are the position.
+ */
+#ifndef RMQ_GB300_H
+#define RMQ_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rmq_handle_s *rmq_handle;   /* opaque, owned by the library */
+
+typedef enum {
+    RMQ_OK = 0,
+    RMQ_ERR_INVALID_ARG = 1,   /* bad pointer, size or option; nothing enqueued */
+    RMQ_ERR_QUERY_RANGE = 2,   /* at least one query had l < 0, r >= n or l > r */
+    RMQ_ERR_OOM = 3,           /* device memory for workspace or a handle ran out */
+    RMQ_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    RMQ_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+    RMQ_ERR_BUDGET = 6         /* a memory budget set by the caller would be exceeded */
+} rmq_status;
+
+typedef enum {
+    RMQ_VARIANT_AUTO = 0,        /* the tuner picks (rmq_tune) */
+    RMQ_VARIANT_PLAIN = 1,       /* BbST without contraction (Sec. 3.2) */
+    RMQ_VARIANT_CONTRACTED = 2   /* BbST_CON (Sec. 3.1) */
+} rmq_variant;
+
+/* Options; a NULL rmq_opts* means all defaults (zeros). */
+typedef struct {
+    int32_t variant;   /* rmq_variant */
+    int32_t k;         /* block size over A (plain form): 0 = tuned, else a power of 2 in [32, 65536] */
+    int32_t k_con;     /* block size over A_Q (contracted form): 0 = tuned, else a power of 2 in [32, 65536] */
+    int32_t flags;     /* reserved, must be 0 */
+} rmq_opts;
+
+/* ------------------------------------------------------------------ batch */
+
+/* Answer q queries over A in one pass (Sec. 3.1 / 3.2): out[i] = leftmost
+ * argmin of A[l[i] .. r[i]].  Form and block size are tuned for (n, q).
+ * A: int32[n]; l, r, out: int32[q]. */
+rmq_status rmq_batch(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r,
+                     int64_t q, int32_t *out, void *stream);
+
+/* rmq_batch with explicit options (form, k, k_con). */
+rmq_status rmq_batch_ex(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r,
+                        int64_t q, int32_t *out, const rmq_opts *opts, void *stream);
+
+/* rmq_batch_ex on HOST buffers: copies A, l, r to the device, answers, copies
+ * out back, and returns after out_host is written (synchronous).  Host
+ * buffers may be pageable or pinned; pinned ones copy faster.  Device
+ * buffers come from the stream-ordered pool.  Invalid queries are reported
+ * in the return value (RMQ_ERR_QUERY_RANGE) as well as by -1 entries. */
+rmq_status rmq_batch_host(const int32_t *A_host, int64_t n, const int32_t *l_host,
+                          const int32_t *r_host, int64_t q, int32_t *out_host,
+                          const rmq_opts *opts, void *stream);
+
+/* -------------------------------------------------------- resident arrays */
+
+/* Build the plain-BbST state of A (Sec. 3.2: block minima and their sparse
+ * table) and keep it resident in a handle.  A is BORROWED: it must stay
+ * alive and unmodified until rmq_free.  The build is enqueued on `stream`;
+ * queries on another stream must be ordered after it by the caller.
+ * opts->variant is ignored (handles are always plain); opts->k picks k. */
+rmq_status rmq_build(const int32_t *A, int64_t n, const rmq_opts *opts, void *stream,
+                     rmq_handle *out_handle);
+
+/* Answer q queries against a built handle (Sec. 3.1 step 4 only). */
+rmq_status rmq_query(rmq_handle h, const int32_t *l, const int32_t *r, int64_t q,
+                     int32_t *out, void *stream);
+
+/* Device bytes owned by the handle (its sparse table), 0 for NULL. */
+int64_t rmq_handle_bytes(rmq_handle h);
+
+/* Block size k of the handle, 0 for NULL. */
+int32_t rmq_handle_k(rmq_handle h);
+
+/* Release a handle (waits for the device work that uses it). NULL is a no-op. */
+void rmq_free(rmq_handle h);
+
+/* ----------------------------------------------------------- diagnostics */
+
+/* Wait for `stream`, then report and clear the sticky device error word of
+ * the current device (errors raised by any call on this device since the
+ * last report): RMQ_OK, RMQ_ERR_QUERY_RANGE or RMQ_ERR_TIMEOUT. */
+rmq_status rmq_stream_status(void *stream);
+
+/* Static description of a status code (never NULL). */
+const char *rmq_strerror(rmq_status s);
+
+/* Bytes of a plain-BbST sparse table for (n, k): nb * (floor(log2 nb) + 1) * 8
+ * with nb = ceil(n / k) (the memory model of Table 2).  -1 on bad arguments. */
+int64_t rmq_table_bytes(int64_t n, int32_t k);
+
+/* The tuner's choice of form and block sizes for (n, q); host only. */
+rmq_status rmq_tune(int64_t n, int64_t q, rmq_opts *out);
+
+/* ------------------------------------------- step-level entry points
+ * One step of the method each, on caller buffers, for composition and for
+ * checking each step on its own.                                          */
+
+/* Sec. 3.1 step 3, level 0: T0[j] = min key over A[j*k .. min(n,(j+1)*k) - 1],
+ * j < ceil(n/k).  T0: uint64[ceil(n/k)]. */
+rmq_status rmq_block_minima(const int32_t *A, int64_t n, int32_t k, uint64_t *T0,
+                            void *stream);
+
+/* Sec. 3.1 step 3, all levels: given level 0 in T[0 .. nb), fill levels
+ * t = 1 .. floor(log2 nb): T[t*nb + j] = min(T[(t-1)*nb + j],
+ * T[(t-1)*nb + j + 2^(t-1)]) for j + 2^t <= nb (other slots are left as they
+ * are).  T: uint64[nb * (floor(log2 nb) + 1)], level-major. */
+rmq_status rmq_sparse_table_build(uint64_t *T, int64_t nb, void *stream);
+
+/* Sec. 3.1 step 1: sort the 2q endpoints (position, tag = 2i + side) by
+ * position, stably (equal positions keep the order l_0, r_0, l_1, ...).
+ * An invalid query (l < 0, r >= n or l > r) takes part as (0, 0) and raises
+ * the device error word.  pos_out, tag_out: uint32[2q]. */
+rmq_status rmq_sort_endpoints(const int32_t *l, const int32_t *r, int64_t q, int64_t n,
+                              uint32_t *pos_out, uint32_t *tag_out, void *stream);
+
+/* Sec. 3.1 step 1 (remapping): from sorted endpoints, P[0 .. m) = distinct
+ * positions in increasing order, rank_l[i] / rank_r[i] = index in P of
+ * l_i / r_i, and *m_dev = m (a device int64).  P_out: uint32[2q]. */
+rmq_status rmq_rank_endpoints(const uint32_t *pos_sorted, const uint32_t *tag_sorted,
+                              int64_t q, uint32_t *P_out, int64_t *m_dev,
+                              int32_t *rank_l, int32_t *rank_r, void *stream);
+
+/* Sec. 3.1 step 2: A_Q[j] = min key over A[P_j .. P_{j+1}] (both ends
+ * included), j < m - 1, where m = *m_dev (device) and m <= m_max (host bound,
+ * used to size the launch).  P must be strictly increasing positions < n.
+ * AQ: uint64[max(m_max - 1, 1)]. */
+rmq_status rmq_contract(const int32_t *A, int64_t n, const uint32_t *P, const int64_t *m_dev,
+                        int64_t m_max, uint64_t *AQ, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RMQ_GB300_H */

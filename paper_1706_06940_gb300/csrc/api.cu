@@ -1,0 +1,376 @@
+// api.cu -- the C ABI declared in include/rmq.h: argument checks, the choice
+// of form and block size, stream-ordered workspace, resident handles and the
+// sticky device error word.  Every computation is done by the kernels of
+// plain.cu and contract.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <mutex>
+
+#include "rmq_internal.cuh"
+
+namespace rmq {
+
+// Sticky per-device error word (ERR_* bits), raised by kernels, read and
+// cleared by rmq_stream_status.
+__device__ unsigned g_err_word;
+
+namespace {
+
+constexpr int kMaxDev = 64;
+std::mutex g_mu;
+int g_sms[kMaxDev];
+unsigned *g_err_ptr[kMaxDev];
+bool g_pool_done[kMaxDev];
+
+}  // namespace
+
+DevInfo dev_info() {
+    int d = 0;
+    cudaGetDevice(&d);
+    if (d < 0 || d >= kMaxDev) return DevInfo{d, 148};
+    if (g_sms[d] == 0) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (g_sms[d] == 0) {
+            int sms = 0;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || sms <= 0) sms = 148;
+            g_sms[d] = sms;
+        }
+    }
+    return DevInfo{d, g_sms[d]};
+}
+
+unsigned *err_word_ptr() {
+    int d = 0;
+    cudaGetDevice(&d);
+    if (d < 0 || d >= kMaxDev) return nullptr;
+    if (!g_err_ptr[d]) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_err_ptr[d]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_err_word) == cudaSuccess) g_err_ptr[d] = static_cast<unsigned *>(p);
+        }
+    }
+    return g_err_ptr[d];
+}
+
+namespace {
+
+// Workspace from the device's default stream-ordered pool; freed memory
+// stays cached in the pool for the next call.
+void pool_setup() {
+    int d = 0;
+    cudaGetDevice(&d);
+    if (d < 0 || d >= kMaxDev || g_pool_done[d]) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_pool_done[d]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, d) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    g_pool_done[d] = true;
+}
+
+struct Workspace {
+    void *p = nullptr;
+    cudaStream_t s = nullptr;
+    rmq_status alloc(size_t bytes, cudaStream_t stream) {
+        pool_setup();
+        s = stream;
+        cudaError_t e = cudaMallocAsync(&p, std::max<size_t>(bytes, 256), stream);
+        if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); p = nullptr; return RMQ_ERR_OOM; }
+        if (e != cudaSuccess) { p = nullptr; return RMQ_ERR_CUDA; }
+        return RMQ_OK;
+    }
+    ~Workspace() {
+        if (p) cudaFreeAsync(p, s);
+    }
+};
+
+bool pow2_in_range(int32_t k) {
+    return k >= (1 << MIN_LOGK) && k <= (1 << MAX_LOGK) && (k & (k - 1)) == 0;
+}
+
+int64_t table_entries(int64_t n, int logk) {
+    const int64_t nb = cdiv(n, 1ll << logk);
+    return nb * (ilog2_host((uint64_t)nb) + 1);
+}
+
+int pow2_log_near(double x, int lo, int hi) {
+    int t = (int)std::lround(std::log2(std::max(x, 1.0)));
+    return std::min(hi, std::max(lo, t));
+}
+
+}  // namespace
+
+}  // namespace rmq
+
+using namespace rmq;
+
+namespace {
+
+cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+constexpr int64_t kMaxN = 2147483647ll;
+constexpr int64_t kMaxQ = 1ll << 30;
+
+rmq_status check_batch_args(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q,
+                            const int32_t *out, const rmq_opts *opts) {
+    if (n <= 0 || n > kMaxN || q < 0 || q > kMaxQ) return RMQ_ERR_INVALID_ARG;
+    if (!A) return RMQ_ERR_INVALID_ARG;
+    if (q > 0 && (!l || !r || !out)) return RMQ_ERR_INVALID_ARG;
+    if (opts) {
+        if (opts->variant < RMQ_VARIANT_AUTO || opts->variant > RMQ_VARIANT_CONTRACTED) return RMQ_ERR_INVALID_ARG;
+        if (opts->k != 0 && !pow2_in_range(opts->k)) return RMQ_ERR_INVALID_ARG;
+        if (opts->k_con != 0 && !pow2_in_range(opts->k_con)) return RMQ_ERR_INVALID_ARG;
+        if (opts->flags != 0) return RMQ_ERR_INVALID_ARG;
+    }
+    return RMQ_OK;
+}
+
+rmq_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return RMQ_OK;
+    if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return RMQ_ERR_OOM; }
+    return RMQ_ERR_CUDA;
+}
+
+// Fill zero fields of opts with the tuner's choice.
+rmq_opts resolve_opts(int64_t n, int64_t q, const rmq_opts *opts) {
+    rmq_opts t;
+    rmq_tune(n, q, &t);
+    if (opts) {
+        if (opts->variant != RMQ_VARIANT_AUTO) t.variant = opts->variant;
+        if (opts->k) t.k = opts->k;
+        if (opts->k_con) t.k_con = opts->k_con;
+    }
+    return t;
+}
+
+rmq_status batch_plain(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
+                       int logk, cudaStream_t s) {
+    const int64_t nb = cdiv(n, 1ll << logk);
+    Workspace ws;
+    rmq_status st = ws.alloc((size_t)table_entries(n, logk) * 8, s);
+    if (st != RMQ_OK) return st;
+    uint64_t *T = static_cast<uint64_t *>(ws.p);
+    cudaError_t e;
+    if ((e = launch_block_minima_i32(A, n, logk, T, s)) != cudaSuccess) return cuda_status(e);
+    if ((e = launch_sparse_table(T, Len{n, nullptr}, logk, nb, s)) != cudaSuccess) return cuda_status(e);
+    return cuda_status(launch_query_plain(A, n, logk, T, nb, l, r, q, out, s));
+}
+
+rmq_status batch_contracted(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
+                            int logk_con, cudaStream_t s) {
+    Workspace ws;
+    rmq_status st = ws.alloc(con_workspace_bytes(n, q, logk_con), s);
+    if (st != RMQ_OK) return st;
+    return cuda_status(run_contracted(A, n, l, r, q, out, logk_con, ws.p, s));
+}
+
+}  // namespace
+
+struct rmq_handle_s {
+    const int32_t *A;
+    int64_t n;
+    int logk;
+    int64_t nb;
+    uint64_t *T;
+    int64_t bytes;
+    int device;
+};
+
+#pragma GCC visibility push(default)
+extern "C" {
+
+rmq_status rmq_batch(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
+                     void *stream) {
+    return rmq_batch_ex(A, n, l, r, q, out, nullptr, stream);
+}
+
+rmq_status rmq_batch_ex(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
+                        const rmq_opts *opts, void *stream) {
+    rmq_status st = check_batch_args(A, n, l, r, q, out, opts);
+    if (st != RMQ_OK) return st;
+    if (q == 0) return RMQ_OK;
+    const rmq_opts o = resolve_opts(n, q, opts);
+    if (o.variant == RMQ_VARIANT_CONTRACTED)
+        return batch_contracted(A, n, l, r, q, out, ilog2_host((uint64_t)o.k_con), as_stream(stream));
+    return batch_plain(A, n, l, r, q, out, ilog2_host((uint64_t)o.k), as_stream(stream));
+}
+
+rmq_status rmq_batch_host(const int32_t *A_host, int64_t n, const int32_t *l_host, const int32_t *r_host, int64_t q,
+                          int32_t *out_host, const rmq_opts *opts, void *stream) {
+    rmq_status st = check_batch_args(A_host, n, l_host, r_host, q, out_host, opts);
+    if (st != RMQ_OK) return st;
+    if (q == 0) return RMQ_OK;
+    cudaStream_t s = as_stream(stream);
+    const size_t bA = (size_t)n * 4, bq = (size_t)q * 4;
+    const size_t oA = 0, oL = (bA + 255) & ~(size_t)255, oR = oL + ((bq + 255) & ~(size_t)255),
+                 oO = oR + ((bq + 255) & ~(size_t)255);
+    char *base = nullptr;
+    {
+        Workspace ws;
+        if ((st = ws.alloc(oO + bq, s)) != RMQ_OK) return st;
+        base = static_cast<char *>(ws.p);
+        int32_t *dA = reinterpret_cast<int32_t *>(base + oA), *dl = reinterpret_cast<int32_t *>(base + oL),
+                *dr = reinterpret_cast<int32_t *>(base + oR), *dout = reinterpret_cast<int32_t *>(base + oO);
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync(dA, A_host, bA, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
+        if ((e = cudaMemcpyAsync(dl, l_host, bq, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
+        if ((e = cudaMemcpyAsync(dr, r_host, bq, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
+        if ((st = rmq_batch_ex(dA, n, dl, dr, q, dout, opts, stream)) != RMQ_OK) return st;
+        if ((e = cudaMemcpyAsync(out_host, dout, bq, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_status(e);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return RMQ_ERR_CUDA;
+    for (int64_t i = 0; i < q; ++i)
+        if (out_host[i] < 0) return RMQ_ERR_QUERY_RANGE;
+    return RMQ_OK;
+}
+
+rmq_status rmq_build(const int32_t *A, int64_t n, const rmq_opts *opts, void *stream, rmq_handle *out_handle) {
+    if (!out_handle) return RMQ_ERR_INVALID_ARG;
+    *out_handle = nullptr;
+    rmq_status st = check_batch_args(A, n, nullptr, nullptr, 0, nullptr, opts);
+    if (st != RMQ_OK) return st;
+    const rmq_opts o = resolve_opts(n, 0, opts);
+    const int logk = ilog2_host((uint64_t)o.k);
+    rmq_handle h = new (std::nothrow) rmq_handle_s();
+    if (!h) return RMQ_ERR_OOM;
+    h->A = A;
+    h->n = n;
+    h->logk = logk;
+    h->nb = cdiv(n, 1ll << logk);
+    h->bytes = table_entries(n, logk) * 8;
+    cudaGetDevice(&h->device);
+    cudaError_t e = cudaMalloc(&h->T, (size_t)h->bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return e == cudaErrorMemoryAllocation ? RMQ_ERR_OOM : RMQ_ERR_CUDA;
+    }
+    cudaStream_t s = as_stream(stream);
+    if ((e = launch_block_minima_i32(A, n, logk, h->T, s)) != cudaSuccess ||
+        (e = launch_sparse_table(h->T, Len{n, nullptr}, logk, h->nb, s)) != cudaSuccess) {
+        cudaFree(h->T);
+        delete h;
+        return cuda_status(e);
+    }
+    *out_handle = h;
+    return RMQ_OK;
+}
+
+rmq_status rmq_query(rmq_handle h, const int32_t *l, const int32_t *r, int64_t q, int32_t *out, void *stream) {
+    if (!h || q < 0 || q > kMaxQ) return RMQ_ERR_INVALID_ARG;
+    if (q == 0) return RMQ_OK;
+    if (!l || !r || !out) return RMQ_ERR_INVALID_ARG;
+    return cuda_status(launch_query_plain(h->A, h->n, h->logk, h->T, h->nb, l, r, q, out, as_stream(stream)));
+}
+
+int64_t rmq_handle_bytes(rmq_handle h) { return h ? h->bytes : 0; }
+
+int32_t rmq_handle_k(rmq_handle h) { return h ? (int32_t)(1 << h->logk) : 0; }
+
+void rmq_free(rmq_handle h) {
+    if (!h) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != h->device) cudaSetDevice(h->device);
+    cudaFree(h->T);
+    if (cur != h->device) cudaSetDevice(cur);
+    delete h;
+}
+
+rmq_status rmq_stream_status(void *stream) {
+    if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return RMQ_ERR_CUDA;
+    unsigned *p = err_word_ptr();
+    if (!p) return RMQ_ERR_CUDA;
+    unsigned w = 0;
+    if (cudaMemcpy(&w, p, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return RMQ_ERR_CUDA;
+    if (w) {
+        const unsigned zero = 0;
+        if (cudaMemcpy(p, &zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess) return RMQ_ERR_CUDA;
+    }
+    if (w & ERR_TIMEOUT) return RMQ_ERR_TIMEOUT;
+    if (w & ERR_QUERY_RANGE) return RMQ_ERR_QUERY_RANGE;
+    return RMQ_OK;
+}
+
+const char *rmq_strerror(rmq_status s) {
+    switch (s) {
+        case RMQ_OK: return "ok";
+        case RMQ_ERR_INVALID_ARG: return "invalid argument (pointer, size or option)";
+        case RMQ_ERR_QUERY_RANGE: return "a query had l < 0, r >= n or l > r (its answer is -1)";
+        case RMQ_ERR_OOM: return "out of device memory";
+        case RMQ_ERR_CUDA: return "a CUDA runtime call failed";
+        case RMQ_ERR_TIMEOUT: return "a bounded device-side wait timed out";
+        case RMQ_ERR_BUDGET: return "the memory budget would be exceeded";
+    }
+    return "unknown status";
+}
+
+int64_t rmq_table_bytes(int64_t n, int32_t k) {
+    if (n <= 0 || n > kMaxN || !pow2_in_range(k)) return -1;
+    return table_entries(n, ilog2_host((uint64_t)k)) * 8;
+}
+
+// The tuner: the plain form over A with k near sqrt(n)/8 (a few extra reads
+// per query against a table that stays small next to A), and, for the
+// contracted form, k_con near sqrt(2q) capped at the paper's default 512.
+rmq_status rmq_tune(int64_t n, int64_t q, rmq_opts *out) {
+    if (!out || n <= 0) return RMQ_ERR_INVALID_ARG;
+    out->variant = RMQ_VARIANT_PLAIN;
+    out->k = 1 << pow2_log_near(std::sqrt((double)n) / 8.0, MIN_LOGK, 12);
+    out->k_con = 1 << pow2_log_near(std::sqrt(2.0 * (double)std::max<int64_t>(q, 1)), MIN_LOGK, 9);
+    out->flags = 0;
+    return RMQ_OK;
+}
+
+rmq_status rmq_block_minima(const int32_t *A, int64_t n, int32_t k, uint64_t *T0, void *stream) {
+    if (!A || !T0 || n <= 0 || n > kMaxN || !pow2_in_range(k)) return RMQ_ERR_INVALID_ARG;
+    return cuda_status(launch_block_minima_i32(A, n, ilog2_host((uint64_t)k), T0, as_stream(stream)));
+}
+
+rmq_status rmq_sparse_table_build(uint64_t *T, int64_t nb, void *stream) {
+    if (!T || nb <= 0 || nb > kMaxN) return RMQ_ERR_INVALID_ARG;
+    return cuda_status(launch_sparse_table(T, Len{nb, nullptr}, 0, nb, as_stream(stream)));
+}
+
+rmq_status rmq_sort_endpoints(const int32_t *l, const int32_t *r, int64_t q, int64_t n, uint32_t *pos_out,
+                              uint32_t *tag_out, void *stream) {
+    if (n <= 0 || n > kMaxN || q < 0 || q > kMaxQ) return RMQ_ERR_INVALID_ARG;
+    if (q == 0) return RMQ_OK;
+    if (!l || !r || !pos_out || !tag_out) return RMQ_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    Workspace ws;
+    const size_t bytes = sort_workspace_bytes(q);
+    rmq_status st = ws.alloc(bytes, s);
+    if (st != RMQ_OK) return st;
+    return cuda_status(sort_endpoints(l, r, q, n, pos_out, tag_out, ws.p, bytes, s));
+}
+
+rmq_status rmq_rank_endpoints(const uint32_t *pos_sorted, const uint32_t *tag_sorted, int64_t q, uint32_t *P_out,
+                              int64_t *m_dev, int32_t *rank_l, int32_t *rank_r, void *stream) {
+    if (q < 0 || q > kMaxQ) return RMQ_ERR_INVALID_ARG;
+    if (!m_dev) return RMQ_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    if (q == 0) return cuda_status(cudaMemsetAsync(m_dev, 0, sizeof(int64_t), s));
+    if (!pos_sorted || !tag_sorted || !P_out || !rank_l || !rank_r) return RMQ_ERR_INVALID_ARG;
+    Workspace ws;
+    rmq_status st = ws.alloc(rank_workspace_bytes(q), s);
+    if (st != RMQ_OK) return st;
+    return cuda_status(rank_endpoints(pos_sorted, tag_sorted, q, P_out, m_dev, rank_l, rank_r, ws.p, s));
+}
+
+rmq_status rmq_contract(const int32_t *A, int64_t n, const uint32_t *P, const int64_t *m_dev, int64_t m_max,
+                        uint64_t *AQ, void *stream) {
+    if (!A || !P || !m_dev || !AQ || n <= 0 || n > kMaxN || m_max < 0) return RMQ_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    Workspace ws;
+    rmq_status st = ws.alloc(contract_workspace_bytes(n), s);
+    if (st != RMQ_OK) return st;
+    return cuda_status(contract(A, n, P, m_dev, AQ, ws.p, s));
+}
+
+}  // extern "C"
+#pragma GCC visibility pop

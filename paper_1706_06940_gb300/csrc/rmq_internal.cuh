@@ -1,0 +1,139 @@
+// rmq_internal.cuh -- shared device helpers and host launcher prototypes of
+// the GB300 BbST library.  Not part of the public ABI (include/rmq.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rmq.h"
+
+namespace rmq {
+
+constexpr uint64_t KEY_MAX = ~0ull;
+constexpr int MIN_LOGK = 5;    // k >= 32
+constexpr int MAX_LOGK = 16;   // k <= 65536
+
+// Bits of the sticky device error word.
+constexpr unsigned ERR_QUERY_RANGE = 1u;
+constexpr unsigned ERR_TIMEOUT = 2u;
+
+// Packed key: unsigned order == (value, position) order; low 32 bits = position.
+__device__ __forceinline__ uint64_t make_key(int32_t v, uint32_t pos) {
+    return ((uint64_t)((uint32_t)v ^ 0x80000000u) << 32) | (uint64_t)pos;
+}
+__device__ __forceinline__ uint64_t kmin(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__device__ __forceinline__ uint32_t key_pos(uint64_t k) { return (uint32_t)k; }
+__device__ __forceinline__ uint32_t key_hi(uint64_t k) { return (uint32_t)(k >> 32); }
+
+__device__ __forceinline__ uint64_t warp_min(uint64_t v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = kmin(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+
+__device__ __forceinline__ int ilog2_dev(uint64_t x) { return 63 - __clzll((long long)x); }
+
+// Streaming 128-bit load that does not allocate in L1 (data read once).
+__device__ __forceinline__ int4 ld_stream_v4(const int4 *p) {
+    int4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ ulonglong2 ld_stream_v2u64(const ulonglong2 *p) {
+    ulonglong2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.u64 {%0,%1}, [%2];"
+                 : "=l"(v.x), "=l"(v.y) : "l"(p));
+    return v;
+}
+
+// ---------------------------------------------------------------- sources
+// A "source" yields packed keys of a sequence: the int32 input A (key built
+// from value and index) or an array of ready keys (the contracted A_Q).
+
+struct SrcI32 {
+    const int32_t *a;
+    static constexpr int EPV = 4;  // elements per 16-byte vector
+    __device__ __forceinline__ uint64_t one(int64_t i) const { return make_key(__ldg(a + i), (uint32_t)i); }
+    // vector vi covers elements [4vi, 4vi + 4); the caller guarantees 4vi + 3 < n
+    template <bool VEC>
+    __device__ __forceinline__ void vec(int64_t vi, uint64_t (&k)[4]) const {
+        const int64_t e = vi * 4;
+        if (VEC) {
+            int4 v = ld_stream_v4(reinterpret_cast<const int4 *>(a) + vi);
+            k[0] = make_key(v.x, (uint32_t)e);
+            k[1] = make_key(v.y, (uint32_t)(e + 1));
+            k[2] = make_key(v.z, (uint32_t)(e + 2));
+            k[3] = make_key(v.w, (uint32_t)(e + 3));
+        } else {
+#pragma unroll
+            for (int x = 0; x < 4; ++x) k[x] = make_key(__ldg(a + e + x), (uint32_t)(e + x));
+        }
+    }
+};
+
+struct SrcU64 {
+    const uint64_t *a;
+    static constexpr int EPV = 2;
+    __device__ __forceinline__ uint64_t one(int64_t i) const { return __ldg(reinterpret_cast<const unsigned long long *>(a) + i); }
+    template <bool VEC>
+    __device__ __forceinline__ void vec(int64_t vi, uint64_t (&k)[2]) const {
+        ulonglong2 v = ld_stream_v2u64(reinterpret_cast<const ulonglong2 *>(a) + vi);
+        k[0] = v.x;
+        k[1] = v.y;
+    }
+};
+
+// Length of a sequence that may live on the device: n = m_dev ? (*m_dev - 1)
+// clamped at 0 : n_host.  The contracted array's length is only known on the
+// device (m - 1), so its kernels read it there and the host sizes launches
+// for the bound.
+struct Len {
+    int64_t n_host;
+    const int64_t *m_dev;
+    __device__ __forceinline__ int64_t get() const {
+        if (!m_dev) return n_host;
+        int64_t m = *m_dev;
+        return m > 1 ? m - 1 : 0;
+    }
+};
+
+// ---------------------------------------------------------------- host side
+
+struct DevInfo {
+    int device;
+    int sms;
+};
+DevInfo dev_info();                      // current device, cached SM count
+unsigned *err_word_ptr();                // device address of the sticky error word (current device)
+
+inline int ilog2_host(uint64_t x) { int t = -1; while (x) { x >>= 1; ++t; } return t; }
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Launchers (plain.cu).  All enqueue on `s` and return the launch status.
+cudaError_t launch_block_minima_i32(const int32_t *A, int64_t n, int logk, uint64_t *T0, cudaStream_t s);
+cudaError_t launch_block_minima_u64(const uint64_t *AQ, Len len, int64_t n_max, int logk, uint64_t *T0,
+                                    cudaStream_t s);
+// levels: number of levels of the table for the largest possible nb (host bound);
+// nb: the actual count, either on the host (nb_dev == nullptr) or derived on the
+// device from a Len and logk.
+cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, cudaStream_t s);
+cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint64_t *T, int64_t nb,
+                               const int32_t *l, const int32_t *r, int64_t q, int32_t *out, cudaStream_t s);
+
+// Contracted form (contract.cu).
+struct ConWork;  // workspace layout, see contract.cu
+size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con);
+cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q,
+                           int32_t *out, int logk_con, void *ws, cudaStream_t s);
+cudaError_t sort_endpoints(const int32_t *l, const int32_t *r, int64_t q, int64_t n, uint32_t *pos_out,
+                           uint32_t *tag_out, void *ws, size_t ws_bytes, cudaStream_t s);
+size_t sort_workspace_bytes(int64_t q);
+cudaError_t rank_endpoints(const uint32_t *pos, const uint32_t *tag, int64_t q, uint32_t *P, int64_t *m_dev,
+                           int32_t *rank_l, int32_t *rank_r, void *ws, cudaStream_t s);
+size_t rank_workspace_bytes(int64_t q);
+cudaError_t contract(const int32_t *A, int64_t n, const uint32_t *P, const int64_t *m_dev, uint64_t *AQ,
+                     void *ws, cudaStream_t s);
+size_t contract_workspace_bytes(int64_t n);
+
+}  // namespace rmq

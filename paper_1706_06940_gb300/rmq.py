@@ -1,0 +1,258 @@
+"""ctypes binding of librmq_gb300.so (include/rmq.h), argument marshalling only.
+
+Functions carry the C ABI's names.  Device arrays are torch CUDA tensors
+(their data pointers are passed through); host arrays are numpy arrays; the
+stream defaults to torch's current stream on the tensor's device.  Every
+step of the computation runs in the library's CUDA kernels; if the library
+is missing this module raises instead of computing anything itself.
+
+Calls that return an rmq_status raise RmqError for anything but RMQ_OK,
+except rmq_stream_status, which returns the status.
+"""
+from __future__ import annotations
+
+import ctypes
+import enum
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librmq_gb300.so")
+
+
+class Status(enum.IntEnum):
+    OK = 0
+    ERR_INVALID_ARG = 1
+    ERR_QUERY_RANGE = 2
+    ERR_OOM = 3
+    ERR_CUDA = 4
+    ERR_TIMEOUT = 5
+    ERR_BUDGET = 6
+
+
+class Variant(enum.IntEnum):
+    AUTO = 0
+    PLAIN = 1
+    CONTRACTED = 2
+
+
+class RmqError(RuntimeError):
+    def __init__(self, status):
+        self.status = Status(status)
+        super().__init__("%s: %s" % (self.status.name, strerror(self.status)))
+
+
+class rmq_opts(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("k_con", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_SIGS = {
+    "rmq_batch": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, _vp]),
+    "rmq_batch_ex": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, ctypes.POINTER(rmq_opts), _vp]),
+    "rmq_batch_host": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, ctypes.POINTER(rmq_opts), _vp]),
+    "rmq_build": (_i32, [_vp, _i64, ctypes.POINTER(rmq_opts), _vp, ctypes.POINTER(_vp)]),
+    "rmq_query": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp]),
+    "rmq_handle_bytes": (_i64, [_vp]),
+    "rmq_handle_k": (_i32, [_vp]),
+    "rmq_free": (None, [_vp]),
+    "rmq_stream_status": (_i32, [_vp]),
+    "rmq_strerror": (ctypes.c_char_p, [_i32]),
+    "rmq_table_bytes": (_i64, [_i64, _i32]),
+    "rmq_tune": (_i32, [_i64, _i64, ctypes.POINTER(rmq_opts)]),
+    "rmq_block_minima": (_i32, [_vp, _i64, _i32, _vp, _vp]),
+    "rmq_sparse_table_build": (_i32, [_vp, _i64, _vp]),
+    "rmq_sort_endpoints": (_i32, [_vp, _vp, _i64, _i64, _vp, _vp, _vp]),
+    "rmq_rank_endpoints": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]),
+    "rmq_contract": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, _vp]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("librmq_gb300.so not found at %s: run __graft_entry__.build() "
+                           "(the library has no CPU fallback)" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def strerror(status) -> str:
+    return load().rmq_strerror(int(status)).decode()
+
+
+def _check(st):
+    if st != 0:
+        raise RmqError(st)
+
+
+def _opts(variant=0, k=0, k_con=0, flags=0):
+    return rmq_opts(int(variant), int(k), int(k_con), int(flags))
+
+
+def _stream(stream, t=None):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    dev = t.device if t is not None else None
+    return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _dptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("%s must have dtype %s" % (name, dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return ctypes.c_void_p(t.data_ptr()) if t.numel() else ctypes.c_void_p(0)
+
+
+def _i32t():
+    import torch
+    return torch.int32
+
+
+# ---------------------------------------------------------------- batch
+
+def rmq_batch(A, l, r, out, stream=None):
+    """out[i] = leftmost argmin of A[l[i]..r[i]] (tuned form and k)."""
+    _check(load().rmq_batch(_dptr(A, _i32t(), "A"), A.numel(), _dptr(l, _i32t(), "l"),
+                            _dptr(r, _i32t(), "r"), l.numel(), _dptr(out, _i32t(), "out"),
+                            _stream(stream, A)))
+
+
+def rmq_batch_ex(A, l, r, out, variant=0, k=0, k_con=0, stream=None, flags=0):
+    o = _opts(variant, k, k_con, flags)
+    _check(load().rmq_batch_ex(_dptr(A, _i32t(), "A"), A.numel(), _dptr(l, _i32t(), "l"),
+                               _dptr(r, _i32t(), "r"), l.numel(), _dptr(out, _i32t(), "out"),
+                               ctypes.byref(o), _stream(stream, A)))
+
+
+def rmq_batch_host(A, l, r, out, variant=0, k=0, k_con=0, stream=None):
+    """Host-buffer batch (numpy int32 arrays, out written in place); waits."""
+    for name, a in (("A", A), ("l", l), ("r", r), ("out", out)):
+        if not (isinstance(a, np.ndarray) and a.dtype == np.int32 and a.flags.c_contiguous):
+            raise ValueError("%s must be a C-contiguous numpy int32 array" % name)
+    o = _opts(variant, k, k_con)
+    st = load().rmq_batch_host(A.ctypes.data, len(A), l.ctypes.data, r.ctypes.data, len(l),
+                               out.ctypes.data, ctypes.byref(o), _stream(stream))
+    _check(st)
+
+
+# ---------------------------------------------------------------- handles
+
+class Handle:
+    """A resident plain-BbST structure (rmq_build).  A is borrowed: the
+    tensor is kept referenced here so it outlives the handle."""
+
+    def __init__(self, ptr, A):
+        self.ptr = ptr
+        self.A = A
+
+    @property
+    def bytes(self) -> int:
+        return int(load().rmq_handle_bytes(self.ptr))
+
+    @property
+    def k(self) -> int:
+        return int(load().rmq_handle_k(self.ptr))
+
+    def free(self):
+        if self.ptr:
+            load().rmq_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def rmq_build(A, k=0, stream=None) -> Handle:
+    h = ctypes.c_void_p()
+    o = _opts(0, k, 0)
+    _check(load().rmq_build(_dptr(A, _i32t(), "A"), A.numel(), ctypes.byref(o),
+                            _stream(stream, A), ctypes.byref(h)))
+    return Handle(h, A)
+
+
+def rmq_query(h: Handle, l, r, out, stream=None):
+    _check(load().rmq_query(h.ptr, _dptr(l, _i32t(), "l"), _dptr(r, _i32t(), "r"), l.numel(),
+                            _dptr(out, _i32t(), "out"), _stream(stream, l)))
+
+
+def rmq_free(h: Handle):
+    h.free()
+
+
+def rmq_handle_bytes(h: Handle) -> int:
+    return h.bytes
+
+
+# ---------------------------------------------------------------- diagnostics
+
+def rmq_stream_status(stream=None) -> Status:
+    return Status(load().rmq_stream_status(_stream(stream)))
+
+
+def rmq_strerror(status) -> str:
+    return strerror(status)
+
+
+def rmq_table_bytes(n: int, k: int) -> int:
+    return int(load().rmq_table_bytes(int(n), int(k)))
+
+
+def rmq_tune(n: int, q: int) -> dict:
+    o = rmq_opts()
+    _check(load().rmq_tune(int(n), int(q), ctypes.byref(o)))
+    return {"variant": Variant(o.variant), "k": o.k, "k_con": o.k_con}
+
+
+# ---------------------------------------------------------------- steps
+
+def rmq_block_minima(A, k, T0, stream=None):
+    _check(load().rmq_block_minima(_dptr(A, _i32t(), "A"), A.numel(), int(k), _dptr(T0, None, "T0"),
+                                   _stream(stream, A)))
+
+
+def rmq_sparse_table_build(T, nb, stream=None):
+    _check(load().rmq_sparse_table_build(_dptr(T, None, "T"), int(nb), _stream(stream, T)))
+
+
+def rmq_sort_endpoints(l, r, n, pos_out, tag_out, stream=None):
+    _check(load().rmq_sort_endpoints(_dptr(l, _i32t(), "l"), _dptr(r, _i32t(), "r"), l.numel(), int(n),
+                                     _dptr(pos_out, None, "pos_out"), _dptr(tag_out, None, "tag_out"),
+                                     _stream(stream, l)))
+
+
+def rmq_rank_endpoints(pos_sorted, tag_sorted, q, P_out, m_dev, rank_l, rank_r, stream=None):
+    _check(load().rmq_rank_endpoints(_dptr(pos_sorted), _dptr(tag_sorted), int(q), _dptr(P_out),
+                                     _dptr(m_dev), _dptr(rank_l), _dptr(rank_r), _stream(stream, pos_sorted)))
+
+
+def rmq_contract(A, P, m_dev, m_max, AQ, stream=None):
+    _check(load().rmq_contract(_dptr(A, _i32t(), "A"), A.numel(), _dptr(P), _dptr(m_dev), int(m_max),
+                               _dptr(AQ), _stream(stream, A)))
