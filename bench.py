@@ -1,0 +1,423 @@
+#!/usr/bin/env python3
+"""Benchmark of batched leftmost-argmin RMQ (block-based sparse table) on GB300.
+
+Workload (default): the paper-shaped single array, A int32 n = 1e8 uniform in
+[0, 2^31), q = 1e7 queries with l, r uniform over [0, n) and l <= r.  One step
+answers the batch once with each form of the method -- plain BbST (block
+minima, sparse table, queries) and BbST_CON (endpoint sort, remap,
+contraction, table over A_Q, queries) -- so a step covers every stage of the
+hot path and answers 2q queries.  Inputs are resident in HBM before timing;
+L2 is flushed (256 MiB write) before each form, outside the timed events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With --impl reference the CPU oracle (naive
+per-query scan, all host cores) answers a bounded sample of the same batch.
+Under torchrun every rank answers its own batch (weak scaling, no collective
+on the data path); the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "queries/s incl. preprocessing and achieved HBM GB/s; served p50/p99 latency vs plain"
+UNIT = "queries/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=float, default=1e8)
+    p.add_argument("--q", type=float, default=1e7)
+    p.add_argument("--seed", type=int, default=1002)
+    p.add_argument("--variant", choices=["both", "plain", "contracted"], default="both")
+    p.add_argument("--k", type=int, default=0, help="plain-form block size (0 = tuned)")
+    p.add_argument("--k-con", type=int, default=0, help="contracted-form block size (0 = tuned)")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+class Dist:
+    """Barrier and max-reduction over ranks (gloo, host tensors)."""
+
+    def __init__(self):
+        self.rank, self.world, self.local = dist_env()
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as td
+            td.init_process_group("gloo")
+            self.pg = td
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def workload(n, q, seed, rank):
+    from paper_1706_06940_gb300 import workloads as W
+    A = W.uniform_array(n, seed + 7919 * rank)
+    l, r = W.uniform_queries(n, q, seed + 7919 * rank + 1)
+    return A, l, r
+
+
+def workload_name(n, q):
+    return ("paper-shaped single array: A int32 n=%g uniform in [0,2^31), q=%g queries with l,r uniform "
+            "over [0,n) swapped so l<=r; one step = the batch answered by plain BbST and by BbST_CON" % (n, q))
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def stop(self, t0=None, t1=None):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        window = [ln for ts, ln in self.lines if t0 is None or t0 - 0.15 <= ts <= t1 + 0.15]
+        for ln in window or [ln for _, ln in self.lines]:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(kernel_src_rel, summary_rel):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current source of the kernel (its sha256 is recorded there)."""
+    try:
+        text = open(os.path.join(ROOT, summary_rel)).read()
+        src = open(os.path.join(ROOT, kernel_src_rel), "rb").read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", text)
+    h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    if not m or not h or h.group(1) != hashlib.sha256(src).hexdigest():
+        return None
+    return int(m.group(1))
+
+
+def cpu_baseline(A, l, r, budget_s):
+    """The oracle (naive leftmost scan per query, OpenMP over all host cores)
+    on the first queries of the same batch, sized to about budget_s."""
+    import numpy as np
+
+    import oracle
+    threads = oracle.max_threads()
+    s = min(len(l), max(threads, 8))
+    t0 = time.perf_counter()
+    oracle.rmq_naive(A, l[:s], r[:s])
+    dt = max(time.perf_counter() - t0, 1e-6)
+    s2 = int(min(len(l), max(s, budget_s * s / dt)))
+    t0 = time.perf_counter()
+    oracle.rmq_naive(A, l[:s2], r[:s2])
+    dt2 = time.perf_counter() - t0
+    width = float(np.sum(r[:s2].astype(np.int64) - l[:s2] + 1))
+    return {"value": s2 / dt2, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "naive oracle on the first %d of the %d queries (%.3g cells scanned), %.1f s"
+                      % (s2, len(l), width, dt2)}
+
+
+# ----------------------------------------------------------------- reference arm
+
+def run_reference(args, dist):
+    """The CPU oracle on bounded samples of the same batch, rank 0 only."""
+    if dist.rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    n, q = int(args.n), int(args.q)
+    A, l, r = workload(n, q, args.seed, 0)
+    threads = oracle.max_threads()
+    per_step = max(0.2, min(2.0, 90.0 / max(args.steps + args.warmup, 1)))
+    s = max(threads, 8)
+    t0 = time.perf_counter()
+    oracle.rmq_naive(A, l[:s], r[:s])
+    rate = s / max(time.perf_counter() - t0, 1e-6)
+    per = int(min(q, max(threads, per_step * rate)))
+    cursor = 0
+    times, answered = [], 0
+    for i in range(args.warmup + args.steps):
+        idx = (np.arange(cursor, cursor + per) % q)
+        cursor += per
+        t0 = time.perf_counter()
+        oracle.rmq_naive(A, l[idx], r[idx])
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            answered += per
+    total = sum(times)
+    value = answered / total
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / max(len(times), 1), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": workload_name(n, q), "n": n, "q": q, "seed": args.seed,
+                   "sample_queries_per_step": per},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "naive oracle, %d queries of the batch per step, %d timed steps"
+                                   % (per, len(times))},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- our arm
+
+def run_ours(args, dist):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    if dist.rank == 0:
+        __graft_entry__.build()
+    dist.barrier()
+    from paper_1706_06940_gb300 import rmq
+
+    rmq.load()
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    n, q = int(args.n), int(args.q)
+    A, l, r = workload(n, q, args.seed, dist.rank)
+    dA = torch.from_numpy(A).to(dev)
+    dl, dr = torch.from_numpy(l).to(dev), torch.from_numpy(r).to(dev)
+    outs = {"plain": torch.empty(q, dtype=torch.int32, device=dev),
+            "contracted": torch.empty(q, dtype=torch.int32, device=dev)}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    tune = rmq.rmq_tune(n, q)
+    k = args.k or tune["k"]
+    k_con = args.k_con or tune["k_con"]
+    forms = ["plain", "contracted"] if args.variant == "both" else [args.variant]
+    nev = {"plain": 4, "contracted": 6}
+    vcode = {"plain": rmq.Variant.PLAIN, "contracted": rmq.Variant.CONTRACTED}
+    stream = torch.cuda.current_stream(dev)
+
+    def one_step(it):
+        evs = {}
+        for f in forms:
+            flush.fill_(it & 0xFF)
+            evs[f] = [torch.cuda.Event(enable_timing=True) for _ in range(nev[f])]
+            rmq.rmq_batch_timed(dA, dl, dr, outs[f], evs[f], variant=vcode[f], k=k, k_con=k_con)
+        return evs
+
+    for i in range(args.warmup):
+        one_step(i)
+    torch.cuda.synchronize()
+    st = rmq.rmq_stream_status()
+    if st != rmq.Status.OK:
+        raise RuntimeError("device status after warm-up: %s" % st.name)
+    # spot check of the answers against the oracle on a sample (outside timing)
+    import oracle
+    idx = np.random.default_rng(5).choice(q, size=min(q, 48), replace=False)
+    want = oracle.rmq_naive(A, l[idx], r[idx])
+    for f in forms:
+        got = outs[f].cpu().numpy()[idx]
+        if not np.array_equal(got, want):
+            raise RuntimeError("%s form: answers differ from the oracle on the spot check" % f)
+
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = rmq.rmq_launch_count()
+    dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    all_evs = [one_step(args.warmup + i) for i in range(args.steps)]
+    torch.cuda.synchronize()
+    t_wall1 = time.perf_counter()
+    t_wall = t_wall1 - t_wall0
+    dist.barrier()
+    launches = rmq.rmq_launch_count() - launches0
+    clk = clocks.stop(t_wall0, t_wall1)
+
+    # per-stage device times (ms), averaged over steps
+    stage_names = {"plain": ["block_minima", "sparse_table", "queries"],
+                   "contracted": ["sort", "remap", "contract", "table_AQ", "queries"]}
+    stages = {f: {s: 0.0 for s in stage_names[f]} for f in forms}
+    form_ms = {f: 0.0 for f in forms}
+    for evs in all_evs:
+        for f in forms:
+            e = evs[f]
+            for j, s in enumerate(stage_names[f]):
+                stages[f][s] += e[j].elapsed_time(e[j + 1]) / args.steps
+            form_ms[f] += e[0].elapsed_time(e[-1]) / args.steps
+    ms_step = sum(form_ms.values())
+    ms_step_max = dist.max(ms_step)
+    units = 2 * q if len(forms) == 2 else q
+    value = dist.world * units / (ms_step_max * 1e-3)
+
+    # roofline of the dominant single kernel: block minima over A (plain a1)
+    peak, peak_kind = measured_peak_hbm()
+    nb = -(-n // k)
+    lv = int(np.floor(np.log2(nb))) + 1
+    bytes_a1 = 4 * n + 8 * nb
+    ms_a1 = stages["plain"]["block_minima"] if "plain" in stages else None
+    roof = None
+    if ms_a1:
+        ach = bytes_a1 / (ms_a1 * 1e-3) / 1e9
+        roof = {"kernel": "k_block_min_warp (block minima over A, plain step a1)", "bound": "hbm",
+                "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "peak_kind": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
+                else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": bytes_a1,
+                "traffic": profiled_traffic("paper_1706_06940_gb300/csrc/plain.cu",
+                                            "profiles/block_minima_n1e8.md")}
+    # whole-form HBM accounting (algorithmic bytes of the plain form)
+    hbm_plain = None
+    if "plain" in form_ms:
+        b = 4 * n + 8 * nb * lv + 12 * q
+        hbm_plain = {"algorithmic_bytes": b, "gbs": b / (form_ms["plain"] * 1e-3) / 1e9,
+                     "frac_of_measured": b / (form_ms["plain"] * 1e-3) / 1e9 / peak,
+                     "frac_of_8tbs_nominal": b / (form_ms["plain"] * 1e-3) / 1e9 / 8000.0}
+
+    # end to end: host buffers through rmq_batch_host, copies inside the timing
+    e2e = None
+    if not args.no_e2e and args.e2e_steps > 0:
+        pA = torch.from_numpy(A).pin_memory()
+        pl, pr = torch.from_numpy(l).pin_memory(), torch.from_numpy(r).pin_memory()
+        pout = torch.empty(q, dtype=torch.int32).pin_memory()
+        hA, hl, hr, ho = pA.numpy(), pl.numpy(), pr.numpy(), pout.numpy()
+        for f in forms:                                          # warm the pool
+            rmq.rmq_batch_host(hA, hl, hr, ho, variant=vcode[f], k=k, k_con=k_con)
+        dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for f in forms:
+                rmq.rmq_batch_host(hA, hl, hr, ho, variant=vcode[f], k=k, k_con=k_con)
+        dt = dist.max(time.perf_counter() - t0)
+        e2e = {"value": dist.world * units * args.e2e_steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": len(forms) * (4 * n + 8 * q),
+               "d2h_bytes_per_step": len(forms) * 4 * q,
+               "ms_per_step": 1e3 * dt / args.e2e_steps, "buffers": "pinned host"}
+
+    cpu = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(A, l, r, args.cpu_seconds)
+
+    if dist.rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": workload_name(n, q), "n": n, "q": q, "seed": args.seed,
+                       "forms": forms, "k": k, "k_con": k_con,
+                       "l2": "flushed by a 256 MiB write before each form (outside the timed events); "
+                             "A alone (%.0f MB) exceeds L2" % (4 * n / 1e6),
+                       "parallelism": "replicas" if dist.world > 1 else "single GPU"},
+            "forms": {f: {"ms": form_ms[f], "queries_per_s": q / (form_ms[f] * 1e-3),
+                          "stages_ms": stages[f]} for f in forms},
+            "hbm_plain": hbm_plain,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "wall_s_timed_region": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist)
+        else:
+            run_ours(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

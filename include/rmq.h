@@ -93,6 +93,18 @@ rmq_status rmq_batch(const int32_t *A, int64_t n, const int32_t *l, const int32_
 rmq_status rmq_batch_ex(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r,
                         int64_t q, int32_t *out, const rmq_opts *opts, void *stream);
 
+/* rmq_batch_ex that also records CUDA events on `stream` at the stage
+ * boundaries of the method, for per-stage timing (the breakdown of Table 1).
+ * events: cudaEvent_t handles created by the caller (passed as void*).
+ * Plain form (Sec. 3.2), 4 events: start | block minima | sparse table |
+ *   queries.
+ * Contracted form (Sec. 3.1), 6 events: start | step 1 sort | step 1 remap |
+ *   step 2 contraction | step 3 block minima and table over A_Q | step 4.
+ * With fewer events only the first n_events boundaries are recorded. */
+rmq_status rmq_batch_timed(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r,
+                           int64_t q, int32_t *out, const rmq_opts *opts, void *stream,
+                           void *const *events, int32_t n_events);
+
 /* rmq_batch_ex on HOST buffers: copies A, l, r to the device, answers, copies
  * out back, and returns after out_host is written (synchronous).  Host
  * buffers may be pageable or pinned; pinned ones copy faster.  Device
@@ -131,6 +143,10 @@ void rmq_free(rmq_handle h);
  * the current device (errors raised by any call on this device since the
  * last report): RMQ_OK, RMQ_ERR_QUERY_RANGE or RMQ_ERR_TIMEOUT. */
 rmq_status rmq_stream_status(void *stream);
+
+/* Number of kernel launches this library has issued in the process so far
+ * (all devices, all threads); host only. */
+int64_t rmq_launch_count(void);
 
 /* Static description of a status code (never NULL). */
 const char *rmq_strerror(rmq_status s);

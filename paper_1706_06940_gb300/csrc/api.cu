@@ -3,6 +3,7 @@
 // sticky device error word.  Every computation is done by the kernels of
 // plain.cu and contract.cu.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <mutex>
@@ -17,6 +18,7 @@ __device__ unsigned g_err_word;
 
 namespace {
 
+std::atomic<int64_t> g_launches{0};
 constexpr int kMaxDev = 64;
 std::mutex g_mu;
 int g_sms[kMaxDev];
@@ -24,6 +26,8 @@ unsigned *g_err_ptr[kMaxDev];
 bool g_pool_done[kMaxDev];
 
 }  // namespace
+
+void note_launches(int count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
 
 DevInfo dev_info() {
     int d = 0;
@@ -148,24 +152,40 @@ rmq_opts resolve_opts(int64_t n, int64_t q, const rmq_opts *opts) {
 }
 
 rmq_status batch_plain(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
-                       int logk, cudaStream_t s) {
+                       int logk, cudaStream_t s, Stages *sg) {
     const int64_t nb = cdiv(n, 1ll << logk);
     Workspace ws;
     rmq_status st = ws.alloc((size_t)table_entries(n, logk) * 8, s);
     if (st != RMQ_OK) return st;
     uint64_t *T = static_cast<uint64_t *>(ws.p);
     cudaError_t e;
+    sg->mark(s);
     if ((e = launch_block_minima_i32(A, n, logk, T, s)) != cudaSuccess) return cuda_status(e);
+    sg->mark(s);
     if ((e = launch_sparse_table(T, Len{n, nullptr}, logk, nb, s)) != cudaSuccess) return cuda_status(e);
-    return cuda_status(launch_query_plain(A, n, logk, T, nb, l, r, q, out, s));
+    sg->mark(s);
+    e = launch_query_plain(A, n, logk, T, nb, l, r, q, out, s);
+    sg->mark(s);
+    return cuda_status(e);
 }
 
 rmq_status batch_contracted(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
-                            int logk_con, cudaStream_t s) {
+                            int logk_con, cudaStream_t s, Stages *sg) {
     Workspace ws;
     rmq_status st = ws.alloc(con_workspace_bytes(n, q, logk_con), s);
     if (st != RMQ_OK) return st;
-    return cuda_status(run_contracted(A, n, l, r, q, out, logk_con, ws.p, s));
+    return cuda_status(run_contracted(A, n, l, r, q, out, logk_con, ws.p, s, sg));
+}
+
+rmq_status batch_dispatch(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
+                          const rmq_opts *opts, cudaStream_t s, Stages *sg) {
+    rmq_status st = check_batch_args(A, n, l, r, q, out, opts);
+    if (st != RMQ_OK) return st;
+    if (q == 0) return RMQ_OK;
+    const rmq_opts o = resolve_opts(n, q, opts);
+    if (o.variant == RMQ_VARIANT_CONTRACTED)
+        return batch_contracted(A, n, l, r, q, out, ilog2_host((uint64_t)o.k_con), s, sg);
+    return batch_plain(A, n, l, r, q, out, ilog2_host((uint64_t)o.k), s, sg);
 }
 
 }  // namespace
@@ -190,14 +210,20 @@ rmq_status rmq_batch(const int32_t *A, int64_t n, const int32_t *l, const int32_
 
 rmq_status rmq_batch_ex(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
                         const rmq_opts *opts, void *stream) {
-    rmq_status st = check_batch_args(A, n, l, r, q, out, opts);
-    if (st != RMQ_OK) return st;
-    if (q == 0) return RMQ_OK;
-    const rmq_opts o = resolve_opts(n, q, opts);
-    if (o.variant == RMQ_VARIANT_CONTRACTED)
-        return batch_contracted(A, n, l, r, q, out, ilog2_host((uint64_t)o.k_con), as_stream(stream));
-    return batch_plain(A, n, l, r, q, out, ilog2_host((uint64_t)o.k), as_stream(stream));
+    Stages none;
+    return batch_dispatch(A, n, l, r, q, out, opts, as_stream(stream), &none);
 }
+
+rmq_status rmq_batch_timed(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
+                           const rmq_opts *opts, void *stream, void *const *events, int32_t n_events) {
+    if (n_events < 0 || (n_events > 0 && !events)) return RMQ_ERR_INVALID_ARG;
+    Stages sg;
+    sg.ev = reinterpret_cast<cudaEvent_t *>(const_cast<void **>(events));
+    sg.n = n_events;
+    return batch_dispatch(A, n, l, r, q, out, opts, as_stream(stream), &sg);
+}
+
+int64_t rmq_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 rmq_status rmq_batch_host(const int32_t *A_host, int64_t n, const int32_t *l_host, const int32_t *r_host, int64_t q,
                           int32_t *out_host, const rmq_opts *opts, void *stream) {

@@ -119,6 +119,7 @@ cudaError_t scan_exclusive(const uint32_t *in, uint32_t *out, int64_t count, uin
     k_scan_partial<<<(unsigned)nc, kT, 0, s>>>(in, count, aux);
     k_scan_top<<<1, kT, 0, s>>>(aux, nc, total_out);
     k_scan_final<<<(unsigned)nc, kT, 0, s>>>(in, out, count, aux);
+    note_launches(3);
     return cudaGetLastError();
 }
 
@@ -541,6 +542,7 @@ cudaError_t sort_endpoints(const int32_t *l, const int32_t *r, int64_t q, int64_
     unsigned *err = err_word_ptr();
     if (!err) return cudaErrorUnknown;
     k_pack<<<(unsigned)pctas, kT, 0, s>>>(l, r, q, n, pk, pv, err);
+    note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     for (int p = 0; p < P; ++p) {
@@ -550,6 +552,7 @@ cudaError_t sort_endpoints(const int32_t *l, const int32_t *r, int64_t q, int64_
         k_rs_upsweep<<<(unsigned)ntiles, kT, 0, s>>>(pk, cnt, shift, hist, ntiles);
         if ((e = scan_exclusive(hist, hist, nhist, aux, nullptr, s)) != cudaSuccess) return e;
         k_rs_downsweep<<<(unsigned)ntiles, kT, 0, s>>>(pk, pv, cnt, shift, hist, ntiles, ok, ov);
+        note_launches(2);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         pk = ok;
         pv = ov;
@@ -573,6 +576,7 @@ cudaError_t rank_endpoints(const uint32_t *pos, const uint32_t *tag, int64_t q, 
     cudaError_t e = scan_exclusive(tc, tc, ntiles, aux, m_dev, s);
     if (e != cudaSuccess) return e;
     k_rank_scatter<<<(unsigned)ntiles, kT, 0, s>>>(pos, tag, cnt, tc, P, rank_l, rank_r);
+    note_launches(2);
     return cudaGetLastError();
 }
 
@@ -593,6 +597,7 @@ cudaError_t contract(const int32_t *A, int64_t n, const uint32_t *P, const int64
         k_contract<true><<<(unsigned)ctas, kT, 0, s>>>(src, n, P, m_dev, so, ntA, AQ);
     else
         k_contract<false><<<(unsigned)ctas, kT, 0, s>>>(src, n, P, m_dev, so, ntA, AQ);
+    note_launches(2);
     return cudaGetLastError();
 }
 
@@ -613,7 +618,7 @@ size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con) {
 }
 
 cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q,
-                           int32_t *out, int logk_con, void *ws, cudaStream_t s) {
+                           int32_t *out, int logk_con, void *ws, cudaStream_t s, Stages *st) {
     const int64_t cnt = 2 * q;
     const int64_t mq_max = std::max<int64_t>(cnt - 1, 1);
     const int64_t nbq = cdiv(mq_max, 1ll << logk_con);
@@ -627,12 +632,19 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     uint64_t *T = c.take<uint64_t>(nbq * lv);
     void *scratch = c.p + c.used;
     cudaError_t e;
+    Stages none;
+    if (!st) st = &none;
+    st->mark(s);
     if ((e = sort_endpoints(l, r, q, n, sk, sv, scratch, 0, s)) != cudaSuccess) return e;                 // step 1
+    st->mark(s);
     if ((e = rank_endpoints(sk, sv, q, P, m_dev, ra, rb, scratch, s)) != cudaSuccess) return e;           // step 1
+    st->mark(s);
     if ((e = contract(A, n, P, m_dev, AQ, scratch, s)) != cudaSuccess) return e;                          // step 2
+    st->mark(s);
     const Len lenq{0, m_dev};
     if ((e = launch_block_minima_u64(AQ, lenq, mq_max, logk_con, T, s)) != cudaSuccess) return e;         // step 3
     if ((e = launch_sparse_table(T, lenq, logk_con, nbq, s)) != cudaSuccess) return e;                    // step 3
+    st->mark(s);
     const DevInfo di = dev_info();
     const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(q, 128 * (kT / 32)), (int64_t)di.sms * 8));
     const bool vecq = ((reinterpret_cast<uintptr_t>(l) | reinterpret_cast<uintptr_t>(r) |
@@ -640,7 +652,10 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     SrcU64 src{AQ};
     if (vecq) k_query_con<true><<<(unsigned)ctas, kT, 0, s>>>(src, lenq, logk_con, T, l, r, ra, rb, n, out, q);  // step 4
     else k_query_con<false><<<(unsigned)ctas, kT, 0, s>>>(src, lenq, logk_con, T, l, r, ra, rb, n, out, q);
-    return cudaGetLastError();
+    note_launches(1);
+    e = cudaGetLastError();
+    st->mark(s);
+    return e;
 }
 
 }  // namespace rmq

@@ -115,6 +115,7 @@ cudaError_t block_min_dispatch(Src src, Len len, int64_t n_max, int logk, uint64
         const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(nvec, 128 * (kThreads / 32)), (int64_t)di.sms * 8));
         k_block_min_group<Src, VEC><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0);
     }
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -202,6 +203,7 @@ cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, 
     {
         const int64_t ctas = cdiv(nb_max, kS0);
         k_st_round<1, kLV0><<<(unsigned)ctas, kThreads, smem0, s>>>(T, len, logk, 0, kS0);
+        note_launches(1);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -211,6 +213,7 @@ cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, 
         const int64_t nstr = cdiv(nb_max, stride);
         const int64_t ctas = ngroups * cdiv(nstr, kS1);
         k_st_round<32, kLV1><<<(unsigned)ctas, kThreads, smem1, s>>>(T, len, logk, b, kS1);
+        note_launches(1);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -299,6 +302,7 @@ cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint
     else if (vec) RMQ_LQ(false, true);
     else RMQ_LQ(false, false);
 #undef RMQ_LQ
+    note_launches(1);
     return cudaGetLastError();
 }
 

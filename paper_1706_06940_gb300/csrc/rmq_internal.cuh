@@ -100,6 +100,21 @@ struct Len {
 
 // ---------------------------------------------------------------- host side
 
+// Stage boundaries: when the caller supplies CUDA events, one is recorded
+// on the stream after each stage of the method.
+struct Stages {
+    cudaEvent_t *ev = nullptr;
+    int n = 0;
+    int i = 0;
+    void mark(cudaStream_t s) {
+        if (ev && i < n) cudaEventRecord(ev[i], s);
+        ++i;
+    }
+};
+
+// Process-wide count of kernel launches issued by this library.
+void note_launches(int count);
+
 struct DevInfo {
     int device;
     int sms;
@@ -114,18 +129,16 @@ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 cudaError_t launch_block_minima_i32(const int32_t *A, int64_t n, int logk, uint64_t *T0, cudaStream_t s);
 cudaError_t launch_block_minima_u64(const uint64_t *AQ, Len len, int64_t n_max, int logk, uint64_t *T0,
                                     cudaStream_t s);
-// levels: number of levels of the table for the largest possible nb (host bound);
-// nb: the actual count, either on the host (nb_dev == nullptr) or derived on the
-// device from a Len and logk.
+// The table's block count is nb = ceil(len / 2^logk), read on the device from
+// `len`; nb_max bounds it on the host and sizes the launches.
 cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, cudaStream_t s);
 cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint64_t *T, int64_t nb,
                                const int32_t *l, const int32_t *r, int64_t q, int32_t *out, cudaStream_t s);
 
 // Contracted form (contract.cu).
-struct ConWork;  // workspace layout, see contract.cu
 size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con);
 cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q,
-                           int32_t *out, int logk_con, void *ws, cudaStream_t s);
+                           int32_t *out, int logk_con, void *ws, cudaStream_t s, Stages *st);
 cudaError_t sort_endpoints(const int32_t *l, const int32_t *r, int64_t q, int64_t n, uint32_t *pos_out,
                            uint32_t *tag_out, void *ws, size_t ws_bytes, cudaStream_t s);
 size_t sort_workspace_bytes(int64_t q);

@@ -54,6 +54,9 @@ _i32 = ctypes.c_int32
 _SIGS = {
     "rmq_batch": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, _vp]),
     "rmq_batch_ex": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, ctypes.POINTER(rmq_opts), _vp]),
+    "rmq_batch_timed": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, ctypes.POINTER(rmq_opts), _vp,
+                               ctypes.POINTER(_vp), _i32]),
+    "rmq_launch_count": (_i64, []),
     "rmq_batch_host": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, ctypes.POINTER(rmq_opts), _vp]),
     "rmq_build": (_i32, [_vp, _i64, ctypes.POINTER(rmq_opts), _vp, ctypes.POINTER(_vp)]),
     "rmq_query": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp]),
@@ -147,6 +150,25 @@ def rmq_batch_ex(A, l, r, out, variant=0, k=0, k_con=0, stream=None, flags=0):
     _check(load().rmq_batch_ex(_dptr(A, _i32t(), "A"), A.numel(), _dptr(l, _i32t(), "l"),
                                _dptr(r, _i32t(), "r"), l.numel(), _dptr(out, _i32t(), "out"),
                                ctypes.byref(o), _stream(stream, A)))
+
+
+def rmq_batch_timed(A, l, r, out, events, variant=0, k=0, k_con=0, stream=None):
+    """rmq_batch_ex recording torch.cuda.Event objects at the stage boundaries
+    (4 for the plain form, 6 for the contracted form)."""
+    handles = []
+    for ev in events:
+        if ev.cuda_event == 0:       # torch creates the CUDA event lazily
+            ev.record()
+        handles.append(ev.cuda_event)
+    arr = (ctypes.c_void_p * max(len(handles), 1))(*handles)
+    o = _opts(variant, k, k_con)
+    _check(load().rmq_batch_timed(_dptr(A, _i32t(), "A"), A.numel(), _dptr(l, _i32t(), "l"),
+                                  _dptr(r, _i32t(), "r"), l.numel(), _dptr(out, _i32t(), "out"),
+                                  ctypes.byref(o), _stream(stream, A), arr, len(handles)))
+
+
+def rmq_launch_count() -> int:
+    return int(load().rmq_launch_count())
 
 
 def rmq_batch_host(A, l, r, out, variant=0, k=0, k_con=0, stream=None):
