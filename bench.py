@@ -350,7 +350,7 @@ def run_ours(args, dist):
                 "peak_kind": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
                 else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_launch": bytes_a1,
-                "traffic": profiled_traffic("paper_1706_06940_gb300/csrc/plain.cu",
+                "traffic": profiled_traffic("paper_1706_06940_gb300/csrc/block_min.cu",
                                             "profiles/block_minima_n1e8.md")}
     # whole-form HBM accounting (algorithmic bytes of the plain form)
     hbm_plain = None

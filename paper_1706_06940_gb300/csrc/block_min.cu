@@ -1,0 +1,134 @@
+// block_min.cu -- block minima (Sec. 3.1 step 3, level 0; Sec. 3.2): for every
+// block of k cells, the minimum packed key.  Generic over the source, so the
+// contracted form reuses it over A_Q.
+#include <algorithm>
+
+#include "rmq_internal.cuh"
+
+namespace rmq {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// ------------------------------------------------------------- block minima
+// Warp per block (k / EPV >= 32 vectors): every lane reads k/(32*EPV)
+// consecutive-lane 16-byte vectors (coalesced, streaming), keeps the minimum
+// packed key, and a shuffle reduction gives the block minimum.  UNR vectors
+// are loaded before any is used to keep enough bytes in flight.
+template <class Src, int UNR, bool VEC>
+__global__ void __launch_bounds__(kThreads) k_block_min_warp(Src src, Len len, int logk, uint64_t *__restrict__ T0) {
+    constexpr int EPV = Src::EPV;
+    const int64_t n = len.get();
+    const int64_t K = 1ll << logk;
+    const int64_t nfull = n >> logk;
+    const int64_t nb = (n + K - 1) >> logk;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int vpb = (int)(K / EPV);
+    const int vpl = vpb >> 5;
+    for (int64_t b = warp; b < nfull; b += nwarps) {
+        const int64_t v0 = b * vpb + lane;
+        uint64_t best = KEY_MAX;
+        for (int u = 0; u < vpl; u += UNR) {
+            uint64_t kk[UNR][EPV];
+#pragma unroll
+            for (int x = 0; x < UNR; ++x) src.template vec<VEC>(v0 + (int64_t)(u + x) * 32, kk[x]);
+#pragma unroll
+            for (int x = 0; x < UNR; ++x)
+#pragma unroll
+                for (int e = 0; e < EPV; ++e) best = kmin(best, kk[x][e]);
+        }
+        best = warp_min(best);
+        if (lane == 0) T0[b] = best;
+    }
+    if (nfull < nb && warp == nfull % nwarps) {  // the short last block
+        uint64_t best = KEY_MAX;
+        for (int64_t i = nfull * K + lane; i < n; i += 32) best = kmin(best, src.one(i));
+        best = warp_min(best);
+        if (lane == 0) T0[nfull] = best;
+    }
+}
+
+// Small blocks (k / EPV < 32 vectors): G = k/EPV lanes per block, 32/G blocks
+// per warp row, 4 rows in flight; the reduction is a width-G shuffle.
+template <class Src, bool VEC>
+__global__ void __launch_bounds__(kThreads) k_block_min_group(Src src, Len len, int logk, uint64_t *__restrict__ T0) {
+    constexpr int EPV = Src::EPV;
+    const int64_t n = len.get();
+    const int64_t K = 1ll << logk;
+    const int64_t nfull = n >> logk;
+    const int64_t nb = (n + K - 1) >> logk;
+    const int G = (int)(K / EPV);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nvec = nfull * G;
+    for (int64_t base = warp * 128; base < nvec; base += nwarps * 128) {
+        uint64_t best[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int64_t vi = base + x * 32 + lane;
+            best[x] = KEY_MAX;
+            if (vi < nvec) {
+                uint64_t kk[EPV];
+                src.template vec<VEC>(vi, kk);
+#pragma unroll
+                for (int e = 0; e < EPV; ++e) best[x] = kmin(best[x], kk[e]);
+            }
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            for (int off = G >> 1; off > 0; off >>= 1) best[x] = kmin(best[x], __shfl_xor_sync(0xffffffffu, best[x], off));
+            const int64_t vi = base + x * 32 + lane;
+            if (vi < nvec && (lane % G) == 0) T0[vi / G] = best[x];
+        }
+    }
+    if (nfull < nb && warp == nfull % nwarps) {
+        uint64_t best = KEY_MAX;
+        for (int64_t i = nfull * K + lane; i < n; i += 32) best = kmin(best, src.one(i));
+        best = warp_min(best);
+        if (lane == 0) T0[nfull] = best;
+    }
+}
+
+template <class Src, bool VEC>
+cudaError_t block_min_dispatch(Src src, Len len, int64_t n_max, int logk, uint64_t *T0, cudaStream_t s) {
+    constexpr int EPV = Src::EPV;
+    const DevInfo di = dev_info();
+    const int64_t K = 1ll << logk;
+    const int64_t nb = cdiv(n_max, K);
+    if (nb <= 0) return cudaSuccess;
+    const int vpb = (int)(K / EPV);
+    if (vpb >= 32) {
+        const int64_t ctas = std::min<int64_t>(cdiv(nb, kThreads / 32), (int64_t)di.sms * 8);
+        const int vpl = vpb / 32;
+        if (vpl >= 8) k_block_min_warp<Src, 8, VEC><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0);
+        else if (vpl >= 4) k_block_min_warp<Src, 4, VEC><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0);
+        else if (vpl >= 2) k_block_min_warp<Src, 2, VEC><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0);
+        else k_block_min_warp<Src, 1, VEC><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0);
+    } else {
+        const int64_t nvec = nb * vpb;
+        const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(nvec, 128 * (kThreads / 32)), (int64_t)di.sms * 8));
+        k_block_min_group<Src, VEC><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0);
+    }
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_block_minima_i32(const int32_t *A, int64_t n, int logk, uint64_t *T0, cudaStream_t s) {
+    SrcI32 src{A};
+    Len len{n, nullptr};
+    if ((reinterpret_cast<uintptr_t>(A) & 15) == 0) return block_min_dispatch<SrcI32, true>(src, len, n, logk, T0, s);
+    return block_min_dispatch<SrcI32, false>(src, len, n, logk, T0, s);
+}
+
+cudaError_t launch_block_minima_u64(const uint64_t *AQ, Len len, int64_t n_max, int logk, uint64_t *T0,
+                                    cudaStream_t s) {
+    return block_min_dispatch<SrcU64, true>(SrcU64{AQ}, len, n_max, logk, T0, s);
+}
+
+}  // namespace rmq

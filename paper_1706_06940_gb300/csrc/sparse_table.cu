@@ -1,0 +1,102 @@
+// sparse_table.cu -- the sparse table over block minima (Sec. 3.1 step 3):
+// level t at block j is the minimum over the 2^t blocks starting at j.
+#include <algorithm>
+
+#include "rmq_internal.cuh"
+
+namespace rmq {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// ------------------------------------------------------------ sparse table
+// Level t holds, for block j, the minimum over the 2^t blocks starting at j
+// (Sec. 3.1 step 3).  Levels are produced in rounds; a round starting from
+// level b computes levels b+1 .. b+nlev in shared memory by doubling:
+//   level b+u at j = min over i < 2^u of level b at j + i * 2^b.
+// A CTA owns R residues rho (mod 2^b) and S consecutive strides s, i.e. the
+// entries j = rho0 + rho + (s0 + s) * 2^b; it loads the S + 2^nlev rows it
+// needs once (coalesced along rho for R = 32, along s for R = 1), doubles in
+// ping-pong buffers and writes every level's rows < S.  Round 0 uses R = 1
+// (contiguous tiles); later rounds start at b >= 5, so R = 32 divides 2^b.
+template <int R, int LV>
+__global__ void __launch_bounds__(kThreads) k_st_round(uint64_t *__restrict__ T, Len len, int logk, int b, int S) {
+    const int64_t n = len.get();
+    const int64_t nb = (n + (1ll << logk) - 1) >> logk;
+    if (nb < 2) return;
+    const int top = ilog2_dev((uint64_t)nb);
+    if (b >= top) return;
+    const int nlev = min(LV, top - b);
+    const int rows = S + (1 << nlev);
+    const int64_t stride = 1ll << b;
+    const int64_t ngroups = (R == 1) ? 1 : (stride / R);
+    const int64_t g = blockIdx.x % ngroups;
+    const int64_t st = blockIdx.x / ngroups;
+    const int64_t rho0 = g * R;
+    const int64_t s0 = st * (int64_t)S;
+    if (rho0 + s0 * stride >= nb) return;
+    extern __shared__ uint64_t smem[];
+    uint64_t *X = smem;
+    uint64_t *Y = smem + (size_t)rows * R;
+    const uint64_t *Tb = T + (int64_t)b * nb;
+    for (int i = threadIdx.x; i < rows * R; i += blockDim.x) {
+        const int srow = i / R, c = i % R;
+        const int64_t j = rho0 + c + (s0 + srow) * stride;
+        X[i] = (j < nb) ? Tb[j] : KEY_MAX;
+    }
+    __syncthreads();
+    for (int u = 1; u <= nlev; ++u) {
+        const int half = 1 << (u - 1);
+        const int cnt = rows - (1 << u) + 1;
+        for (int i = threadIdx.x; i < cnt * R; i += blockDim.x) Y[i] = kmin(X[i], X[i + half * R]);
+        __syncthreads();
+        const int64_t span = 1ll << (b + u);
+        uint64_t *Tu = T + (int64_t)(b + u) * nb;
+        for (int i = threadIdx.x; i < S * R; i += blockDim.x) {
+            const int srow = i / R, c = i % R;
+            const int64_t j = rho0 + c + (s0 + srow) * stride;
+            if (j + span <= nb) Tu[j] = Y[i];
+        }
+        uint64_t *tmp = X; X = Y; Y = tmp;
+    }
+}
+
+constexpr int kLV0 = 12, kS0 = 256;   // round 0: levels 1..12, 256 outputs per CTA
+constexpr int kLV1 = 6, kS1 = 64;     // later rounds: 6 levels, 32 residues x 64 strides
+
+}  // namespace
+
+cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, cudaStream_t s) {
+    if (nb_max < 2) return cudaSuccess;
+    const int top = ilog2_host((uint64_t)nb_max);
+    static bool attr_done[64] = {false};
+    const DevInfo di = dev_info();
+    const size_t smem0 = 2ull * (kS0 + (1 << kLV0)) * 1 * sizeof(uint64_t);
+    const size_t smem1 = 2ull * (kS1 + (1 << kLV1)) * 32 * sizeof(uint64_t);
+    if (di.device < 64 && !attr_done[di.device]) {
+        cudaFuncSetAttribute(k_st_round<1, kLV0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem0);
+        cudaFuncSetAttribute(k_st_round<32, kLV1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+        attr_done[di.device] = true;
+    }
+    {
+        const int64_t ctas = cdiv(nb_max, kS0);
+        k_st_round<1, kLV0><<<(unsigned)ctas, kThreads, smem0, s>>>(T, len, logk, 0, kS0);
+        note_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    for (int b = kLV0; b < top; b += kLV1) {
+        const int64_t stride = 1ll << b;
+        const int64_t ngroups = stride / 32;
+        const int64_t nstr = cdiv(nb_max, stride);
+        const int64_t ctas = ngroups * cdiv(nstr, kS1);
+        k_st_round<32, kLV1><<<(unsigned)ctas, kThreads, smem1, s>>>(T, len, logk, b, kS1);
+        note_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace rmq
