@@ -64,7 +64,8 @@ typedef enum {
     RMQ_ERR_OOM = 3,           /* device memory for workspace or a handle ran out */
     RMQ_ERR_CUDA = 4,          /* a CUDA runtime call failed */
     RMQ_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
-    RMQ_ERR_BUDGET = 6         /* a memory budget set by the caller would be exceeded */
+    RMQ_ERR_BUDGET = 6,        /* a memory budget set by the caller would be exceeded */
+    RMQ_ERR_SCRATCH_LIMIT = 7  /* rmq_batch_noalloc: the table does not fit its fixed buffer */
 } rmq_status;
 
 typedef enum {
@@ -80,6 +81,10 @@ typedef struct {
     int32_t k_con;     /* block size over A_Q (contracted form): 0 = tuned, else a power of 2 in [32, 65536] */
     int32_t flags;     /* reserved, must be 0 */
 } rmq_opts;
+
+/* Capacity of the fixed table buffer of rmq_batch_noalloc, in 8-byte entries
+ * (4 MiB). */
+#define RMQ_NOALLOC_TABLE_ENTRIES (1 << 19)
 
 /* ------------------------------------------------------------------ batch */
 
@@ -113,6 +118,29 @@ rmq_status rmq_batch_timed(const int32_t *A, int64_t n, const int32_t *l, const 
 rmq_status rmq_batch_host(const int32_t *A_host, int64_t n, const int32_t *l_host,
                           const int32_t *r_host, int64_t q, int32_t *out_host,
                           const rmq_opts *opts, void *stream);
+
+/* Plain-BbST batch that allocates no device memory (the paper has no
+ * counterpart: this is a deployment variant of rmq_batch_ex with the plain
+ * form).  Some callers cannot call cudaMalloc: hosts that reserve all device
+ * memory for their own allocator up front, and loops that forbid allocation
+ * after start-up because it can synchronise the device and take unbounded
+ * time.  This entry point keeps the sparse table in a fixed buffer of
+ * RMQ_NOALLOC_TABLE_ENTRIES entries (4 MiB) inside the library's device image,
+ * held on every GPU that loads the library until the process exits; it calls
+ * no cudaMalloc, cudaFree or other allocating routine.  The caller passes A, l,
+ * r and out as for rmq_batch_ex.
+ *   k: block size, a power of 2 in [32, 65536], or 0 for the tuned k, raised
+ *      (doubled) until the table fits.
+ *   Returns RMQ_ERR_SCRATCH_LIMIT, enqueuing nothing, when the table for (n, k)
+ *   needs more than RMQ_NOALLOC_TABLE_ENTRIES entries (rmq_table_bytes(n, k) / 8).
+ * The first call on a device looks up the buffer's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls on a device share the one buffer, and every entry a call
+ * reads is written by that call first, so leftovers of earlier calls do not
+ * matter; but calls whose work overlaps on the GPU (other streams, or other
+ * threads) race on the buffer and must be serialised by the caller. */
+rmq_status rmq_batch_noalloc(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r,
+                             int64_t q, int32_t *out, int32_t k, void *stream);
 
 /* -------------------------------------------------------- resident arrays */
 

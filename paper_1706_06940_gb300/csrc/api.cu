@@ -331,6 +331,7 @@ const char *rmq_strerror(rmq_status s) {
         case RMQ_ERR_CUDA: return "a CUDA runtime call failed";
         case RMQ_ERR_TIMEOUT: return "a bounded device-side wait timed out";
         case RMQ_ERR_BUDGET: return "the memory budget would be exceeded";
+        case RMQ_ERR_SCRATCH_LIMIT: return "the table does not fit the fixed buffer of rmq_batch_noalloc";
     }
     return "unknown status";
 }

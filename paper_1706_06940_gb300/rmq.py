@@ -29,6 +29,7 @@ class Status(enum.IntEnum):
     ERR_CUDA = 4
     ERR_TIMEOUT = 5
     ERR_BUDGET = 6
+    ERR_SCRATCH_LIMIT = 7
 
 
 class Variant(enum.IntEnum):
@@ -57,6 +58,7 @@ _SIGS = {
     "rmq_batch_timed": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, ctypes.POINTER(rmq_opts), _vp,
                                ctypes.POINTER(_vp), _i32]),
     "rmq_launch_count": (_i64, []),
+    "rmq_batch_noalloc": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, _i32, _vp]),
     "rmq_batch_host": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, ctypes.POINTER(rmq_opts), _vp]),
     "rmq_build": (_i32, [_vp, _i64, ctypes.POINTER(rmq_opts), _vp, ctypes.POINTER(_vp)]),
     "rmq_query": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp]),
@@ -165,6 +167,14 @@ def rmq_batch_timed(A, l, r, out, events, variant=0, k=0, k_con=0, stream=None):
     _check(load().rmq_batch_timed(_dptr(A, _i32t(), "A"), A.numel(), _dptr(l, _i32t(), "l"),
                                   _dptr(r, _i32t(), "r"), l.numel(), _dptr(out, _i32t(), "out"),
                                   ctypes.byref(o), _stream(stream, A), arr, len(handles)))
+
+
+def rmq_batch_noalloc(A, l, r, out, k=0, stream=None):
+    """Plain-form batch whose table sits in the library's fixed device buffer
+    (no device allocation); see include/rmq.h."""
+    _check(load().rmq_batch_noalloc(_dptr(A, _i32t(), "A"), A.numel(), _dptr(l, _i32t(), "l"),
+                                    _dptr(r, _i32t(), "r"), l.numel(), _dptr(out, _i32t(), "out"),
+                                    int(k), _stream(stream, A)))
 
 
 def rmq_launch_count() -> int:
