@@ -83,7 +83,7 @@ typedef struct {
 } rmq_opts;
 
 /* Capacity of the fixed table buffer of rmq_batch_noalloc, in 8-byte entries
- * (4 MiB). */
+ * (4 MiB; the buffer also holds the table's 32 KiB coarse summary). */
 #define RMQ_NOALLOC_TABLE_ENTRIES (1 << 19)
 
 /* ------------------------------------------------------------------ batch */
@@ -125,7 +125,8 @@ rmq_status rmq_batch_host(const int32_t *A_host, int64_t n, const int32_t *l_hos
  * memory for their own allocator up front, and loops that forbid allocation
  * after start-up because it can synchronise the device and take unbounded
  * time.  This entry point keeps the sparse table in a fixed buffer of
- * RMQ_NOALLOC_TABLE_ENTRIES entries (4 MiB) inside the library's device image,
+ * RMQ_NOALLOC_TABLE_ENTRIES entries (4 MiB, plus 32 KiB for the table's
+ * coarse summary) inside the library's device image,
  * held on every GPU that loads the library until the process exits; it calls
  * no cudaMalloc, cudaFree or other allocating routine.  The caller passes A, l,
  * r and out as for rmq_batch_ex.

@@ -155,16 +155,19 @@ rmq_status batch_plain(const int32_t *A, int64_t n, const int32_t *l, const int3
                        int logk, cudaStream_t s, Stages *sg) {
     const int64_t nb = cdiv(n, 1ll << logk);
     Workspace ws;
-    rmq_status st = ws.alloc((size_t)table_entries(n, logk) * 8, s);
+    const int64_t te = two_level_entries(nb);
+    rmq_status st = ws.alloc((size_t)(te + kCoarseCap) * 8 + query_residual_bytes(q, dev_info().sms), s);
     if (st != RMQ_OK) return st;
     uint64_t *T = static_cast<uint64_t *>(ws.p);
+    uint64_t *Cs = T + te;
+    void *res = Cs + kCoarseCap;
     cudaError_t e;
     sg->mark(s);
     if ((e = launch_block_minima_i32(A, n, logk, T, s)) != cudaSuccess) return cuda_status(e);
     sg->mark(s);
-    if ((e = launch_sparse_table(T, Len{n, nullptr}, logk, nb, s)) != cudaSuccess) return cuda_status(e);
+    if ((e = launch_sparse_table(T, Len{n, nullptr}, logk, nb, s, Cs)) != cudaSuccess) return cuda_status(e);
     sg->mark(s);
-    e = launch_query_plain(A, n, logk, T, nb, l, r, q, out, s);
+    e = launch_query_plain(A, n, logk, T, Cs, nb, l, r, q, out, res, s);
     sg->mark(s);
     return cuda_status(e);
 }
@@ -196,6 +199,7 @@ struct rmq_handle_s {
     int logk;
     int64_t nb;
     uint64_t *T;
+    uint64_t *Cs;  // coarse summary, right after the table
     int64_t bytes;
     int device;
 };
@@ -267,7 +271,8 @@ rmq_status rmq_build(const int32_t *A, int64_t n, const rmq_opts *opts, void *st
     h->n = n;
     h->logk = logk;
     h->nb = cdiv(n, 1ll << logk);
-    h->bytes = table_entries(n, logk) * 8;
+    const int64_t te = two_level_entries(h->nb);
+    h->bytes = (te + kCoarseCap) * 8;
     cudaGetDevice(&h->device);
     cudaError_t e = cudaMalloc(&h->T, (size_t)h->bytes);
     if (e != cudaSuccess) {
@@ -276,8 +281,9 @@ rmq_status rmq_build(const int32_t *A, int64_t n, const rmq_opts *opts, void *st
         return e == cudaErrorMemoryAllocation ? RMQ_ERR_OOM : RMQ_ERR_CUDA;
     }
     cudaStream_t s = as_stream(stream);
+    h->Cs = h->T + te;
     if ((e = launch_block_minima_i32(A, n, logk, h->T, s)) != cudaSuccess ||
-        (e = launch_sparse_table(h->T, Len{n, nullptr}, logk, h->nb, s)) != cudaSuccess) {
+        (e = launch_sparse_table(h->T, Len{n, nullptr}, logk, h->nb, s, h->Cs)) != cudaSuccess) {
         cudaFree(h->T);
         delete h;
         return cuda_status(e);
@@ -290,7 +296,11 @@ rmq_status rmq_query(rmq_handle h, const int32_t *l, const int32_t *r, int64_t q
     if (!h || q < 0 || q > kMaxQ) return RMQ_ERR_INVALID_ARG;
     if (q == 0) return RMQ_OK;
     if (!l || !r || !out) return RMQ_ERR_INVALID_ARG;
-    return cuda_status(launch_query_plain(h->A, h->n, h->logk, h->T, h->nb, l, r, q, out, as_stream(stream)));
+    cudaStream_t s = as_stream(stream);
+    Workspace ws;
+    rmq_status st = ws.alloc(query_residual_bytes(q, dev_info().sms), s);
+    if (st != RMQ_OK) return st;
+    return cuda_status(launch_query_plain(h->A, h->n, h->logk, h->T, h->Cs, h->nb, l, r, q, out, ws.p, s));
 }
 
 int64_t rmq_handle_bytes(rmq_handle h) { return h ? h->bytes : 0; }

@@ -3,6 +3,7 @@
 // to A_Q[j] = min over A[P_j .. P_{j+1}] (step 2), then the block table over
 // A_Q (step 3, kernels of plain.cu) and query answering over A_Q (step 4).
 #include <algorithm>
+#include <climits>
 
 #include "query.cuh"
 #include "rmq_internal.cuh"
@@ -14,7 +15,7 @@ namespace {
 constexpr int kT = 256;                 // threads per CTA
 constexpr int kIPT = 16;                // items per thread
 constexpr int kTile = kT * kIPT;        // 4096 items per CTA tile
-constexpr int kRadixBits = 8;
+constexpr int kRadixBits = 9;           // digits of at most 9 bits: 3 passes for positions below 2^27
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kATile = 1024;            // elements of A per warp in the contraction
 
@@ -146,17 +147,21 @@ __global__ void __launch_bounds__(kT) k_pack(const int32_t *__restrict__ L, cons
 // downsweep per digit.  Within a tile items keep their input order (warp w
 // owns items [512w, 512w + 512) in rows of 32), so every pass is stable.
 __global__ void __launch_bounds__(kT) k_rs_upsweep(const uint32_t *__restrict__ keys, int64_t cnt, int shift,
-                                                   uint32_t *__restrict__ hist, int64_t ntiles) {
+                                                   uint32_t mask, uint32_t *__restrict__ hist, int64_t ntiles) {
     __shared__ uint32_t h[kT / 32][kRadix];
     const int w = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < (kT / 32) * kRadix; i += kT) (&h[0][0])[i] = 0;
-    __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kTile;
-#pragma unroll 4
+    uint32_t kr[kIPT];
+#pragma unroll
     for (int i = 0; i < kIPT; ++i) {
         const int64_t idx = base + i * kT + threadIdx.x;
-        if (idx < cnt) atomicAdd(&h[w][(keys[idx] >> shift) & (kRadix - 1)], 1u);
+        kr[i] = idx < cnt ? __ldcs(keys + idx) : 0xffffffffu;
     }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kIPT; ++i)
+        if (base + i * kT + threadIdx.x < cnt) atomicAdd(&h[w][(kr[i] >> shift) & mask], 1u);
     __syncthreads();
     for (int d = threadIdx.x; d < kRadix; d += kT) {
         uint32_t s = 0;
@@ -166,57 +171,83 @@ __global__ void __launch_bounds__(kT) k_rs_upsweep(const uint32_t *__restrict__ 
     }
 }
 
-__global__ void __launch_bounds__(kT) k_rs_downsweep(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
-                                                     int64_t cnt, int shift, const uint32_t *__restrict__ goff,
+__global__ void __launch_bounds__(kT, 3) k_rs_downsweep(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                                     int64_t cnt, int shift, int width,
+                                                     const uint32_t *__restrict__ goff,
                                                      int64_t ntiles, uint32_t *__restrict__ kout,
                                                      uint32_t *__restrict__ vout) {
-    __shared__ uint32_t wcnt[kT / 32][kRadix];
-    __shared__ uint32_t dstart[kRadix];
+    __shared__ uint16_t wcnt[kT / 32][kRadix];   // per warp and digit: count, then tile offset (< 4096)
     __shared__ uint32_t gbase[kRadix];
     __shared__ uint32_t ks[kTile];
     __shared__ uint32_t vs[kTile];
     __shared__ uint32_t wsum[kT / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
+    const uint32_t mask = (1u << width) - 1u;
     for (int i = threadIdx.x; i < (kT / 32) * kRadix; i += kT) (&wcnt[0][0])[i] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kTile;
     uint32_t kr[kIPT], vr[kIPT], lo[kIPT];
 #pragma unroll
+    for (int row = 0; row < kIPT; ++row) {             // every load of the tile is in flight at once
+        const int64_t idx = base + w * (32 * kIPT) + row * 32 + lane;
+        kr[row] = idx < cnt ? __ldcs(kin + idx) : 0u;
+        vr[row] = idx < cnt ? __ldcs(vin + idx) : 0u;
+    }
+#pragma unroll
     for (int row = 0; row < kIPT; ++row) {
         const int64_t idx = base + w * (32 * kIPT) + row * 32 + lane;
         const bool valid = idx < cnt;
-        const uint32_t k = valid ? kin[idx] : 0u;
-        const uint32_t v = valid ? vin[idx] : 0u;
-        const uint32_t d = (k >> shift) & (kRadix - 1);
-        const unsigned peers = __match_any_sync(0xffffffffu, valid ? d : 0x100u);
+        const uint32_t k = kr[row];
+        const uint32_t d = (k >> shift) & mask;
+        // lanes holding the same digit: intersect one ballot per digit bit
+        unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int b = 0; b < kRadixBits; ++b) {  // bits above the digit width are 0 in every lane
+            const bool bit = (d >> b) & 1u;
+            const unsigned bb = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? bb : ~bb;
+        }
         const uint32_t rank = __popc(peers & lt);
         const uint32_t before = valid ? wcnt[w][d] : 0u;
         __syncwarp();
-        if (valid && rank == 0) wcnt[w][d] = before + __popc(peers);
+        if (valid && rank == 0) wcnt[w][d] = (uint16_t)(before + __popc(peers));
         __syncwarp();
-        kr[row] = k;
-        vr[row] = v;
         lo[row] = before + rank;
     }
     __syncthreads();
-    uint32_t run = 0;
-    for (int x = 0; x < kT / 32; ++x) {
-        const uint32_t c = wcnt[x][threadIdx.x];
-        wcnt[x][threadIdx.x] = run;
-        run += c;
+    // per digit: exclusive prefix over the warps, then over the digits
+    constexpr int DPT = kRadix / kT;  // digits per thread
+    uint32_t run[DPT], tsum = 0;
+#pragma unroll
+    for (int x = 0; x < DPT; ++x) {
+        const int d = threadIdx.x * DPT + x;
+        uint32_t r = 0;
+        for (int y = 0; y < kT / 32; ++y) r += wcnt[y][d];
+        run[x] = r;
+        tsum += r;
     }
     uint32_t total;
-    const uint32_t ex = block_excl_scan(run, wsum, total);
-    dstart[threadIdx.x] = ex;
-    gbase[threadIdx.x] = goff[(int64_t)threadIdx.x * ntiles + blockIdx.x] - ex;
+    uint32_t ex = block_excl_scan(tsum, wsum, total);
+#pragma unroll
+    for (int x = 0; x < DPT; ++x) {
+        const int d = threadIdx.x * DPT + x;
+        gbase[d] = goff[(int64_t)d * ntiles + blockIdx.x] - ex;
+        uint32_t r = ex;                       // tile offset of digit d for each warp
+        for (int y = 0; y < kT / 32; ++y) {
+            const uint32_t c = wcnt[y][d];
+            wcnt[y][d] = (uint16_t)r;
+            r += c;
+        }
+        ex += run[x];
+    }
     __syncthreads();
 #pragma unroll
     for (int row = 0; row < kIPT; ++row) {
         const int64_t idx = base + w * (32 * kIPT) + row * 32 + lane;
         if (idx < cnt) {
-            const uint32_t d = (kr[row] >> shift) & (kRadix - 1);
-            const uint32_t p = dstart[d] + wcnt[w][d] + lo[row];
+            const uint32_t d = (kr[row] >> shift) & mask;
+            const uint32_t p = wcnt[w][d] + lo[row];
             ks[p] = kr[row];
             vs[p] = vr[row];
         }
@@ -225,7 +256,7 @@ __global__ void __launch_bounds__(kT) k_rs_downsweep(const uint32_t *__restrict_
     const int tcnt = (int)((cnt - base) < kTile ? (cnt - base) : kTile);
     for (int i = threadIdx.x; i < tcnt; i += kT) {
         const uint32_t k = ks[i];
-        const uint32_t g = gbase[(k >> shift) & (kRadix - 1)] + (uint32_t)i;
+        const uint32_t g = gbase[(k >> shift) & mask] + (uint32_t)i;
         kout[g] = k;
         vout[g] = vs[i];
     }
@@ -233,23 +264,22 @@ __global__ void __launch_bounds__(kT) k_rs_downsweep(const uint32_t *__restrict_
 
 // ------------------------------------------------------------------ rank
 // flag(i) = (i == 0 || key[i] != key[i-1]); rank(i) = (#flags in [0, i]) - 1.
-__device__ __forceinline__ bool rank_flag(const uint32_t *K, int64_t idx, int64_t cnt, uint32_t &k) {
-    if (idx >= cnt) return false;
-    k = K[idx];
-    return idx == 0 || K[idx - 1] != k;
-}
-
 __global__ void __launch_bounds__(kT) k_rank_count(const uint32_t *__restrict__ K, int64_t cnt,
                                                    uint32_t *__restrict__ tile_cnt) {
     __shared__ uint32_t wsum[kT / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t base = (int64_t)blockIdx.x * kTile + w * (32 * kIPT);
-    uint32_t c = 0;
-#pragma unroll 4
+    uint32_t kr[kIPT], pv[kIPT];
+#pragma unroll
     for (int row = 0; row < kIPT; ++row) {
-        uint32_t k;
-        c += __popc(__ballot_sync(0xffffffffu, rank_flag(K, base + row * 32 + lane, cnt, k)));
+        const int64_t idx = base + row * 32 + lane;
+        kr[row] = idx < cnt ? K[idx] : 0u;
+        pv[row] = (idx < cnt && idx > 0) ? K[idx - 1] : ~kr[row];
     }
+    uint32_t c = 0;
+#pragma unroll
+    for (int row = 0; row < kIPT; ++row)
+        c += __popc(__ballot_sync(0xffffffffu, base + row * 32 + lane < cnt && kr[row] != pv[row]));
     uint32_t total;
     block_excl_scan(lane == 0 ? c : 0u, wsum, total);
     if (threadIdx.x == 0) tile_cnt[blockIdx.x] = total;
@@ -263,12 +293,19 @@ __global__ void __launch_bounds__(kT) k_rank_scatter(const uint32_t *__restrict_
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
     const int64_t base = (int64_t)blockIdx.x * kTile + w * (32 * kIPT);
+    uint32_t kr[kIPT], vr[kIPT];
     unsigned bal[kIPT];
     uint32_t c = 0;
 #pragma unroll
     for (int row = 0; row < kIPT; ++row) {
-        uint32_t k;
-        bal[row] = __ballot_sync(0xffffffffu, rank_flag(K, base + row * 32 + lane, cnt, k));
+        const int64_t idx = base + row * 32 + lane;
+        kr[row] = idx < cnt ? K[idx] : 0u;
+        vr[row] = idx < cnt ? __ldcs(V + idx) : 0u;
+        bal[row] = (idx < cnt && idx > 0) ? K[idx - 1] : ~kr[row];   // previous key, for the flag below
+    }
+#pragma unroll
+    for (int row = 0; row < kIPT; ++row) {
+        bal[row] = __ballot_sync(0xffffffffu, base + row * 32 + lane < cnt && kr[row] != bal[row]);
         c += __popc(bal[row]);
     }
     uint32_t total;
@@ -280,8 +317,8 @@ __global__ void __launch_bounds__(kT) k_rank_scatter(const uint32_t *__restrict_
         if (idx < cnt) {
             const bool f = (bal[row] >> lane) & 1u;
             const int32_t rank = (int32_t)(run + __popc(bal[row] & lt) + (f ? 1u : 0u)) - 1;
-            if (f) P[rank] = K[idx];
-            const uint32_t tag = V[idx];
+            if (f) P[rank] = kr[row];
+            const uint32_t tag = vr[row];
             if (tag & 1u) rank_r[tag >> 1] = rank;
             else rank_l[tag >> 1] = rank;
         }
@@ -316,191 +353,153 @@ __device__ __forceinline__ void emit_atomic(uint64_t *H, int64_t s, uint64_t v) 
         atomicMin(reinterpret_cast<unsigned long long *>(H) + s, (unsigned long long)v);
 }
 
-// One warp per tile of kATile = 1024 cells: 8 rows of 32 lanes x 4 cells.
-// Segment j covers A[P_j .. P_{j+1}]; a boundary cell P_j closes segment j-1
-// (it is its last cell) and opens segment j.  Each row finds its lanes'
-// boundary bits in a per-warp bitmap, every lane folds its 4 cells into the
-// segment open at its start (head), closes segments that begin and end inside
-// it, and leaves its last segment open (tail); a segmented min-scan over the
-// lanes then carries each open value to the lane that closes it.
+// One warp per tile of kATile = 1024 cells; lane L owns the 32 consecutive
+// cells [32L, 32L + 32) of the tile.  Segment j covers A[P_j .. P_{j+1}]; a
+// boundary cell P_j closes segment j-1 (it is its last cell) and opens
+// segment j.  The tile is read with coalesced 16-byte loads and handed to the
+// lanes through shared memory (swizzled so that neither side has bank
+// conflicts); the boundaries of the tile form a 1024-bit bitmap, one word per
+// lane.  The b-th boundary of the tile closes segment s_t + b, so every lane
+// writes the value of each segment it closes into slot b of a per-warp array;
+// a segmented min-scan over the lanes adds, to the first slot of each lane,
+// the part of that segment held by the lanes before it; the slots are then
+// stored to A_Q in order (coalesced).  Only the first segment (begun in an
+// earlier tile) and the one left open at the end are combined with atomics.
+__device__ __forceinline__ int swz(int x) { return (x & ~7) | ((x & 7) ^ ((x >> 3) & 7)); }
+
+constexpr int kContractSmem = (kT / 32) * kATile * 8 + (kT / 32) * 32 * 4;   // slots (tile view) + bitmaps
+
 template <bool VEC>
 __global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const uint32_t *__restrict__ P,
                                                  const int64_t *m_dev, const int32_t *__restrict__ so, int64_t ntA,
                                                  uint64_t *__restrict__ H) {
-    __shared__ uint32_t bm[kT / 32][kATile / 32];
+    extern __shared__ uint64_t csmem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const unsigned lt = lanemask_lt();
+    uint64_t *slot = csmem + (size_t)w * kATile;                      // 1024 slots per warp
+    int4 *tile = reinterpret_cast<int4 *>(slot);                      // the same memory, first 4 KB
+    uint32_t *bm = reinterpret_cast<uint32_t *>(csmem + (size_t)(kT / 32) * kATile) + w * 32;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t m = *m_dev;
     const int64_t nv = n / 4;  // vectors wholly inside [0, n)
     for (int64_t t = warp; t < ntA; t += nwarps) {
+        // the tile's cells are requested together with its segment numbers (one
+        // round trip); tiles outside [P_0, P_{m-1}] are skipped after the fact
         const int64_t s_t = so[t], s_n = so[t + 1];
-        if (s_t == s_n && (s_t < 0 || s_t > m - 2)) continue;
         const int64_t ts = t * kATile;
-        uint64_t kk[8][4];
+        int4 v[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int64_t vi = ts / 4 + u * 32 + lane;
             if (vi < nv) {
-                src.template vec<VEC>(vi, kk[u]);
+                v[u] = VEC ? ld_stream_v4(reinterpret_cast<const int4 *>(src.a) + vi)
+                           : make_int4(__ldg(src.a + 4 * vi), __ldg(src.a + 4 * vi + 1), __ldg(src.a + 4 * vi + 2),
+                                       __ldg(src.a + 4 * vi + 3));
             } else {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) kk[u][e] = (vi * 4 + e < n) ? src.one(vi * 4 + e) : KEY_MAX;
+                const int64_t e = 4 * vi;
+                v[u] = make_int4(e < n ? __ldg(src.a + e) : INT_MAX, e + 1 < n ? __ldg(src.a + e + 1) : INT_MAX,
+                                 e + 2 < n ? __ldg(src.a + e + 2) : INT_MAX, e + 3 < n ? __ldg(src.a + e + 3) : INT_MAX);
             }
         }
-        if (s_t == s_n) {  // no boundary in the tile: one partial minimum
-            uint64_t v = KEY_MAX;
+        if (s_t == s_n && (s_t < 0 || s_t > m - 2)) continue;
+        if (s_t == s_n) {  // no boundary in the tile: one partial minimum of segment s_t
+            uint64_t best = KEY_MAX;
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) v = kmin(v, kk[u][e]);
-            v = warp_min(v);
-            if (lane == 0) emit_atomic(H, s_t, v);
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t e = (uint32_t)(ts + 4 * (u * 32 + lane));
+                best = kmin(best, kmin(kmin(make_key(v[u].x, e), make_key(v[u].y, e + 1)),
+                                       kmin(make_key(v[u].z, e + 2), make_key(v[u].w, e + 3))));
+            }
+            best = warp_min(best);
+            if (lane == 0) emit_atomic(H, s_t, best);
             continue;
         }
-        __syncwarp();  // every lane is done reading the previous tile's bitmap
-        bm[w][lane] = 0;
+        __syncwarp();  // the previous tile's slots are no longer read
+#pragma unroll
+        for (int u = 0; u < 8; ++u) tile[swz(u * 32 + lane)] = v[u];
+        bm[lane] = 0;
         __syncwarp();
-        for (int64_t j = s_t + 1 + lane; j <= s_n; j += 32) {
-            const uint32_t off = (uint32_t)((int64_t)P[j] - ts);
-            atomicOr(&bm[w][off >> 5], 1u << (off & 31));
+        const int cnt = (int)(s_n - s_t);
+        for (int64_t j0 = s_t + 1; j0 <= s_n; j0 += 256) {
+            uint32_t pp[8];
+#pragma unroll
+            for (int x = 0; x < 8; ++x) {
+                const int64_t j = j0 + x * 32 + lane;
+                pp[x] = j <= s_n ? P[j] : 0xffffffffu;
+            }
+#pragma unroll
+            for (int x = 0; x < 8; ++x)
+                if (pp[x] != 0xffffffffu) {
+                    const uint32_t off = (uint32_t)((int64_t)pp[x] - ts);
+                    atomicOr(&bm[off >> 5], 1u << (off & 31));
+                }
         }
         __syncwarp();
-        int64_t open = s_t;
-        uint64_t carry = KEY_MAX;
+        const uint32_t word = bm[lane];
+        const uint32_t nbits = __popc(word);
+        uint32_t pre = nbits;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const unsigned bits = (bm[w][4 * u + (lane >> 3)] >> ((lane & 7) * 4)) & 0xFu;
-            const unsigned nb1 = __popc(bits);
-            const unsigned b0 = __ballot_sync(0xffffffffu, nb1 & 1u);
-            const unsigned b1 = __ballot_sync(0xffffffffu, nb1 & 2u);
-            const unsigned b2 = __ballot_sync(0xffffffffu, nb1 & 4u);
-            const int tot = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
-            if (tot == 0) {
-                uint64_t v = kmin(kmin(kk[u][0], kk[u][1]), kmin(kk[u][2], kk[u][3]));
-                carry = kmin(carry, warp_min(v));
-                continue;
-            }
-            const int pre = __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt);
-            const int64_t seg0 = open + pre;
-            uint64_t head = KEY_MAX, cur = KEY_MAX;
-            int64_t s = seg0;
-            bool closed = false;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const uint64_t k = kk[u][e];
-                if ((bits >> e) & 1u) {
-                    const uint64_t v = kmin(cur, k);
-                    if (!closed) { head = v; closed = true; }
-                    else if (s >= 0 && s <= m - 2) H[s] = v;  // opened and closed inside this lane
-                    ++s;
-                    cur = k;
-                } else {
-                    cur = kmin(cur, k);
-                }
-            }
-            bool f = closed;
-            uint64_t val = cur;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const bool of = __shfl_up_sync(0xffffffffu, f, d);
-                const uint64_t ov = __shfl_up_sync(0xffffffffu, val, d);
-                if (lane >= d) {
-                    if (!f) val = kmin(val, ov);
-                    f = f || of;
-                }
-            }
-            bool exf = __shfl_up_sync(0xffffffffu, f, 1);
-            uint64_t exv = __shfl_up_sync(0xffffffffu, val, 1);
-            if (lane == 0) { exf = false; exv = KEY_MAX; }
-            const uint64_t carry_in = exf ? exv : kmin(carry, exv);
-            if (closed && seg0 >= 0 && seg0 <= m - 2) {
-                const uint64_t tv = kmin(carry_in, head);
-                if (seg0 == s_t) emit_atomic(H, seg0, tv);
-                else H[seg0] = tv;
-            }
-            const bool lf = __shfl_sync(0xffffffffu, f, 31);
-            const uint64_t lv = __shfl_sync(0xffffffffu, val, 31);
-            carry = lf ? lv : kmin(carry, lv);
-            open += tot;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, pre, d);
+            if (lane >= d) pre += y;
         }
-        if (lane == 0 && open >= 0 && open <= m - 2) emit_atomic(H, open, carry);
+        pre -= nbits;
+        int32_t vals[32];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            const int4 q4 = tile[swz(8 * lane + x)];
+            vals[4 * x] = q4.x; vals[4 * x + 1] = q4.y; vals[4 * x + 2] = q4.z; vals[4 * x + 3] = q4.w;
+        }
+        __syncwarp();  // the tile is read; its memory now holds the slots
+        // running minimum of the open segment as (value, cell); cells are met in
+        // increasing order, so a strict comparison keeps the leftmost
+        const uint32_t cell0 = (uint32_t)(ts + 32 * lane);
+        int32_t cv = vals[0];
+        uint32_t cp = cell0;
+        uint32_t k = pre;
+        if (word & 1u) { slot[k++] = make_key(cv, cp); }
+#pragma unroll
+        for (int c = 1; c < 32; ++c) {
+            const int32_t vv = vals[c];
+            if (word & (1u << c)) {
+                // boundary cell: last cell of the open segment, first of the next
+                const bool keep = cv <= vv;
+                slot[k++] = make_key(keep ? cv : vv, keep ? cp : cell0 + c);
+                cv = vv;
+                cp = cell0 + c;
+            } else if (vv < cv) {
+                cv = vv;
+                cp = cell0 + c;
+            }
+        }
+        bool f = nbits != 0;
+        uint64_t val = make_key(cv, cp);
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const bool of = __shfl_up_sync(0xffffffffu, f, d);
+            const uint64_t ov = __shfl_up_sync(0xffffffffu, val, d);
+            if (lane >= d) {
+                if (!f) val = kmin(val, ov);
+                f = f || of;
+            }
+        }
+        uint64_t carry_in = __shfl_up_sync(0xffffffffu, val, 1);
+        if (lane == 0) carry_in = KEY_MAX;
+        if (nbits) slot[pre] = kmin(slot[pre], carry_in);
+        const uint64_t tail = __shfl_sync(0xffffffffu, val, 31);
+        __syncwarp();
+        for (int b = lane; b < cnt; b += 32) {
+            const int64_t sg = s_t + b;
+            if (sg < 0 || sg > m - 2) continue;
+            if (b == 0) emit_atomic(H, sg, slot[0]);
+            else H[sg] = slot[b];
+        }
+        if (lane == 0 && s_n >= 0 && s_n <= m - 2) emit_atomic(H, s_n, tail);
     }
 }
 
-// ------------------------------------------------------ contracted queries
-// Query i covers A_Q[a .. b-1] with a = rank(l_i), b = rank(r_i); a == b
-// means l_i == r_i.  The answer is the position inside the minimum key.
-template <bool VECQ>
-__global__ void __launch_bounds__(kT) k_query_con(SrcU64 src, Len lenq, int logk, const uint64_t *__restrict__ T,
-                                                  const int32_t *__restrict__ L, const int32_t *__restrict__ R,
-                                                  const int32_t *__restrict__ RL, const int32_t *__restrict__ RR,
-                                                  int64_t n, int32_t *__restrict__ out, int64_t q) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t mq = lenq.get();
-    const int64_t nb = (mq + (1ll << logk) - 1) >> logk;
-    for (int64_t wb = warp * 128; wb < q; wb += nwarps * 128) {
-        const int64_t base = wb + lane * 4;
-        int32_t lq[4], rq[4], aq[4], bq[4];
-        bool present[4];
-        if (VECQ && base + 3 < q) {
-            const int4 x0 = __ldcs(reinterpret_cast<const int4 *>(L + base));
-            const int4 x1 = __ldcs(reinterpret_cast<const int4 *>(R + base));
-            const int4 x2 = __ldcs(reinterpret_cast<const int4 *>(RL + base));
-            const int4 x3 = __ldcs(reinterpret_cast<const int4 *>(RR + base));
-            lq[0] = x0.x; lq[1] = x0.y; lq[2] = x0.z; lq[3] = x0.w;
-            rq[0] = x1.x; rq[1] = x1.y; rq[2] = x1.z; rq[3] = x1.w;
-            aq[0] = x2.x; aq[1] = x2.y; aq[2] = x2.z; aq[3] = x2.w;
-            bq[0] = x3.x; bq[1] = x3.y; bq[2] = x3.z; bq[3] = x3.w;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) present[i] = true;
-        } else {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                present[i] = base + i < q;
-                lq[i] = present[i] ? __ldcs(L + base + i) : 0;
-                rq[i] = present[i] ? __ldcs(R + base + i) : 0;
-                aq[i] = present[i] ? __ldcs(RL + base + i) : 0;
-                bq[i] = present[i] ? __ldcs(RR + base + i) : 0;
-            }
-        }
-        uint64_t best[4];
-        Pending pl[4], pr[4];
-        bool hl[4], hr[4], ok[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            ok[i] = present[i] && lq[i] >= 0 && rq[i] >= lq[i] && (int64_t)rq[i] < n;
-            hl[i] = hr[i] = false;
-            best[i] = KEY_MAX;
-            if (ok[i] && aq[i] < bq[i])
-                best[i] = resolve_query(T, nb, logk, aq[i], bq[i] - 1, (uint32_t)lq[i], (uint32_t)rq[i], pl[i], pr[i],
-                                        hl[i], hr[i]);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            warp_drain_scans<SrcU64, true>(src, mq, hl[i], pl[i], best[i]);
-            warp_drain_scans<SrcU64, true>(src, mq, hr[i], pr[i], best[i]);
-        }
-        int32_t o[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) o[i] = !ok[i] ? -1 : (aq[i] < bq[i] ? (int32_t)key_pos(best[i]) : lq[i]);
-        if (VECQ && base + 3 < q) {
-            __stcs(reinterpret_cast<int4 *>(out + base), make_int4(o[0], o[1], o[2], o[3]));
-        } else {
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (present[i]) out[base + i] = o[i];
-        }
-    }
-}
-
-int sort_passes(int64_t n) {
-    const int bits = n > 1 ? ilog2_host((uint64_t)(n - 1)) + 1 : 0;
-    return (bits + kRadixBits - 1) / kRadixBits;
-}
+int key_bits(int64_t n) { return n > 1 ? ilog2_host((uint64_t)(n - 1)) + 1 : 0; }
+int sort_passes(int64_t n) { return (key_bits(n) + kRadixBits - 1) / kRadixBits; }
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -545,13 +544,16 @@ cudaError_t sort_endpoints(const int32_t *l, const int32_t *r, int64_t q, int64_
     note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    const int bits = key_bits(n);
+    const int width = P ? (bits + P - 1) / P : 0;      // equal digit widths, at most kRadixBits
     for (int p = 0; p < P; ++p) {
         const bool to_out = ((P - 1 - p) & 1) == 0;
         uint32_t *ok = to_out ? pos_out : tk, *ov = to_out ? tag_out : tv;
-        const int shift = p * kRadixBits;
-        k_rs_upsweep<<<(unsigned)ntiles, kT, 0, s>>>(pk, cnt, shift, hist, ntiles);
+        const int shift = p * width;
+        const uint32_t mask = (1u << width) - 1u;
+        k_rs_upsweep<<<(unsigned)ntiles, kT, 0, s>>>(pk, cnt, shift, mask, hist, ntiles);
         if ((e = scan_exclusive(hist, hist, nhist, aux, nullptr, s)) != cudaSuccess) return e;
-        k_rs_downsweep<<<(unsigned)ntiles, kT, 0, s>>>(pk, pv, cnt, shift, hist, ntiles, ok, ov);
+        k_rs_downsweep<<<(unsigned)ntiles, kT, 0, s>>>(pk, pv, cnt, shift, width, hist, ntiles, ok, ov);
         note_launches(2);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         pk = ok;
@@ -591,12 +593,18 @@ cudaError_t contract(const int32_t *A, int64_t n, const uint32_t *P, const int64
     k_con_prep<<<(unsigned)pctas, kT, 0, s>>>(P, m_dev, ntA, so, AQ);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(ntA, kT / 32), (int64_t)di.sms * 8));
+    const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(ntA, kT / 32), (int64_t)di.sms * 3));
     SrcI32 src{A};
+    static bool attr[64] = {false};
+    if (di.device >= 0 && di.device < 64 && !attr[di.device]) {
+        cudaFuncSetAttribute(k_contract<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kContractSmem);
+        cudaFuncSetAttribute(k_contract<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kContractSmem);
+        attr[di.device] = true;
+    }
     if ((reinterpret_cast<uintptr_t>(A) & 15) == 0)
-        k_contract<true><<<(unsigned)ctas, kT, 0, s>>>(src, n, P, m_dev, so, ntA, AQ);
+        k_contract<true><<<(unsigned)ctas, kT, kContractSmem, s>>>(src, n, P, m_dev, so, ntA, AQ);
     else
-        k_contract<false><<<(unsigned)ctas, kT, 0, s>>>(src, n, P, m_dev, so, ntA, AQ);
+        k_contract<false><<<(unsigned)ctas, kT, kContractSmem, s>>>(src, n, P, m_dev, so, ntA, AQ);
     note_launches(2);
     return cudaGetLastError();
 }
@@ -605,7 +613,7 @@ size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con) {
     const int64_t cnt = 2 * q;
     const int64_t mq_max = std::max<int64_t>(cnt - 1, 1);
     const int64_t nbq = cdiv(mq_max, 1ll << logk_con);
-    const int64_t lv = ilog2_host((uint64_t)nbq) + 1;
+    const int64_t lv = coarse_geom(nbq).lc + 1;
     size_t b = 0;
     b += align256(cnt * 4) * 2;                       // sorted endpoints
     b += align256(cnt * 4);                           // P
@@ -613,6 +621,8 @@ size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con) {
     b += align256(q * 4) * 2;                         // ranks
     b += align256(mq_max * 8);                        // A_Q
     b += align256(nbq * lv * 8);                      // table over A_Q
+    b += align256(kCoarseCap * 8);                    // its coarse summary
+    b += align256(query_residual_bytes(q, dev_info().sms));  // residual list of the query
     b += std::max({sort_workspace_bytes(q), rank_workspace_bytes(q), contract_workspace_bytes(n)});
     return b;
 }
@@ -622,7 +632,7 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     const int64_t cnt = 2 * q;
     const int64_t mq_max = std::max<int64_t>(cnt - 1, 1);
     const int64_t nbq = cdiv(mq_max, 1ll << logk_con);
-    const int64_t lv = ilog2_host((uint64_t)nbq) + 1;
+    const int64_t lv = coarse_geom(nbq).lc + 1;
     Carver c{static_cast<char *>(ws)};
     uint32_t *sk = c.take<uint32_t>(cnt), *sv = c.take<uint32_t>(cnt);
     uint32_t *P = c.take<uint32_t>(cnt);
@@ -630,6 +640,8 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     int32_t *ra = c.take<int32_t>(q), *rb = c.take<int32_t>(q);
     uint64_t *AQ = c.take<uint64_t>(mq_max);
     uint64_t *T = c.take<uint64_t>(nbq * lv);
+    uint64_t *Cs = c.take<uint64_t>(kCoarseCap);
+    char *resw = c.take<char>(query_residual_bytes(q, dev_info().sms));
     void *scratch = c.p + c.used;
     cudaError_t e;
     Stages none;
@@ -643,15 +655,18 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     st->mark(s);
     const Len lenq{0, m_dev};
     if ((e = launch_block_minima_u64(AQ, lenq, mq_max, logk_con, T, s)) != cudaSuccess) return e;         // step 3
-    if ((e = launch_sparse_table(T, lenq, logk_con, nbq, s)) != cudaSuccess) return e;                    // step 3
+    if ((e = launch_sparse_table(T, lenq, logk_con, nbq, s, Cs)) != cudaSuccess) return e;                // step 3
     st->mark(s);
     const DevInfo di = dev_info();
-    const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(q, 128 * (kT / 32)), (int64_t)di.sms * 8));
     const bool vecq = ((reinterpret_cast<uintptr_t>(l) | reinterpret_cast<uintptr_t>(r) |
                         reinterpret_cast<uintptr_t>(out)) & 15) == 0;
     SrcU64 src{AQ};
-    if (vecq) k_query_con<true><<<(unsigned)ctas, kT, 0, s>>>(src, lenq, logk_con, T, l, r, ra, rb, n, out, q);  // step 4
-    else k_query_con<false><<<(unsigned)ctas, kT, 0, s>>>(src, lenq, logk_con, T, l, r, ra, rb, n, out, q);
+    const ResidualPlan rp = residual_plan(q, di.sms);                                                    // step 4
+    Residual *res = reinterpret_cast<Residual *>(resw);
+    if (vecq)
+        k_query_two<SrcU64, true, true, true><<<(unsigned)rp.ctas, kT, 0, s>>>(src, lenq, logk_con, T, Cs, l, r, ra, rb, n, out, q, res, rp.region, nullptr);
+    else
+        k_query_two<SrcU64, true, false, true><<<(unsigned)rp.ctas, kT, 0, s>>>(src, lenq, logk_con, T, Cs, l, r, ra, rb, n, out, q, res, rp.region, nullptr);
     note_launches(1);
     e = cudaGetLastError();
     st->mark(s);

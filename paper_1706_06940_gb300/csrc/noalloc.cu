@@ -10,10 +10,11 @@ namespace rmq {
 
 namespace {
 
-// The fixed table buffer: RMQ_NOALLOC_TABLE_ENTRIES packed keys (4 MiB).  It
-// exists on every GPU on which the library is loaded, for the life of the
-// process, and all calls on a device share it.
-static __device__ __align__(256) unsigned long long g_noalloc_table[RMQ_NOALLOC_TABLE_ENTRIES];
+// The fixed buffer: RMQ_NOALLOC_TABLE_ENTRIES packed keys for the table (4 MiB)
+// followed by the table's coarse summary (kCoarseCap keys, 32 KiB).  It exists
+// on every GPU on which the library is loaded, for the life of the process,
+// and all calls on a device share it.
+static __device__ __align__(256) unsigned long long g_noalloc_table[RMQ_NOALLOC_TABLE_ENTRIES + kCoarseCap];
 
 constexpr int kMaxDev = 64;
 std::mutex g_noalloc_mu;
@@ -78,8 +79,9 @@ extern "C" rmq_status rmq_batch_noalloc(const int32_t *A, int64_t n, const int32
     // Every table entry the queries read is written by these launches first,
     // so the buffer needs no clearing between calls.
     if (launch_block_minima_i32(A, n, logk, T, s) != cudaSuccess) return RMQ_ERR_CUDA;
-    if (launch_sparse_table(T, Len{n, nullptr}, logk, nb, s) != cudaSuccess) return RMQ_ERR_CUDA;
-    if (launch_query_plain(A, n, logk, T, nb, l, r, q, out, s) != cudaSuccess) return RMQ_ERR_CUDA;
+    uint64_t *Cs = T + RMQ_NOALLOC_TABLE_ENTRIES;
+    if (launch_sparse_table(T, Len{n, nullptr}, logk, nb, s, Cs) != cudaSuccess) return RMQ_ERR_CUDA;
+    if (launch_query_plain(A, n, logk, T, Cs, nb, l, r, q, out, nullptr, s) != cudaSuccess) return RMQ_ERR_CUDA;
     return RMQ_OK;
 }
 #pragma GCC visibility pop

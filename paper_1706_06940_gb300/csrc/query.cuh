@@ -14,14 +14,16 @@ struct Pending {
     uint32_t lb = 0;
 };
 
-// Step 4 for one valid query, before any scan.  [lo, hi] is the query in the
-// source's index space; [la, ra] are its ends in A's positions (equal to
-// [lo, hi] for the plain form; for A_Q, entry j covers A[P_j .. P_{j+1}], so a
-// key whose position lies in [la, ra] is always attained inside the range).
+// Step 4 on the block table for one valid (sub)query, before any scan.
+// [lo, hi] is the range in the source's index space; [la, ra] bound its ends
+// in A's positions (equal to [lo, hi] for the plain form; for A_Q, entry j
+// covers A[P_j .. P_{j+1}], so a key whose position lies in [la, ra] is always
+// attained inside the range; a caller passes la = 0 or ra = UINT32_MAX for an
+// end that is a whole block inside the query).
 //
 //   * blocks bl = lo/k, br = hi/k;
 //   * m' = min over the blocks strictly between them, from two overlapping
-//     table lookups at level t = floor(log2(br - bl - 1)) (Sec. 3.1 step 4);
+//     table lookups at level t = floor(log2(br - bl - 1));
 //   * speculative reads of the two end-block minima: an end block is only
 //     looked at when its minimum beats m'.  If that minimum's position lies
 //     inside the query it is the end part's minimum and no scan is needed
@@ -33,9 +35,9 @@ __device__ __forceinline__ uint64_t resolve_query(const uint64_t *__restrict__ T
                                                   int64_t lo, int64_t hi, uint32_t la, uint32_t ra,
                                                   Pending &pl, Pending &pr, bool &hl, bool &hr) {
     const int64_t bl = lo >> logk, br = hi >> logk;
-    hl = hr = false;
+    const unsigned long long *Tu = reinterpret_cast<const unsigned long long *>(T);
     if (bl == br) {
-        const uint64_t t0 = __ldg(reinterpret_cast<const unsigned long long *>(T) + bl);
+        const uint64_t t0 = __ldg(Tu + bl);
         const uint32_t p = key_pos(t0);
         if (p >= la && p <= ra) return t0;
         pl.lo = lo; pl.hi = hi; pl.lb = key_hi(t0);
@@ -43,7 +45,6 @@ __device__ __forceinline__ uint64_t resolve_query(const uint64_t *__restrict__ T
         return KEY_MAX;
     }
     uint64_t best = KEY_MAX;
-    const unsigned long long *Tu = reinterpret_cast<const unsigned long long *>(T);
     const uint64_t tl = __ldg(Tu + bl);
     const uint64_t tr = __ldg(Tu + br);
     if (br - bl >= 2) {
@@ -58,6 +59,45 @@ __device__ __forceinline__ uint64_t resolve_query(const uint64_t *__restrict__ T
     if (tr < best) {
         if (key_pos(tr) <= ra) best = tr;
         else { pr.lo = br << logk; pr.hi = hi; pr.lb = key_hi(tr); hr = true; }
+    }
+    return best;
+}
+
+// The same step one level up, on the coarse summary in shared memory (coarse
+// blocks of 2^lc blocks).  Returns the best key found so far and which parts
+// still need the block table: the whole range (when it lies in one coarse
+// block whose minimum is outside it), or the part in the left / right end
+// coarse block (when that block's minimum beats the inner coarse span but
+// lies outside the query).
+enum : int { SUB_NONE = 0, SUB_WHOLE = 1, SUB_LEFT = 2, SUB_RIGHT = 4 };
+
+__device__ __forceinline__ uint64_t resolve_coarse(const uint64_t *cs, const Coarse &g, int logk, uint32_t lo,
+                                                   uint32_t hi, uint32_t la, uint32_t ra, int &sub) {
+    // all indices fit in 32 bits: positions < 2^31, coarse blocks < kCoarseCap
+    const int sh = logk + g.lc;
+    const uint32_t BL = lo >> sh, BR = hi >> sh;
+    if (BL == BR) {
+        const uint64_t c0 = cs[BL];
+        const uint32_t p = key_pos(c0);
+        if (p >= la && p <= ra) { sub = SUB_NONE; return c0; }
+        sub = SUB_WHOLE;
+        return KEY_MAX;
+    }
+    sub = SUB_NONE;
+    uint64_t best = KEY_MAX;
+    if (BR - BL >= 2) {
+        const int t = 31 - __clz((int)(BR - BL - 1));
+        const uint64_t *row = cs + (uint32_t)t * (uint32_t)g.nbc;
+        best = kmin(row[BL + 1], row[BR - (1u << t)]);
+    }
+    const uint64_t cl = cs[BL], cr = cs[BR];
+    if (cl < best) {
+        if (key_pos(cl) >= la) best = cl;
+        else sub |= SUB_LEFT;
+    }
+    if (cr < best) {
+        if (key_pos(cr) <= ra) best = cr;
+        else sub |= SUB_RIGHT;
     }
     return best;
 }
@@ -114,6 +154,325 @@ __device__ __forceinline__ void warp_drain_scans(const Src &src, int64_t n, bool
         const uint32_t lb = __shfl_sync(0xffffffffu, p.lb, s);
         const uint64_t v = warp_scan_min<Src, VEC>(src, n, lo, hi, lb);
         if (lane == s) best = kmin(best, v);
+    }
+}
+
+// Copy the coarse table into shared memory: every thread issues all its loads
+// before any store, so the copy costs one round trip to L2.
+__device__ __forceinline__ void load_coarse(uint64_t *cs, const uint64_t *__restrict__ Cs, int total) {
+    constexpr int PER = kCoarseCap / 256;
+    uint64_t tmp[PER];
+#pragma unroll
+    for (int x = 0; x < PER; ++x) {
+        const int i = threadIdx.x + x * 256;
+        tmp[x] = i < total ? __ldg(reinterpret_cast<const unsigned long long *>(Cs) + i) : 0ull;
+    }
+#pragma unroll
+    for (int x = 0; x < PER; ++x) {
+        const int i = threadIdx.x + x * 256;
+        if (i < total) cs[i] = tmp[x];
+    }
+}
+
+// Query kernel, both forms.  Each CTA first copies the coarse summary into
+// shared memory; then every thread takes 4 queries at a time (16-byte loads
+// of l and r when aligned): coarse resolution from shared memory, block-table
+// lookups only for the parts the coarse level leaves open, and finally the
+// warp-cooperative partial-block scans.
+//   plain (CON = false): the source is A; query i covers [l_i, r_i].
+//   contracted (CON = true): the source is A_Q; query i covers
+//     A_Q[a_i .. b_i - 1] with a_i = RL[i], b_i = RR[i]; a_i == b_i means
+//     l_i == r_i and the answer is l_i.
+template <class Src, bool CON, bool VECQ, bool VEC>
+__global__ void __launch_bounds__(256) k_query(Src src, Len len, int logk, const uint64_t *__restrict__ T,
+                                                const uint64_t *__restrict__ Cs, const int32_t *__restrict__ L,
+                                                const int32_t *__restrict__ R, const int32_t *__restrict__ RL,
+                                                const int32_t *__restrict__ RR, int64_t n_a,
+                                                int32_t *__restrict__ out, int64_t q, unsigned *err) {
+    __shared__ uint64_t cs[kCoarseCap];
+    const int64_t n = len.get();
+    const int64_t nb = (n + (1ll << logk) - 1) >> logk;
+    const Coarse g = coarse_geom(nb);
+    load_coarse(cs, Cs, (int)(g.nbc * g.lvc));
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t wb = warp * 128; wb < q; wb += nwarps * 128) {
+        const int64_t base = wb + lane * 4;
+        const bool full = VECQ && base + 3 < q;
+        int32_t lq[4], rq[4], aq[4], bq[4];
+        bool present[4];
+        if (full) {
+            const int4 x0 = __ldcs(reinterpret_cast<const int4 *>(L + base));
+            const int4 x1 = __ldcs(reinterpret_cast<const int4 *>(R + base));
+            lq[0] = x0.x; lq[1] = x0.y; lq[2] = x0.z; lq[3] = x0.w;
+            rq[0] = x1.x; rq[1] = x1.y; rq[2] = x1.z; rq[3] = x1.w;
+            if (CON) {
+                const int4 x2 = __ldcs(reinterpret_cast<const int4 *>(RL + base));
+                const int4 x3 = __ldcs(reinterpret_cast<const int4 *>(RR + base));
+                aq[0] = x2.x; aq[1] = x2.y; aq[2] = x2.z; aq[3] = x2.w;
+                bq[0] = x3.x; bq[1] = x3.y; bq[2] = x3.z; bq[3] = x3.w;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) present[i] = true;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                present[i] = base + i < q;
+                lq[i] = present[i] ? __ldcs(L + base + i) : 0;
+                rq[i] = present[i] ? __ldcs(R + base + i) : 0;
+                if (CON) {
+                    aq[i] = present[i] ? __ldcs(RL + base + i) : 0;
+                    bq[i] = present[i] ? __ldcs(RR + base + i) : 0;
+                }
+            }
+        }
+        uint64_t best[4];
+        Pending pl[4], pr[4];
+        bool hl[4], hr[4], ok[4];
+        bool bad = false;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            ok[i] = present[i] && lq[i] >= 0 && rq[i] >= lq[i] && (int64_t)rq[i] < n_a;
+            bad |= present[i] && !ok[i];
+            hl[i] = hr[i] = false;
+            best[i] = KEY_MAX;
+            const int64_t lo = CON ? aq[i] : lq[i];
+            const int64_t hi = CON ? (int64_t)bq[i] - 1 : rq[i];
+            if (!ok[i] || hi < lo) continue;
+            const uint32_t la = (uint32_t)lq[i], ra = (uint32_t)rq[i];
+            int sub;
+            best[i] = resolve_coarse(cs, g, logk, (uint32_t)lo, (uint32_t)hi, la, ra, sub);
+            if (sub == SUB_WHOLE) {
+                best[i] = resolve_query(T, nb, logk, lo, hi, la, ra, pl[i], pr[i], hl[i], hr[i]);
+            } else if (sub != SUB_NONE) {
+                Pending unused;
+                bool unused_flag = false;
+                const int sh = logk + g.lc;
+                if (sub & SUB_LEFT) {
+                    const int64_t end_l = (((lo >> sh) + 1) << sh) - 1;
+                    best[i] = kmin(best[i], resolve_query(T, nb, logk, lo, end_l, la, 0xffffffffu, pl[i], unused,
+                                                          hl[i], unused_flag));
+                }
+                if (sub & SUB_RIGHT) {
+                    // the right part's only possible scan is its right partial block,
+                    // recorded in the first slot when the part lies in one block
+                    const int64_t start_r = (hi >> sh) << sh;
+                    Pending a, b;
+                    bool ha = false, hb = false;
+                    best[i] = kmin(best[i], resolve_query(T, nb, logk, start_r, hi, 0u, ra, a, b, ha, hb));
+                    if (ha) { pr[i] = a; hr[i] = true; }
+                    if (hb) { pr[i] = b; hr[i] = true; }
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            warp_drain_scans<Src, VEC>(src, n, hl[i], pl[i], best[i]);
+            warp_drain_scans<Src, VEC>(src, n, hr[i], pr[i], best[i]);
+        }
+        int32_t o[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const bool single = CON && ok[i] && aq[i] >= bq[i];
+            o[i] = !ok[i] ? -1 : (single ? lq[i] : (int32_t)key_pos(best[i]));
+        }
+        if (full) {
+            __stcs(reinterpret_cast<int4 *>(out + base), make_int4(o[0], o[1], o[2], o[3]));
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (present[i]) out[base + i] = o[i];
+        }
+        if (!CON && bad && err) atomicOr(err, ERR_QUERY_RANGE);
+    }
+}
+
+// ---------------------------------------------------------------- two phases
+// The batch paths split the query kernel in two so that the common case runs
+// lean: phase A (k_query_coarse) answers every query the coarse summary
+// settles, from shared memory alone, and appends the others to a residual
+// list; phase B (k_query_fine) finishes the residual queries on the block
+// table and with partial-block scans.
+struct Residual {
+    uint32_t qid;
+    int32_t l, r;
+    uint32_t pad;
+};
+
+// Phase A's test: the minimum over every coarse block the query touches,
+// from two reads of the coarse table.  When its position lies inside the
+// query it is the answer; this settles most queries of a long batch.
+__device__ __forceinline__ bool coarse_span_min(const uint64_t *cs, const Coarse &g, int logk, uint32_t lo, uint32_t hi,
+                                                uint32_t la, uint32_t ra, uint64_t &m) {
+    const int sh = logk + g.lc;
+    const uint32_t BL = lo >> sh, BR = hi >> sh;
+    const int t = 31 - __clz((int)(BR - BL + 1));
+    const uint64_t *row = cs + (uint32_t)t * (uint32_t)g.nbc;
+    m = kmin(row[BL], row[BR + 1 - (1u << t)]);
+    const uint32_t p = key_pos(m);
+    return p >= la && p <= ra;
+}
+
+template <class Src, bool CON, bool VECQ, bool VEC>
+__global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk, const uint64_t *__restrict__ T,
+                                                    const uint64_t *__restrict__ Cs,
+                                                    const int32_t *__restrict__ L, const int32_t *__restrict__ R,
+                                                    const int32_t *__restrict__ RL, const int32_t *__restrict__ RR,
+                                                    int64_t n_a, int32_t *__restrict__ out, int64_t q,
+                                                    Residual *__restrict__ res, int64_t region, unsigned *err) {
+    // Phase A: each CTA answers the queries the coarse table settles and
+    // appends the others to its own region of `region` entries of the residual
+    // list (counted in shared memory, no global atomics).  Phase B: the same
+    // CTA then finishes its residual queries, with the coarse table still in
+    // shared memory.
+    __shared__ uint64_t cs[kCoarseCap];
+    __shared__ uint32_t n_open;
+    if (threadIdx.x == 0) n_open = 0;
+    Residual *my = res + (int64_t)blockIdx.x * region;
+    const int64_t n = len.get();
+    const int64_t nb = (n + (1ll << logk) - 1) >> logk;
+    const Coarse g = coarse_geom(nb);
+    load_coarse(cs, Cs, (int)(g.nbc * g.lvc));
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // the next step's l, r (and ranks) are loaded before the current step is
+    // processed, so every warp keeps a batch of loads in flight
+    const int64_t stride = nwarps * 128;
+    int4 p0 = make_int4(0, 0, 0, 0), p1 = p0, p2 = p0, p3 = p0;
+    auto fetch = [&](int64_t b) {
+        if (VECQ && b + 3 < q) {
+            p0 = __ldcs(reinterpret_cast<const int4 *>(L + b));
+            p1 = __ldcs(reinterpret_cast<const int4 *>(R + b));
+            if (CON) {
+                p2 = __ldcs(reinterpret_cast<const int4 *>(RL + b));
+                p3 = __ldcs(reinterpret_cast<const int4 *>(RR + b));
+            }
+        }
+    };
+    fetch(warp * 128 + lane * 4);
+    for (int64_t wb = warp * 128; wb < q; wb += stride) {
+        const int64_t base = wb + lane * 4;
+        const bool full = VECQ && base + 3 < q;
+        int32_t lq[4], rq[4], aq[4], bq[4];
+        if (full) {
+            lq[0] = p0.x; lq[1] = p0.y; lq[2] = p0.z; lq[3] = p0.w;
+            rq[0] = p1.x; rq[1] = p1.y; rq[2] = p1.z; rq[3] = p1.w;
+            if (CON) {
+                aq[0] = p2.x; aq[1] = p2.y; aq[2] = p2.z; aq[3] = p2.w;
+                bq[0] = p3.x; bq[1] = p3.y; bq[2] = p3.z; bq[3] = p3.w;
+            }
+        }
+        fetch(base + stride);
+        if (!full) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const bool p = base + i < q;
+                lq[i] = p ? __ldcs(L + base + i) : 0;
+                rq[i] = p ? __ldcs(R + base + i) : -1;   // absent: reads as invalid
+                if (CON) {
+                    aq[i] = p ? __ldcs(RL + base + i) : 0;
+                    bq[i] = p ? __ldcs(RR + base + i) : 0;
+                }
+            }
+        }
+        int32_t o[4];
+        uint64_t rb[4];
+        unsigned need = 0;
+        bool bad = false;
+        const int32_t na = (int32_t)n_a;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const bool present = base + i < q;
+            const bool ok = lq[i] >= 0 && rq[i] >= lq[i] && rq[i] < na;
+            bad |= present && !ok;
+            o[i] = -1;
+            rb[i] = KEY_MAX;
+            if (!ok) continue;
+            if (CON && aq[i] >= bq[i]) { o[i] = lq[i]; continue; }   // contracted l == r
+            const uint32_t lo = (uint32_t)(CON ? aq[i] : lq[i]);
+            const uint32_t hi = (uint32_t)(CON ? bq[i] - 1 : rq[i]);
+            if (coarse_span_min(cs, g, logk, lo, hi, (uint32_t)lq[i], (uint32_t)rq[i], rb[i])) o[i] = (int32_t)key_pos(rb[i]);
+            else need |= 1u << i;
+        }
+        if (full) {
+            __stcs(reinterpret_cast<int4 *>(out + base), make_int4(o[0], o[1], o[2], o[3]));
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (base + i < q) out[base + i] = o[i];
+        }
+        // append the open queries to the residual list, one atomic per warp
+        const unsigned c = __popc(need);
+        unsigned pre = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, pre, d);
+            if (lane >= d) pre += y;
+        }
+        const unsigned tot = __shfl_sync(0xffffffffu, pre, 31);
+        if (tot) {
+            uint32_t slot = 0;
+            if (lane == 31) slot = atomicAdd(&n_open, tot);
+            slot = __shfl_sync(0xffffffffu, slot, 31) + (pre - c);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (need & (1u << i)) {
+                    Residual e;
+                    e.qid = (uint32_t)(base + i);
+                    e.l = lq[i];
+                    e.r = rq[i];
+                    e.pad = 0;
+                    my[slot++] = e;
+                }
+        }
+        if (!CON && bad && err) atomicOr(err, ERR_QUERY_RANGE);
+    }
+    __syncthreads();  // n_open is final and the region's entries are visible to the CTA
+    const int64_t cnt = n_open;
+    const int sh = logk + g.lc;
+    for (int64_t wb = (threadIdx.x >> 5) * 32; wb < cnt; wb += (blockDim.x >> 5) * 32) {
+        const int64_t idx = wb + lane;
+        const bool has = idx < cnt;
+        Pending pl, pr;
+        bool hl = false, hr = false;
+        uint64_t best = KEY_MAX;
+        uint32_t qid = 0;
+        if (has) {
+            const Residual e = my[idx];
+            qid = e.qid;
+            const int32_t l = e.l, r = e.r;
+            const int64_t lo = CON ? RL[qid] : l;
+            const int64_t hi = CON ? (int64_t)RR[qid] - 1 : r;
+            int sub;
+            best = resolve_coarse(cs, g, logk, (uint32_t)lo, (uint32_t)hi, (uint32_t)l, (uint32_t)r, sub);
+            if (sub == SUB_WHOLE) {
+                best = resolve_query(T, nb, logk, lo, hi, (uint32_t)l, (uint32_t)r, pl, pr, hl, hr);
+            } else if (sub != SUB_NONE) {
+                Pending unused;
+                bool unused_flag = false;
+                if (sub & SUB_LEFT) {
+                    const int64_t end_l = (((lo >> sh) + 1) << sh) - 1;
+                    best = kmin(best, resolve_query(T, nb, logk, lo, end_l, (uint32_t)l, 0xffffffffu, pl, unused, hl,
+                                                    unused_flag));
+                }
+                if (sub & SUB_RIGHT) {
+                    // a part inside one block records its scan in the first slot
+                    const int64_t start_r = (hi >> sh) << sh;
+                    Pending a, b;
+                    bool ha = false, hb = false;
+                    best = kmin(best, resolve_query(T, nb, logk, start_r, hi, 0u, (uint32_t)r, a, b, ha, hb));
+                    if (ha) { pr = a; hr = true; }
+                    if (hb) { pr = b; hr = true; }
+                }
+            }
+        }
+        warp_drain_scans<Src, VEC>(src, n, hl, pl, best);
+        warp_drain_scans<Src, VEC>(src, n, hr, pr, best);
+        if (has) out[qid] = (int32_t)key_pos(best);
     }
 }
 

@@ -33,6 +33,40 @@ __device__ __forceinline__ uint64_t warp_min(uint64_t v) {
 
 __device__ __forceinline__ int ilog2_dev(uint64_t x) { return 63 - __clzll((long long)x); }
 
+__host__ __device__ __forceinline__ int ilog2_hd(uint64_t x) {
+#ifdef __CUDA_ARCH__
+    return 63 - __clzll((long long)x);
+#else
+    return 63 - __builtin_clzll(x);
+#endif
+}
+
+// Coarse summary of a block sparse table (the two-level scheme of Sec. 3.3
+// applied to the memory hierarchy): coarse blocks are 2^lc consecutive
+// blocks, and the summary holds levels lc .. lc + lvc - 1 of the table at the
+// coarse block starts, i.e. a sparse table over nbc coarse blocks, small
+// enough (<= kCoarseCap entries) to live in shared memory while queries run.
+// lc is the smallest shift for which it fits.
+constexpr int kCoarseCap = 4096;
+struct Coarse {
+    int lc;            // log2 of blocks per coarse block
+    int lvc;           // levels of the coarse table
+    int64_t nbc;       // coarse blocks (the last may be partial)
+    int64_t nbc_full;  // coarse blocks made of 2^lc whole blocks
+};
+__host__ __device__ __forceinline__ Coarse coarse_geom(int64_t nb) {
+    Coarse g{0, 1, nb, nb};
+    if (nb < 1) { g.nbc = g.nbc_full = 0; return g; }
+    for (int lc = 0;; ++lc) {
+        const int64_t nbc = (nb + (1ll << lc) - 1) >> lc;
+        const int lvc = ilog2_hd((uint64_t)nbc) + 1;
+        if (nbc * lvc <= kCoarseCap) {
+            g.lc = lc; g.lvc = lvc; g.nbc = nbc; g.nbc_full = nb >> lc;
+            return g;
+        }
+    }
+}
+
 // Streaming 128-bit load that does not allocate in L1 (data read once).
 __device__ __forceinline__ int4 ld_stream_v4(const int4 *p) {
     int4 v;
@@ -131,9 +165,38 @@ cudaError_t launch_block_minima_u64(const uint64_t *AQ, Len len, int64_t n_max, 
                                     cudaStream_t s);
 // The table's block count is nb = ceil(len / 2^logk), read on the device from
 // `len`; nb_max bounds it on the host and sizes the launches.
-cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, cudaStream_t s);
-cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint64_t *T, int64_t nb,
-                               const int32_t *l, const int32_t *r, int64_t q, int32_t *out, cudaStream_t s);
+// Cs == nullptr: every level 1 .. floor(log2 nb) of the block table.
+// Cs != nullptr: the two-level layout -- levels 1 .. lc of the block table and
+//   the coarse table (kCoarseCap entries) in Cs.
+cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, cudaStream_t s,
+                                uint64_t *Cs = nullptr);
+// Entries of the two-level block table (levels 0 .. lc) for nb blocks.
+inline int64_t two_level_entries(int64_t nb) { return nb < 1 ? 0 : nb * (coarse_geom(nb).lc + 1); }
+// Two-phase query: kQueryCtasPerSm CTAs per SM; each CTA owns a region of the
+// residual list sized for every query it can see.
+// With res_ws == nullptr the query runs as one fused kernel that needs no scratch.
+constexpr int kQueryCtasPerSm = 4;    // resident CTAs per SM (32 KB shared memory, <= 64 registers)
+struct ResidualPlan {
+    int64_t ctas;    // phase-A CTAs
+    int64_t region;  // entries per CTA region
+};
+inline ResidualPlan residual_plan(int64_t q, int sms) {
+    const int64_t batches = (q + 127) / 128;                     // 4 queries x 32 lanes per warp step
+    int64_t ctas = (batches + 7) / 8;
+    const int64_t cap = (int64_t)sms * kQueryCtasPerSm;          // one wave: every CTA resident at once
+    if (ctas > cap) ctas = cap;
+    if (ctas < 1) ctas = 1;
+    const int64_t warps = ctas * 8;
+    const int64_t per_warp = (batches + warps - 1) / warps;       // warp steps per warp
+    return ResidualPlan{ctas, per_warp * 8 * 128};
+}
+inline size_t query_residual_bytes(int64_t q, int sms) {
+    const ResidualPlan p = residual_plan(q, sms);
+    return (size_t)(p.ctas * p.region) * 16;
+}
+cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint64_t *T, const uint64_t *Cs,
+                               int64_t nb, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
+                               void *res_ws, cudaStream_t s);
 
 // Contracted form (contract.cu).
 size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con);

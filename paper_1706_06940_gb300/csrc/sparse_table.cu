@@ -21,11 +21,12 @@ constexpr int kThreads = 256;
 // ping-pong buffers and writes every level's rows < S.  Round 0 uses R = 1
 // (contiguous tiles); later rounds start at b >= 5, so R = 32 divides 2^b.
 template <int R, int LV>
-__global__ void __launch_bounds__(kThreads) k_st_round(uint64_t *__restrict__ T, Len len, int logk, int b, int S) {
+__global__ void __launch_bounds__(kThreads) k_st_round(uint64_t *__restrict__ T, Len len, int logk, int b, int S,
+                                                      bool two_level) {
     const int64_t n = len.get();
     const int64_t nb = (n + (1ll << logk) - 1) >> logk;
     if (nb < 2) return;
-    const int top = ilog2_dev((uint64_t)nb);
+    const int top = two_level ? coarse_geom(nb).lc : ilog2_dev((uint64_t)nb);
     if (b >= top) return;
     const int nlev = min(LV, top - b);
     const int rows = S + (1 << nlev);
@@ -62,14 +63,49 @@ __global__ void __launch_bounds__(kThreads) k_st_round(uint64_t *__restrict__ T,
     }
 }
 
+// Coarse table of the two-level layout: level 0 holds the minima of the
+// coarse blocks (level lc of the block table at the coarse block starts; the
+// last, partial coarse block from two overlapping lookups of lower levels),
+// and the levels above come by doubling over the coarse blocks -- all in one
+// CTA's shared memory, since the coarse table has at most kCoarseCap entries.
+__global__ void __launch_bounds__(1024) k_coarse_table(const uint64_t *__restrict__ T, Len len, int logk,
+                                                       uint64_t *__restrict__ Cs) {
+    __shared__ uint64_t c[kCoarseCap];
+    const int64_t n = len.get();
+    const int64_t nb = (n + (1ll << logk) - 1) >> logk;
+    if (nb < 1) return;
+    const Coarse g = coarse_geom(nb);
+    for (int64_t J = threadIdx.x; J < g.nbc; J += blockDim.x) {
+        uint64_t v;
+        if (J < g.nbc_full) {
+            v = T[(int64_t)g.lc * nb + (J << g.lc)];
+        } else {
+            const int64_t s0 = J << g.lc;
+            const int tt = ilog2_dev((uint64_t)(nb - s0));
+            v = kmin(T[(int64_t)tt * nb + s0], T[(int64_t)tt * nb + nb - (1ll << tt)]);
+        }
+        c[J] = v;
+    }
+    __syncthreads();
+    for (int t = 1; t < g.lvc; ++t) {
+        const int64_t half = 1ll << (t - 1), cnt = g.nbc - (1ll << t) + 1;
+        uint64_t *cur = c + (int64_t)t * g.nbc;
+        const uint64_t *prev = c + (int64_t)(t - 1) * g.nbc;
+        for (int64_t J = threadIdx.x; J < cnt; J += blockDim.x) cur[J] = kmin(prev[J], prev[J + half]);
+        __syncthreads();
+    }
+    for (int64_t i = threadIdx.x; i < g.nbc * g.lvc; i += blockDim.x) Cs[i] = c[i];
+}
+
 constexpr int kLV0 = 12, kS0 = 256;   // round 0: levels 1..12, 256 outputs per CTA
 constexpr int kLV1 = 6, kS1 = 64;     // later rounds: 6 levels, 32 residues x 64 strides
 
 }  // namespace
 
-cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, cudaStream_t s) {
-    if (nb_max < 2) return cudaSuccess;
-    const int top = ilog2_host((uint64_t)nb_max);
+cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, cudaStream_t s, uint64_t *Cs) {
+    const bool two = Cs != nullptr;
+    if (nb_max < 1) return cudaSuccess;
+    const int top = two ? coarse_geom(nb_max).lc : (nb_max >= 2 ? ilog2_host((uint64_t)nb_max) : 0);
     static bool attr_done[64] = {false};
     const DevInfo di = dev_info();
     const size_t smem0 = 2ull * (kS0 + (1 << kLV0)) * 1 * sizeof(uint64_t);
@@ -81,8 +117,10 @@ cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, 
     }
     {
         const int64_t ctas = cdiv(nb_max, kS0);
-        k_st_round<1, kLV0><<<(unsigned)ctas, kThreads, smem0, s>>>(T, len, logk, 0, kS0);
-        note_launches(1);
+        if (top > 0) {
+            k_st_round<1, kLV0><<<(unsigned)ctas, kThreads, smem0, s>>>(T, len, logk, 0, kS0, two);
+            note_launches(1);
+        }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -91,10 +129,15 @@ cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, 
         const int64_t ngroups = stride / 32;
         const int64_t nstr = cdiv(nb_max, stride);
         const int64_t ctas = ngroups * cdiv(nstr, kS1);
-        k_st_round<32, kLV1><<<(unsigned)ctas, kThreads, smem1, s>>>(T, len, logk, b, kS1);
+        k_st_round<32, kLV1><<<(unsigned)ctas, kThreads, smem1, s>>>(T, len, logk, b, kS1, two);
         note_launches(1);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+    }
+    if (two) {
+        k_coarse_table<<<1, 1024, 0, s>>>(T, len, logk, Cs);
+        note_launches(1);
+        return cudaGetLastError();
     }
     return cudaSuccess;
 }
