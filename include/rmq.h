@@ -74,13 +74,26 @@ typedef enum {
     RMQ_VARIANT_CONTRACTED = 2   /* BbST_CON (Sec. 3.1) */
 } rmq_variant;
 
+/* rmq_opts.flags bits. */
+#define RMQ_FLAG_TEST_WITHHOLD_READY 1u  /* rmq_batch_multi test hook: array 0's table is never
+                                            marked ready, so its queries time out (answers -1,
+                                            RMQ_ERR_TIMEOUT) after a short bounded wait */
+
 /* Options; a NULL rmq_opts* means all defaults (zeros). */
 typedef struct {
     int32_t variant;   /* rmq_variant */
     int32_t k;         /* block size over A (plain form): 0 = tuned, else a power of 2 in [32, 65536] */
     int32_t k_con;     /* block size over A_Q (contracted form): 0 = tuned, else a power of 2 in [32, 65536] */
-    int32_t flags;     /* reserved, must be 0 */
+    int32_t flags;     /* 0, or RMQ_FLAG_* bits where an entry point allows them */
 } rmq_opts;
+
+/* One array of a multi-array batch: A is a device pointer to n int32 cells;
+ * the array's q queries are the next q entries of the batch's l, r, out. */
+typedef struct {
+    const int32_t *A;
+    int64_t n;
+    int64_t q;
+} rmq_array;
 
 /* Capacity of the fixed table buffer of rmq_batch_noalloc, in 8-byte entries
  * (4 MiB; the buffer also holds the table's 32 KiB coarse summary). */
@@ -142,6 +155,22 @@ rmq_status rmq_batch_host(const int32_t *A_host, int64_t n, const int32_t *l_hos
  * threads) race on the buffer and must be serialised by the caller. */
 rmq_status rmq_batch_noalloc(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r,
                              int64_t q, int32_t *out, int32_t k, void *stream);
+
+/* Many independent arrays, each with its own queries, answered in ONE
+ * persistent kernel launch (plain BbST per array, Sec. 3.2, with a coarse
+ * level as in Sec. 3.3): block minima, tables and answers for every array.
+ * arrays: host array of H descriptors (A device pointers, n >= 1 when q > 0,
+ * q >= 0).  The queries of array h are l/r/out entries [s_h, s_h + q_h) with
+ * s_h = q_0 + ... + q_{h-1}; their positions are relative to array h, and so
+ * are the answers.  Invalid queries answer -1 (RMQ_ERR_QUERY_RANGE via
+ * rmq_stream_status).  opts->k forces one block size for every array (0 =
+ * chosen per array); opts->variant is ignored; opts->flags may hold
+ * RMQ_FLAG_TEST_WITHHOLD_READY.  Workspace comes from the stream-ordered pool
+ * and the call only enqueues memsets and kernel launches, so it can be
+ * captured in a CUDA graph.  Arrays beyond 1024 are handled by further
+ * launches of the same kernel. */
+rmq_status rmq_batch_multi(const rmq_array *arrays, int32_t H, const int32_t *l, const int32_t *r,
+                           int32_t *out, const rmq_opts *opts, void *stream);
 
 /* -------------------------------------------------------- resident arrays */
 

@@ -258,6 +258,55 @@ rmq_status rmq_batch_host(const int32_t *A_host, int64_t n, const int32_t *l_hos
     return RMQ_OK;
 }
 
+rmq_status rmq_batch_multi(const rmq_array *arrays, int32_t H, const int32_t *l, const int32_t *r, int32_t *out,
+                           const rmq_opts *opts, void *stream) {
+    if (H < 0 || (H > 0 && !arrays)) return RMQ_ERR_INVALID_ARG;
+    uint32_t flags = 0;
+    int32_t kforce = 0;
+    if (opts) {
+        if (opts->flags & ~(int32_t)RMQ_FLAG_TEST_WITHHOLD_READY) return RMQ_ERR_INVALID_ARG;
+        if (opts->k != 0 && !pow2_in_range(opts->k)) return RMQ_ERR_INVALID_ARG;
+        flags = (uint32_t)opts->flags;
+        kforce = opts->k;
+    }
+    int64_t qtot = 0;
+    for (int32_t h = 0; h < H; ++h) {
+        const rmq_array &a = arrays[h];
+        if (a.q < 0 || a.q > kMaxQ || a.n < 0 || a.n > kMaxN) return RMQ_ERR_INVALID_ARG;
+        if (a.q > 0 && (a.n < 1 || !a.A)) return RMQ_ERR_INVALID_ARG;
+        qtot += a.q;
+    }
+    if (qtot > kMaxQ) return RMQ_ERR_INVALID_ARG;
+    if (qtot == 0) return RMQ_OK;
+    if (!l || !r || !out) return RMQ_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    int64_t qoff = 0;
+    for (int32_t g0 = 0; g0 < H; g0 += kMultiMax) {
+        const int cnt = (int)std::min<int64_t>(kMultiMax, H - g0);
+        const int32_t *Ap[kMultiMax];
+        int64_t nn[kMultiMax], qq[kMultiMax];
+        int32_t lk[kMultiMax];
+        int64_t gq = 0;
+        for (int i = 0; i < cnt; ++i) {
+            const rmq_array &a = arrays[g0 + i];
+            Ap[i] = a.A;
+            nn[i] = a.q > 0 ? a.n : 0;
+            qq[i] = a.q;
+            lk[i] = a.q > 0 ? (kforce ? ilog2_host((uint64_t)kforce) : multi_logk(a.n)) : MIN_LOGK;
+            gq += a.q;
+        }
+        if (gq > 0) {
+            Workspace ws;
+            rmq_status st = ws.alloc(multi_workspace_bytes(nn, qq, lk, cnt), s);
+            if (st != RMQ_OK) return st;
+            cudaError_t e = launch_multi(Ap, nn, qq, lk, cnt, l + qoff, r + qoff, out + qoff, flags, ws.p, s);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        qoff += gq;
+    }
+    return RMQ_OK;
+}
+
 rmq_status rmq_build(const int32_t *A, int64_t n, const rmq_opts *opts, void *stream, rmq_handle *out_handle) {
     if (!out_handle) return RMQ_ERR_INVALID_ARG;
     *out_handle = nullptr;

@@ -198,6 +198,13 @@ cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint
                                int64_t nb, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
                                void *res_ws, cudaStream_t s);
 
+// Many arrays in one persistent launch (multi.cu).
+constexpr int kMultiMax = 1024;   // arrays per launch (their descriptors travel as a kernel parameter)
+int multi_logk(int64_t n);
+size_t multi_workspace_bytes(const int64_t *n, const int64_t *q, const int32_t *logk, int H);
+cudaError_t launch_multi(const int32_t *const *A, const int64_t *n, const int64_t *q, const int32_t *logk, int H,
+                         const int32_t *l, const int32_t *r, int32_t *out, uint32_t flags, void *ws, cudaStream_t s);
+
 // Contracted form (contract.cu).
 size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con);
 cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q,

@@ -44,6 +44,13 @@ class RmqError(RuntimeError):
         super().__init__("%s: %s" % (self.status.name, strerror(self.status)))
 
 
+FLAG_TEST_WITHHOLD_READY = 1
+
+
+class rmq_array(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("n", ctypes.c_int64), ("q", ctypes.c_int64)]
+
+
 class rmq_opts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("k", ctypes.c_int32),
                 ("k_con", ctypes.c_int32), ("flags", ctypes.c_int32)]
@@ -59,6 +66,7 @@ _SIGS = {
                                ctypes.POINTER(_vp), _i32]),
     "rmq_launch_count": (_i64, []),
     "rmq_batch_noalloc": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, _i32, _vp]),
+    "rmq_batch_multi": (_i32, [ctypes.c_void_p, _i32, _vp, _vp, _vp, ctypes.POINTER(rmq_opts), _vp]),
     "rmq_batch_host": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, ctypes.POINTER(rmq_opts), _vp]),
     "rmq_build": (_i32, [_vp, _i64, ctypes.POINTER(rmq_opts), _vp, ctypes.POINTER(_vp)]),
     "rmq_query": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp]),
@@ -175,6 +183,20 @@ def rmq_batch_noalloc(A, l, r, out, k=0, stream=None):
     _check(load().rmq_batch_noalloc(_dptr(A, _i32t(), "A"), A.numel(), _dptr(l, _i32t(), "l"),
                                     _dptr(r, _i32t(), "r"), l.numel(), _dptr(out, _i32t(), "out"),
                                     int(k), _stream(stream, A)))
+
+
+def rmq_batch_multi(arrays, qs, l, r, out, k=0, flags=0, stream=None):
+    """Many arrays in one launch.  arrays: list of int32 CUDA tensors; qs: number
+    of queries of each (consecutive in l, r, out; positions relative to the array)."""
+    H = len(arrays)
+    desc = (rmq_array * max(H, 1))()
+    for h, (A, q) in enumerate(zip(arrays, qs)):
+        desc[h] = rmq_array(ctypes.c_void_p(_dptr(A, _i32t(), "A").value), A.numel(), int(q))
+    o = _opts(0, k, 0, flags)
+    dev = arrays[0] if H else l
+    _check(load().rmq_batch_multi(ctypes.cast(desc, ctypes.c_void_p), H, _dptr(l, _i32t(), "l"),
+                                  _dptr(r, _i32t(), "r"), _dptr(out, _i32t(), "out"), ctypes.byref(o),
+                                  _stream(stream, dev)))
 
 
 def rmq_launch_count() -> int:
