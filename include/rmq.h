@@ -164,7 +164,7 @@ rmq_status rmq_batch_noalloc(const int32_t *A, int64_t n, const int32_t *l, cons
  * s_h = q_0 + ... + q_{h-1}; their positions are relative to array h, and so
  * are the answers.  Invalid queries answer -1 (RMQ_ERR_QUERY_RANGE via
  * rmq_stream_status).  opts->k forces one block size for every array (0 =
- * chosen per array); opts->variant is ignored; opts->flags may hold
+ * chosen per array; at most 32768 here); opts->variant is ignored; opts->flags may hold
  * RMQ_FLAG_TEST_WITHHOLD_READY.  Workspace comes from the stream-ordered pool
  * and the call only enqueues memsets and kernel launches, so it can be
  * captured in a CUDA graph.  Arrays beyond 1024 are handled by further

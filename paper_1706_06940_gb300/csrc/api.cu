@@ -265,7 +265,7 @@ rmq_status rmq_batch_multi(const rmq_array *arrays, int32_t H, const int32_t *l,
     int32_t kforce = 0;
     if (opts) {
         if (opts->flags & ~(int32_t)RMQ_FLAG_TEST_WITHHOLD_READY) return RMQ_ERR_INVALID_ARG;
-        if (opts->k != 0 && !pow2_in_range(opts->k)) return RMQ_ERR_INVALID_ARG;
+        if (opts->k != 0 && (!pow2_in_range(opts->k) || opts->k > (1 << multi_max_logk()))) return RMQ_ERR_INVALID_ARG;
         flags = (uint32_t)opts->flags;
         kforce = opts->k;
     }

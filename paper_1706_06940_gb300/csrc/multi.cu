@@ -3,7 +3,7 @@
 // with a coarse level as in Sec. 3.3).
 //
 // Work is a queue of items taken in order through one atomic counter:
-//   phase 1: (array h, 8 consecutive blocks) -- block minima (Sec. 3.1 step 3,
+//   phase 1: (array h, 32768 consecutive cells) -- block minima (Sec. 3.1 step 3,
 //            level 0) written to the array's T0, and folded with atomicMin into
 //            level 0 of its coarse table (coarse blocks of 2^lc blocks);
 //            the CTA that finishes the last phase-1 item of array h builds the
@@ -28,7 +28,7 @@ namespace rmq {
 namespace {
 
 constexpr int kMT = 256;
-constexpr int kBlocksPerItem = kMT / 32;  // one block per warp
+constexpr int kLogChunk = 15;             // phase-1 item: 32768 cells of one array (k <= 32768)
 constexpr int kQueriesPerItem = 1024;     // 4 per thread
 constexpr int kMultiLcMax = 5;            // coarse blocks of at most 32 blocks: short T0 scans
 
@@ -154,7 +154,7 @@ __device__ __forceinline__ uint64_t resolve_t0(const uint64_t *T0, int logk, int
     return best;
 }
 
-__global__ void __launch_bounds__(kMT) k_multi(const __grid_constant__ MultiParams p) {
+__global__ void __launch_bounds__(kMT, 3) k_multi(const __grid_constant__ MultiParams p) {
     extern __shared__ uint64_t msm[];
     uint64_t *cs = msm;                                             // kCoarseCap
     int64_t *t0off = reinterpret_cast<int64_t *>(cs + kCoarseCap);   // kMultiMax + 1
@@ -171,12 +171,18 @@ __global__ void __launch_bounds__(kMT) k_multi(const __grid_constant__ MultiPara
     array_prefix<int64_t>(t0off, H, [&](int h) { return p.d[h].q > 0 ? nblocks(p.d[h]) : 0ll; }, wsum64);
     array_prefix<int64_t>(qoff, H, [&](int h) { return (int64_t)p.d[h].q; }, wsum64);
     array_prefix<int32_t>(pre1, H, [&](int h) {
-        return p.d[h].q > 0 ? (int32_t)((nblocks(p.d[h]) + kBlocksPerItem - 1) / kBlocksPerItem) : 0; }, wsum32);
+        return p.d[h].q > 0 ? (int32_t)(((int64_t)p.d[h].n + (1 << kLogChunk) - 1) >> kLogChunk) : 0; }, wsum32);
     array_prefix<int32_t>(pre3, H, [&](int h) { return (p.d[h].q + kQueriesPerItem - 1) / kQueriesPerItem; }, wsum32);
     const int64_t tot1 = pre1[H], tot3 = pre3[H];
 
+    // thread 0 asks for the next item while the CTA works on the current one
+    long long ahead = 0;
+    if (threadIdx.x == 0) ahead = (long long)atomicAdd(p.next, 1ull);
     for (;;) {
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(p.next, 1ull);
+        if (threadIdx.x == 0) {
+            s_item = ahead;
+            if (ahead < tot1 + tot3) ahead = (long long)atomicAdd(p.next, 1ull);
+        }
         __syncthreads();
         const int64_t item = s_item;
         __syncthreads();
@@ -187,35 +193,84 @@ __global__ void __launch_bounds__(kMT) k_multi(const __grid_constant__ MultiPara
             const MultiDesc d = p.d[h];
             const int64_t nb = nblocks(d);
             const Coarse g = coarse_geom(nb);
-            const int64_t b = (item - pre1[h]) * kBlocksPerItem + w;
-            if (b < nb) {
-                const int64_t K = 1ll << d.logk, lo = b << d.logk;
-                const int64_t hi = min((int64_t)d.n, lo + K) - 1;
-                uint64_t best = KEY_MAX;
-                const bool vec = ((reinterpret_cast<uintptr_t>(d.A) & 15) == 0) && hi - lo + 1 == K && K >= 4;
-                if (vec) {
-                    const int4 *v4 = reinterpret_cast<const int4 *>(d.A + lo);
-                    const int nv = (int)(K >> 2);
-                    for (int v0 = lane; v0 < nv; v0 += 128) {
-                        int4 x[4];
+            const int64_t c0 = (item - pre1[h]) << kLogChunk;
+            const int64_t c1 = min((int64_t)d.n, (int64_t)(c0 + (1ll << kLogChunk)));
+            const int64_t K = 1ll << d.logk;
+            const bool aligned = (reinterpret_cast<uintptr_t>(d.A) & 15) == 0;
+            uint64_t *T0h = p.T0 + t0off[h];
+            unsigned long long *C0 = reinterpret_cast<unsigned long long *>(p.Cs + (int64_t)h * kCoarseCap);
+            const int64_t s0 = c0 + (int64_t)w * 4096;  // this warp's slice: 32 rows of 32 16-byte vectors
+            if (K <= 2048 && aligned && s0 + 4096 <= d.n) {
+                // streaming slice: rows of 128 cells; blocks of k cells are groups of
+                // k/4 lanes (k < 128) or of k/128 whole rows (k >= 128)
+                const int4 *v4 = reinterpret_cast<const int4 *>(d.A + s0);
+                const int G = (int)(K >> 2);                  // lanes per block when k < 128
+                const int rpb = K >= 128 ? (int)(K >> 7) : 1;  // rows per block when k >= 128
+                uint64_t acc = KEY_MAX;
+#pragma unroll 1
+                for (int r0 = 0; r0 < 32; r0 += 8) {
+                    int4 x[8];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) x[u] = (v0 + 32 * u < nv) ? ld_stream_v4(v4 + v0 + 32 * u) : make_int4(0, 0, 0, 0);
+                    for (int u = 0; u < 8; ++u) x[u] = ld_stream_v4(v4 + (r0 + u) * 32 + lane);
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            if (v0 + 32 * u >= nv) continue;
-                            const uint32_t e = (uint32_t)(lo + 4 * (v0 + 32 * u));
-                            best = kmin(best, kmin(kmin(make_key(x[u].x, e), make_key(x[u].y, e + 1)),
-                                                   kmin(make_key(x[u].z, e + 2), make_key(x[u].w, e + 3))));
+                    for (int u = 0; u < 8; ++u) {
+                        const int r = r0 + u;
+                        const uint32_t e = (uint32_t)(s0 + 128 * r + 4 * lane);
+                        uint64_t v = kmin(kmin(make_key(x[u].x, e), make_key(x[u].y, e + 1)),
+                                          kmin(make_key(x[u].z, e + 2), make_key(x[u].w, e + 3)));
+                        if (K < 128) {
+                            for (int off = G >> 1; off > 0; off >>= 1) v = kmin(v, __shfl_xor_sync(0xffffffffu, v, off));
+                            if ((lane % G) == 0) {
+                                const int64_t b = (s0 + 128 * r + 4 * lane) >> d.logk;
+                                T0h[b] = v;
+                                atomicMin(C0 + (b >> g.lc), (unsigned long long)v);
+                            }
+                        } else {
+                            acc = kmin(acc, v);
+                            if ((r + 1) % rpb == 0) {
+                                const uint64_t bm = warp_min(acc);
+                                acc = KEY_MAX;
+                                if (lane == 0) {
+                                    const int64_t b = (s0 + 128 * r) >> d.logk;
+                                    T0h[b] = bm;
+                                    atomicMin(C0 + (b >> g.lc), (unsigned long long)bm);
+                                }
+                            }
                         }
                     }
-                } else {
-                    for (int64_t i = lo + lane; i <= hi; i += 32) best = kmin(best, make_key(__ldg(d.A + i), (uint32_t)i));
                 }
-                best = warp_min(best);
-                if (lane == 0) {
-                    p.T0[t0off[h] + b] = best;
-                    atomicMin(reinterpret_cast<unsigned long long *>(p.Cs + (int64_t)h * kCoarseCap) + (b >> g.lc),
-                              (unsigned long long)best);
+            } else {
+                // block by block (large k, an unaligned array, or the array's last slice)
+                const int64_t first = K <= 2048 ? (s0 >> d.logk) : (c0 >> d.logk) + w;
+                const int64_t step = K <= 2048 ? 1 : kMT / 32;
+                const int64_t end = K <= 2048 ? min(c1, s0 + 4096) : c1;
+                for (int64_t b = first; (b << d.logk) < end; b += step) {
+                    const int64_t lo = b << d.logk;
+                    const int64_t hi = min((int64_t)d.n, lo + K) - 1;
+                    uint64_t best = KEY_MAX;
+                    if (aligned && hi - lo + 1 == K) {
+                        const int4 *v4 = reinterpret_cast<const int4 *>(d.A + lo);
+                        const int nv = (int)(K >> 2);
+                        for (int v0 = lane; v0 < nv; v0 += 128) {
+                            int4 x[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) x[u] = (v0 + 32 * u < nv) ? ld_stream_v4(v4 + v0 + 32 * u) : make_int4(0, 0, 0, 0);
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                if (v0 + 32 * u >= nv) continue;
+                                const uint32_t e = (uint32_t)(lo + 4 * (v0 + 32 * u));
+                                best = kmin(best, kmin(kmin(make_key(x[u].x, e), make_key(x[u].y, e + 1)),
+                                                       kmin(make_key(x[u].z, e + 2), make_key(x[u].w, e + 3))));
+                            }
+                        }
+                    } else {
+                        for (int64_t i = lo + lane; i <= hi; i += 32) best = kmin(best, make_key(__ldg(d.A + i), (uint32_t)i));
+                    }
+                    best = warp_min(best);
+                    if (lane == 0) {
+                        T0h[b] = best;
+                        atomicMin(C0 + (b >> g.lc), (unsigned long long)best);
+                    }
                 }
             }
             __threadfence();
@@ -335,12 +390,14 @@ constexpr size_t kMultiSmem = (size_t)kCoarseCap * 8 + (size_t)(kMultiMax + 1) *
 // Block size for an array of the multi-array launch: the smallest power of
 // two >= 32 whose coarse blocks hold at most 32 blocks (short T0 scans).
 int multi_logk(int64_t n) {
-    for (int lk = MIN_LOGK; lk < MAX_LOGK; ++lk) {
+    for (int lk = MIN_LOGK; lk < kLogChunk; ++lk) {
         const int64_t nb = cdiv(n, 1ll << lk);
         if (coarse_geom(nb).lc <= kMultiLcMax) return lk;
     }
-    return MAX_LOGK;
+    return kLogChunk;
 }
+
+int multi_max_logk() { return kLogChunk; }
 
 size_t multi_workspace_bytes(const int64_t *n, const int64_t *q, const int32_t *logk, int H) {
     int64_t t0 = 0;

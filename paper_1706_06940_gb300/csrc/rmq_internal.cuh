@@ -201,6 +201,7 @@ cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint
 // Many arrays in one persistent launch (multi.cu).
 constexpr int kMultiMax = 1024;   // arrays per launch (their descriptors travel as a kernel parameter)
 int multi_logk(int64_t n);
+int multi_max_logk();   // the largest block size the multi-array launch accepts
 size_t multi_workspace_bytes(const int64_t *n, const int64_t *q, const int32_t *logk, int H);
 cudaError_t launch_multi(const int32_t *const *A, const int64_t *n, const int64_t *q, const int32_t *logk, int H,
                          const int32_t *l, const int32_t *r, int32_t *out, uint32_t flags, void *ws, cudaStream_t s);
