@@ -186,6 +186,13 @@ rmq_status rmq_build(const int32_t *A, int64_t n, const rmq_opts *opts, void *st
 rmq_status rmq_query(rmq_handle h, const int32_t *l, const int32_t *r, int64_t q,
                      int32_t *out, void *stream);
 
+/* Queries of H requests against resident handles in ONE kernel launch:
+ * request h asks q_counts[h] queries (consecutive in l, r, out; positions
+ * relative to hs[h]'s array).  A handle may appear in several requests.
+ * q_counts: host array.  Invalid queries answer -1.  Graph-capturable. */
+rmq_status rmq_query_multi(const rmq_handle *hs, const int64_t *q_counts, int32_t H, const int32_t *l,
+                           const int32_t *r, int32_t *out, void *stream);
+
 /* Device bytes owned by the handle (its sparse table), 0 for NULL. */
 int64_t rmq_handle_bytes(rmq_handle h);
 
@@ -194,6 +201,58 @@ int32_t rmq_handle_k(rmq_handle h);
 
 /* Release a handle (waits for the device work that uses it). NULL is a no-op. */
 void rmq_free(rmq_handle h);
+
+/* ---------------------------------------------------------------- serving
+ * A continuous-batching request server over resident arrays (host threads
+ * inside the library).  Arrays are admitted while the array plus an upper
+ * bound of its tables fit the memory budget.  Each submitted request (an
+ * array id and HOST buffers l, r, out of q entries) is queued; a scheduler
+ * thread packs all pending requests into one batch per tick and runs it on
+ * one of several streams (upload, one rmq_query_multi launch, download) while
+ * earlier batches are still running; a completion thread copies the answers
+ * into the requests' out buffers.  The caller keeps l, r, out alive and
+ * unmodified until rmq_server_wait returns for the ticket. */
+typedef struct rmq_server_s *rmq_server;
+
+typedef struct {
+    int64_t budget_bytes;       /* device bytes for resident arrays and tables; 0 = no limit */
+    int32_t inflight;           /* batches on the GPU at once (streams); 0 = 4 */
+    int32_t max_batch_queries;  /* queries per batch and per request at most; 0 = 4194304 */
+    int32_t flags;              /* reserved, must be 0 */
+    int32_t pad;
+} rmq_server_opts;
+
+typedef struct {
+    int64_t requests;            /* completed requests */
+    int64_t queries;             /* their queries */
+    int64_t batches;             /* batches launched */
+    int64_t table_bytes_in_use;  /* bytes reserved for resident arrays and tables */
+    int64_t resident_arrays;
+} rmq_server_stats;
+
+/* Create a server on the current device. */
+rmq_status rmq_server_create(const rmq_server_opts *opts, rmq_server *out);
+
+/* Build and keep resident the plain-BbST state of device array A (borrowed,
+ * like rmq_build); k = 0 picks it.  Waits for the build.  RMQ_ERR_BUDGET (and
+ * nothing is built) when it does not fit the budget. */
+rmq_status rmq_server_admit(rmq_server s, const int32_t *A, int64_t n, int32_t k, int32_t *id_out);
+
+/* Release an array's tables once no queued or running request uses it. */
+rmq_status rmq_server_evict(rmq_server s, int32_t id);
+
+/* Queue a request of q queries on array id; returns a ticket at once. */
+rmq_status rmq_server_submit(rmq_server s, int32_t id, const int32_t *l_host, const int32_t *r_host, int64_t q,
+                             int32_t *out_host, int64_t *ticket_out);
+
+/* Wait until the ticket's answers are in its out buffer; *latency_s = time
+ * from submit to answers (seconds, may be NULL).  Each ticket is waited once. */
+rmq_status rmq_server_wait(rmq_server s, int64_t ticket, double *latency_s);
+
+rmq_status rmq_server_stats_get(rmq_server s, rmq_server_stats *out);
+
+/* Stop the threads, finish running batches and free everything. */
+void rmq_server_destroy(rmq_server s);
 
 /* ----------------------------------------------------------- diagnostics */
 

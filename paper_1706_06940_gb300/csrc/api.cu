@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <mutex>
+#include <vector>
 
 #include "rmq_internal.cuh"
 
@@ -204,6 +205,14 @@ struct rmq_handle_s {
     int device;
 };
 
+namespace rmq {
+const int32_t *h_array(rmq_handle h) { return h->A; }
+const uint64_t *h_table(rmq_handle h) { return h->T; }
+const uint64_t *h_coarse(rmq_handle h) { return h->Cs; }
+int64_t h_n(rmq_handle h) { return h->n; }
+int32_t h_logk(rmq_handle h) { return h->logk; }
+}  // namespace rmq
+
 #pragma GCC visibility push(default)
 extern "C" {
 
@@ -350,6 +359,38 @@ rmq_status rmq_query(rmq_handle h, const int32_t *l, const int32_t *r, int64_t q
     rmq_status st = ws.alloc(query_residual_bytes(q, dev_info().sms), s);
     if (st != RMQ_OK) return st;
     return cuda_status(launch_query_plain(h->A, h->n, h->logk, h->T, h->Cs, h->nb, l, r, q, out, ws.p, s));
+}
+
+rmq_status rmq_query_multi(const rmq_handle *hs, const int64_t *q_counts, int32_t H, const int32_t *l,
+                           const int32_t *r, int32_t *out, void *stream) {
+    if (H < 0 || (H > 0 && (!hs || !q_counts))) return RMQ_ERR_INVALID_ARG;
+    int64_t qtot = 0;
+    for (int32_t h = 0; h < H; ++h) {
+        if (!hs[h] || q_counts[h] < 0 || q_counts[h] > kMaxQ) return RMQ_ERR_INVALID_ARG;
+        qtot += q_counts[h];
+    }
+    if (qtot > kMaxQ) return RMQ_ERR_INVALID_ARG;
+    if (qtot == 0) return RMQ_OK;
+    if (!l || !r || !out) return RMQ_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    int64_t off = 0;
+    std::vector<QueryReq> reqs;
+    for (int32_t g0 = 0; g0 < H; g0 += kReqMax) {
+        const int cnt = (int)std::min<int64_t>(kReqMax, H - g0);
+        reqs.clear();
+        int64_t gq = 0;
+        for (int i = 0; i < cnt; ++i) {
+            const rmq_handle h = hs[g0 + i];
+            reqs.push_back(QueryReq{h->A, h->T, h->Cs, h->n, q_counts[g0 + i], h->logk});
+            gq += q_counts[g0 + i];
+        }
+        if (gq > 0) {
+            cudaError_t e = launch_query_handles(reqs.data(), cnt, l + off, r + off, out + off, s);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        off += gq;
+    }
+    return RMQ_OK;
 }
 
 int64_t rmq_handle_bytes(rmq_handle h) { return h ? h->bytes : 0; }

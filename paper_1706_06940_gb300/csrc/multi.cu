@@ -65,11 +65,11 @@ __device__ __forceinline__ bool wait_flag(const uint32_t *flag, int64_t limit) {
     }
 }
 
-// Exclusive prefix over the H arrays of a per-array count (H <= kMultiMax),
-// into shared memory pre[0 .. H] (pre[H] = total).
-template <class T, class F>
-__device__ void array_prefix(T *pre, int H, F count, T *wsum) {
-    constexpr int PER = kMultiMax / kMT;
+// Exclusive prefix over the H arrays of a per-array count (H <= CAP), into
+// shared memory pre[0 .. H] (pre[H] = total).
+template <class T, int CAP, class F>
+__device__ void array_prefix_n(T *pre, int H, F count, T *wsum) {
+    constexpr int PER = CAP / kMT;
     T v[PER], tsum = 0;
 #pragma unroll
     for (int x = 0; x < PER; ++x) {
@@ -94,8 +94,13 @@ __device__ void array_prefix(T *pre, int H, F count, T *wsum) {
         if (i <= H) pre[i] = run;
         run += v[x];
     }
-    if (threadIdx.x == kMT - 1 && H == kMultiMax) pre[H] = run;
+    if (threadIdx.x == kMT - 1 && H == CAP) pre[H] = run;
     __syncthreads();
+}
+
+template <class T, class F>
+__device__ void array_prefix(T *pre, int H, F count, T *wsum) {
+    array_prefix_n<T, kMultiMax>(pre, H, count, wsum);
 }
 
 template <class T>
@@ -451,6 +456,157 @@ cudaError_t launch_multi(const int32_t *const *A, const int64_t *n, const int64_
     }
     delete p;
     return e;
+}
+
+}  // namespace rmq
+
+// ---------------------------------------------------------------------------
+// Queries of many requests against resident handles, in one launch.  Item =
+// (request h, 1024 queries); no item depends on another.  Each item copies
+// its handle's coarse table into shared memory, answers what the coarse level
+// settles, and finishes the rest (at most 1024, kept in shared memory) with
+// the handle's block table and partial-block scans.
+namespace rmq {
+namespace {
+
+struct ReqDesc {
+    const int32_t *A;
+    const uint64_t *T;
+    const uint64_t *Cs;
+    int32_t n;
+    int32_t q;
+    int32_t logk;
+    int32_t pad;
+};
+
+struct ReqParams {
+    int32_t H;
+    int32_t pad;
+    const int32_t *L, *R;
+    int32_t *out;
+    unsigned *err;
+    ReqDesc d[kReqMax];
+};
+
+__global__ void __launch_bounds__(kMT, 3) k_query_handles(const __grid_constant__ ReqParams p) {
+    __shared__ uint64_t cs[kCoarseCap];
+    __shared__ int64_t qoff[kReqMax + 1];
+    __shared__ int32_t pre[kReqMax + 1];
+    __shared__ int64_t wsum64[kMT / 32];
+    __shared__ int32_t wsum32[kMT / 32];
+    __shared__ uint16_t open_q[kQueriesPerItem];   // indices (inside the item) of the open queries
+    __shared__ int n_open;
+    const int H = p.H;
+    const int lane = threadIdx.x & 31;
+    array_prefix_n<int64_t, kReqMax>(qoff, H, [&](int h) { return (int64_t)p.d[h].q; }, wsum64);
+    array_prefix_n<int32_t, kReqMax>(pre, H, [&](int h) { return (p.d[h].q + kQueriesPerItem - 1) / kQueriesPerItem; }, wsum32);
+    const int64_t items = pre[H];
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int h = find_array<int32_t>(pre, H, (int32_t)it);
+        const ReqDesc d = p.d[h];
+        const int64_t nb = ((int64_t)d.n + (1ll << d.logk) - 1) >> d.logk;
+        const Coarse g = coarse_geom(nb);
+        const int64_t c0 = (it - pre[h]) * kQueriesPerItem;
+        const int64_t qn = min((int64_t)kQueriesPerItem, (int64_t)d.q - c0);
+        const int64_t qbase = qoff[h] + c0;
+        if (threadIdx.x == 0) n_open = 0;
+        load_coarse(cs, d.Cs, (int)(g.nbc * g.lvc));
+        __syncthreads();
+        bool bad = false;
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int64_t qi = threadIdx.x * 4 + x;
+            if (qi >= qn) continue;
+            const int32_t l = p.L[qbase + qi], r = p.R[qbase + qi];
+            const bool ok = l >= 0 && r >= l && r < d.n;
+            int32_t o = -1;
+            bad |= !ok;
+            if (ok) {
+                uint64_t m;
+                if (coarse_span_min(cs, g, d.logk, (uint32_t)l, (uint32_t)r, (uint32_t)l, (uint32_t)r, m)) {
+                    o = (int32_t)key_pos(m);
+                } else {
+                    open_q[atomicAdd(&n_open, 1)] = (uint16_t)qi;
+                    continue;
+                }
+            }
+            p.out[qbase + qi] = o;
+        }
+        if (bad && p.err) atomicOr(p.err, ERR_QUERY_RANGE);
+        __syncthreads();
+        const int cnt = n_open;
+        const int sh = d.logk + g.lc;
+        const SrcI32 src{d.A};
+        const bool vecA = (reinterpret_cast<uintptr_t>(d.A) & 15) == 0;
+        for (int wb = (threadIdx.x >> 5) * 32; wb < cnt; wb += (kMT >> 5) * 32) {
+            const int idx = wb + lane;
+            const bool has = idx < cnt;
+            Pending pl, pr;
+            bool hl = false, hr = false;
+            uint64_t best = KEY_MAX;
+            struct { int32_t i, l, r; } e{0, 0, 0};
+            if (has) {
+                e.i = open_q[idx];
+                e.l = p.L[qbase + e.i];
+                e.r = p.R[qbase + e.i];
+                int sub;
+                best = resolve_coarse(cs, g, d.logk, (uint32_t)e.l, (uint32_t)e.r, (uint32_t)e.l, (uint32_t)e.r, sub);
+                if (sub == SUB_WHOLE) {
+                    best = resolve_query(d.T, nb, d.logk, e.l, e.r, (uint32_t)e.l, (uint32_t)e.r, pl, pr, hl, hr);
+                } else if (sub != SUB_NONE) {
+                    Pending unused;
+                    bool unused_flag = false;
+                    if (sub & SUB_LEFT) {
+                        const int64_t end_l = ((((int64_t)e.l >> sh) + 1) << sh) - 1;
+                        best = kmin(best, resolve_query(d.T, nb, d.logk, e.l, end_l, (uint32_t)e.l, 0xffffffffu, pl,
+                                                        unused, hl, unused_flag));
+                    }
+                    if (sub & SUB_RIGHT) {
+                        const int64_t start_r = ((int64_t)e.r >> sh) << sh;
+                        Pending a, b2;
+                        bool ha = false, hb = false;
+                        best = kmin(best, resolve_query(d.T, nb, d.logk, start_r, e.r, 0u, (uint32_t)e.r, a, b2, ha, hb));
+                        if (ha) { pr = a; hr = true; }
+                        if (hb) { pr = b2; hr = true; }
+                    }
+                }
+            }
+            if (vecA) {
+                warp_drain_scans<SrcI32, true>(src, d.n, hl, pl, best);
+                warp_drain_scans<SrcI32, true>(src, d.n, hr, pr, best);
+            } else {
+                warp_drain_scans<SrcI32, false>(src, d.n, hl, pl, best);
+                warp_drain_scans<SrcI32, false>(src, d.n, hr, pr, best);
+            }
+            if (has) p.out[qbase + e.i] = (int32_t)key_pos(best);
+        }
+        __syncthreads();  // shared memory is reused by the next item
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_query_handles(const QueryReq *reqs, int H, const int32_t *l, const int32_t *r, int32_t *out,
+                                 cudaStream_t s) {
+    const DevInfo di = dev_info();
+    unsigned *err = err_word_ptr();
+    if (!err) return cudaErrorUnknown;
+    ReqParams *p = new ReqParams();
+    p->H = H;
+    p->L = l;
+    p->R = r;
+    p->out = out;
+    p->err = err;
+    int64_t items = 0;
+    for (int h = 0; h < H; ++h) {
+        p->d[h] = ReqDesc{reqs[h].A, reqs[h].T, reqs[h].Cs, (int32_t)reqs[h].n, (int32_t)reqs[h].q, reqs[h].logk, 0};
+        items += cdiv(reqs[h].q, kQueriesPerItem);
+    }
+    const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)di.sms * 3));
+    k_query_handles<<<(unsigned)ctas, kMT, 0, s>>>(*p);
+    note_launches(1);
+    delete p;
+    return cudaGetLastError();
 }
 
 }  // namespace rmq

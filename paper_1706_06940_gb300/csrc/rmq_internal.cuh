@@ -206,6 +206,26 @@ size_t multi_workspace_bytes(const int64_t *n, const int64_t *q, const int32_t *
 cudaError_t launch_multi(const int32_t *const *A, const int64_t *n, const int64_t *q, const int32_t *logk, int H,
                          const int32_t *l, const int32_t *r, int32_t *out, uint32_t flags, void *ws, cudaStream_t s);
 
+// Queries against many resident handles in one launch (multi.cu).
+constexpr int kReqMax = 512;      // requests per launch (descriptors travel as a kernel parameter)
+struct QueryReq {
+    const int32_t *A;
+    const uint64_t *T;
+    const uint64_t *Cs;
+    int64_t n;
+    int64_t q;
+    int32_t logk;
+};
+cudaError_t launch_query_handles(const QueryReq *reqs, int H, const int32_t *l, const int32_t *r, int32_t *out,
+                                 cudaStream_t s);
+
+// Internals of a resident handle (api.cu), for the multi-request paths.
+const int32_t *h_array(rmq_handle h);
+const uint64_t *h_table(rmq_handle h);
+const uint64_t *h_coarse(rmq_handle h);
+int64_t h_n(rmq_handle h);
+int32_t h_logk(rmq_handle h);
+
 // Contracted form (contract.cu).
 size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con);
 cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q,

@@ -51,6 +51,16 @@ class rmq_array(ctypes.Structure):
     _fields_ = [("A", ctypes.c_void_p), ("n", ctypes.c_int64), ("q", ctypes.c_int64)]
 
 
+class rmq_server_opts(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("inflight", ctypes.c_int32),
+                ("max_batch_queries", ctypes.c_int32), ("flags", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class rmq_server_stats(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_int64), ("queries", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("table_bytes_in_use", ctypes.c_int64), ("resident_arrays", ctypes.c_int64)]
+
+
 class rmq_opts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("k", ctypes.c_int32),
                 ("k_con", ctypes.c_int32), ("flags", ctypes.c_int32)]
@@ -67,6 +77,14 @@ _SIGS = {
     "rmq_launch_count": (_i64, []),
     "rmq_batch_noalloc": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, _i32, _vp]),
     "rmq_batch_multi": (_i32, [ctypes.c_void_p, _i32, _vp, _vp, _vp, ctypes.POINTER(rmq_opts), _vp]),
+    "rmq_query_multi": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _vp]),
+    "rmq_server_create": (_i32, [ctypes.POINTER(rmq_server_opts), ctypes.POINTER(_vp)]),
+    "rmq_server_admit": (_i32, [_vp, _vp, _i64, _i32, ctypes.POINTER(_i32)]),
+    "rmq_server_evict": (_i32, [_vp, _i32]),
+    "rmq_server_submit": (_i32, [_vp, _i32, _vp, _vp, _i64, _vp, ctypes.POINTER(_i64)]),
+    "rmq_server_wait": (_i32, [_vp, _i64, ctypes.POINTER(ctypes.c_double)]),
+    "rmq_server_stats_get": (_i32, [_vp, ctypes.POINTER(rmq_server_stats)]),
+    "rmq_server_destroy": (None, [_vp]),
     "rmq_batch_host": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, ctypes.POINTER(rmq_opts), _vp]),
     "rmq_build": (_i32, [_vp, _i64, ctypes.POINTER(rmq_opts), _vp, ctypes.POINTER(_vp)]),
     "rmq_query": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp]),
@@ -255,6 +273,72 @@ def rmq_build(A, k=0, stream=None) -> Handle:
 def rmq_query(h: Handle, l, r, out, stream=None):
     _check(load().rmq_query(h.ptr, _dptr(l, _i32t(), "l"), _dptr(r, _i32t(), "r"), l.numel(),
                             _dptr(out, _i32t(), "out"), _stream(stream, l)))
+
+
+def rmq_query_multi(handles, qs, l, r, out, stream=None):
+    """Queries of several requests against resident handles in one launch."""
+    H = len(handles)
+    hs = (ctypes.c_void_p * max(H, 1))(*[h.ptr.value if isinstance(h.ptr, ctypes.c_void_p) else h.ptr
+                                         for h in handles])
+    qc = (ctypes.c_int64 * max(H, 1))(*[int(q) for q in qs])
+    _check(load().rmq_query_multi(ctypes.cast(hs, ctypes.c_void_p), ctypes.cast(qc, ctypes.c_void_p), H,
+                                  _dptr(l, _i32t(), "l"), _dptr(r, _i32t(), "r"), _dptr(out, _i32t(), "out"),
+                                  _stream(stream, l)))
+
+
+class Server:
+    """The library's continuous-batching server (rmq_server_*).  Requests use
+    host numpy int32 arrays, kept referenced here until their ticket is waited."""
+
+    def __init__(self, budget_bytes=0, inflight=0, max_batch_queries=0):
+        o = rmq_server_opts(int(budget_bytes), int(inflight), int(max_batch_queries), 0, 0)
+        self.ptr = ctypes.c_void_p()
+        _check(load().rmq_server_create(ctypes.byref(o), ctypes.byref(self.ptr)))
+        self._arrays = {}
+        self._live = {}
+
+    def admit(self, A, k=0) -> int:
+        i = ctypes.c_int32()
+        _check(load().rmq_server_admit(self.ptr, _dptr(A, _i32t(), "A"), A.numel(), int(k), ctypes.byref(i)))
+        self._arrays[i.value] = A
+        return i.value
+
+    def evict(self, array_id):
+        _check(load().rmq_server_evict(self.ptr, int(array_id)))
+        self._arrays.pop(array_id, None)
+
+    def submit(self, array_id, l, r, out) -> int:
+        for name, a in (("l", l), ("r", r), ("out", out)):
+            if not (isinstance(a, np.ndarray) and a.dtype == np.int32 and a.flags.c_contiguous):
+                raise ValueError("%s must be a C-contiguous numpy int32 array" % name)
+        t = ctypes.c_int64()
+        _check(load().rmq_server_submit(self.ptr, int(array_id), l.ctypes.data, r.ctypes.data, len(l),
+                                        out.ctypes.data, ctypes.byref(t)))
+        self._live[t.value] = (l, r, out)
+        return t.value
+
+    def wait(self, ticket) -> float:
+        lat = ctypes.c_double()
+        st = load().rmq_server_wait(self.ptr, int(ticket), ctypes.byref(lat))
+        self._live.pop(ticket, None)
+        _check(st)
+        return lat.value
+
+    def stats(self) -> dict:
+        s = rmq_server_stats()
+        _check(load().rmq_server_stats_get(self.ptr, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in rmq_server_stats._fields_}
+
+    def close(self):
+        if self.ptr:
+            load().rmq_server_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def rmq_free(h: Handle):

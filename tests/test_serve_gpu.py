@@ -1,0 +1,113 @@
+"""The continuous-batching server: admission by memory budget, requests of
+very different sizes from several threads while earlier batches run, and
+every request's answers identical alone (rmq_query on the same handle) and
+in the mix, and equal to the oracle."""
+import threading
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1706_06940_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1706_06940_gb300 import rmq
+    return rmq
+
+
+def test_results_same_alone_and_in_the_mix(R):
+    ns = [3_000_000, 700_001, 20_000]
+    arrays = [W.uniform_array(n, 70 + i, 0, 1000 if i == 1 else 2**31) for i, n in enumerate(ns)]
+    dA = [torch.from_numpy(A).to(DEV) for A in arrays]
+    srv = R.Server(inflight=3)
+    ids = [srv.admit(A) for A in dA]
+    rng = np.random.default_rng(5)
+    reqs = []
+    for i in range(300):
+        h = int(rng.integers(0, len(ns)))
+        q = int(np.exp(rng.random() * np.log(100_000)))
+        if i % 3 == 0:
+            l, r = W.log_width_queries(ns[h], q, 1000 + i, 1, 5000)
+        else:
+            l, r = W.uniform_queries(ns[h], q, 1000 + i)
+        reqs.append((h, l, r, np.full(q, -7, dtype=np.int32)))
+    tickets = [None] * len(reqs)
+
+    def producer(part):
+        for j in range(part, len(reqs), 2):
+            h, l, r, out = reqs[j]
+            tickets[j] = srv.submit(ids[h], l, r, out)
+
+    th = [threading.Thread(target=producer, args=(p,)) for p in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    lat = [srv.wait(t) for t in tickets]
+    assert all(x >= 0 for x in lat)
+    st = srv.stats()
+    assert st["requests"] == len(reqs) and st["batches"] <= len(reqs)
+    handles = [R.rmq_build(A) for A in dA]
+    for (h, l, r, out) in reqs:
+        alone = torch.empty(len(l), dtype=torch.int32, device=DEV)
+        R.rmq_query(handles[h], torch.from_numpy(l).to(DEV), torch.from_numpy(r).to(DEV), alone)
+        assert np.array_equal(out, alone.cpu().numpy())
+        idx = rng.choice(len(l), min(len(l), 64), replace=False)
+        assert np.array_equal(out[idx], oracle.rmq_naive(arrays[h], l[idx], r[idx]))
+    for h in handles:
+        h.free()
+    srv.close()
+
+
+def test_admission_budget_and_eviction(R):
+    A = torch.from_numpy(W.uniform_array(5_000_000, 80)).to(DEV)
+    B = torch.from_numpy(W.uniform_array(5_000_000, 81)).to(DEV)
+    srv = R.Server(budget_bytes=30_000_000)          # room for one 20 MB array and its tables
+    a = srv.admit(A)
+    with pytest.raises(R.RmqError) as ei:
+        srv.admit(B)
+    assert ei.value.status == R.Status.ERR_BUDGET
+    l, r = W.uniform_queries(5_000_000, 1000, 82)
+    out = np.zeros(1000, np.int32)
+    srv.wait(srv.submit(a, l, r, out))
+    srv.evict(a)
+    b = srv.admit(B)
+    out2 = np.zeros(1000, np.int32)
+    srv.wait(srv.submit(b, l, r, out2))
+    assert np.array_equal(out2, oracle.rmq_naive(B.cpu().numpy(), l, r))
+    with pytest.raises(R.RmqError):
+        srv.submit(a, l, r, out)                      # evicted id
+    srv.close()
+
+
+def test_query_multi_over_handles(R):
+    arrays = [W.uniform_array(n, 90 + n % 7, 0, 50) for n in (100_000, 1, 64, 333_333)]
+    dA = [torch.from_numpy(A).to(DEV) for A in arrays]
+    hs = [R.rmq_build(A) for A in dA]
+    reqs = [(0, 500), (3, 70_000), (1, 3), (0, 1), (2, 0), (3, 5)]
+    ls, rs = [], []
+    for j, (h, q) in enumerate(reqs):
+        l, r = W.uniform_queries(len(arrays[h]), q, 300 + j)
+        ls.append(l)
+        rs.append(r)
+    L = torch.from_numpy(np.concatenate(ls)).to(DEV)
+    Rr = torch.from_numpy(np.concatenate(rs)).to(DEV)
+    out = torch.full((len(L),), -7, dtype=torch.int32, device=DEV)
+    R.rmq_query_multi([hs[h] for h, _ in reqs], [q for _, q in reqs], L, Rr, out)
+    got = out.cpu().numpy()
+    want = np.concatenate([oracle.rmq_naive(arrays[h], l, r) for (h, _), l, r in zip(reqs, ls, rs)])
+    assert np.array_equal(got, want)
+    assert R.rmq_stream_status() == R.Status.OK
+    for h in hs:
+        h.free()
