@@ -43,8 +43,11 @@ def parse_args():
     p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["single", "multi"], default="single",
-                   help="single: one n=1e8 array (default); multi: 512 uneven arrays in one launch")
+    p.add_argument("--workload", choices=["single", "multi", "served"], default="single",
+                   help="single: one n=1e8 array (default); multi: 512 uneven arrays in one launch; "
+                        "served: 64 resident arrays, Poisson request stream")
+    p.add_argument("--duration", type=float, default=2.0, help="served: seconds of arrivals")
+    p.add_argument("--rate", type=float, default=1e4, help="served: requests per second")
     p.add_argument("--arrays", type=int, default=512)
     p.add_argument("--n", type=float, default=1e8)
     p.add_argument("--q", type=float, default=1e7)
@@ -524,6 +527,131 @@ def run_multi(args, dist):
         print(json.dumps(line), flush=True)
 
 
+def run_served(args, dist):
+    """64 resident arrays totalling 4e9 cells (n log-uniform in [1e6, 2e8],
+    rescaled), requests arriving as a Poisson stream, each on a random array
+    with a log-uniform batch of [1, 1e5] uniform queries.  The library's
+    server (continuous batching over several streams) against one rmq_query
+    per request in arrival order on one stream, on the same arrival trace."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    if dist.rank == 0:
+        __graft_entry__.build()
+    dist.barrier()
+    from paper_1706_06940_gb300 import rmq, workloads as W
+
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    sizes = W.served_array_sizes(64, 4_000_000_000, args.seed + 7919 * dist.rank)
+    gen = torch.Generator(device=dev)
+    dA = []
+    for h, n in enumerate(sizes):
+        gen.manual_seed(args.seed + 31 * h)
+        dA.append(torch.randint(0, 2**31 - 1, (int(n),), dtype=torch.int32, device=dev, generator=gen))
+    torch.cuda.synchronize()                    # the arrays are written before the server reads them
+    free0, _ = torch.cuda.mem_get_info(dev)
+    srv = rmq.Server(budget_bytes=int(free0 * 0.8), inflight=4)
+    t_adm = time.perf_counter()
+    ids = [srv.admit(A) for A in dA]
+    t_adm = time.perf_counter() - t_adm
+    g = np.random.default_rng(args.seed + 1)
+    nreq = int(args.rate * args.duration)
+    arrive = np.cumsum(g.exponential(1.0 / args.rate, nreq))
+    arr = g.integers(0, len(dA), nreq)
+    qs = W.log_uniform_ints(g, nreq, 1, 1e5)
+    reqs = []
+    for i in range(nreq):
+        n = int(sizes[arr[i]])
+        a = g.integers(0, n, int(qs[i]), dtype=np.int64)
+        b = g.integers(0, n, int(qs[i]), dtype=np.int64)
+        reqs.append((int(arr[i]), np.minimum(a, b).astype(np.int32), np.maximum(a, b).astype(np.int32)))
+    qtot = int(qs.sum())
+
+    def served_run():
+        outs = [np.empty(len(l), np.int32) for _, l, _ in reqs]
+        tickets = [None] * nreq
+        lat = np.zeros(nreq)
+        done_t = [0.0]
+
+        def waiter():
+            for i in range(nreq):
+                while tickets[i] is None:
+                    time.sleep(20e-6)
+                lat[i] = srv.wait(tickets[i])
+            done_t[0] = time.perf_counter()
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        t0 = time.perf_counter()
+        for i, (h, l, r) in enumerate(reqs):
+            while time.perf_counter() - t0 < arrive[i]:
+                pass
+            tickets[i] = srv.submit(ids[h], l, r, outs[i])
+        th.join()
+        return lat, done_t[0] - t0, outs
+
+    handles = [rmq.rmq_build(A) for A in dA]
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream(dev)
+
+    def fifo_run():
+        lat = np.zeros(nreq)
+        outs = []
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s):
+            for i, (h, l, r) in enumerate(reqs):
+                while time.perf_counter() - t0 < arrive[i]:
+                    pass
+                dl = torch.from_numpy(l).to(dev, non_blocking=False)
+                dr = torch.from_numpy(r).to(dev, non_blocking=False)
+                out = torch.empty(len(l), dtype=torch.int32, device=dev)
+                rmq.rmq_query(handles[h], dl, dr, out, stream=s.cuda_stream)
+                o = out.cpu()
+                lat[i] = time.perf_counter() - t0 - arrive[i]
+                outs.append(o.numpy())
+        return lat, time.perf_counter() - t0, outs
+
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    lat_s, wall_s, outs_s = served_run()
+    clk = clocks.stop()
+    lat_f, wall_f, outs_f = fifo_run()
+    st = srv.stats()
+    for i in range(0, nreq, max(1, nreq // 200)):
+        if not np.array_equal(outs_s[i], outs_f[i]):
+            raise RuntimeError("served and per-request answers differ on request %d" % i)
+    import oracle
+    for i in g.choice(nreq, 16, replace=False):
+        h, l, r = reqs[i]
+        idx = g.choice(len(l), min(len(l), 16), replace=False)
+        if not np.array_equal(outs_s[i][idx], oracle.rmq_naive(dA[h].cpu().numpy(), l[idx], r[idx])):
+            raise RuntimeError("served answers differ from the oracle on request %d" % i)
+    srv.close()
+    for hd in handles:
+        hd.free()
+    if dist.rank == 0:
+        pct = lambda a, p: float(np.percentile(a, p) * 1e3)
+        line = {
+            "metric": METRIC, "value": qtot / wall_s, "unit": UNIT, "n_gpus": dist.world, "steps": nreq,
+            "warmup": 0, "ms_per_step": 1e3 * wall_s / nreq, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "served: 64 resident int32 arrays totalling %d cells (n log-uniform in "
+                                   "[1e6,2e8], rescaled), Poisson arrivals at %g req/s for %g s, batch log-uniform "
+                                   "in [1,1e5] uniform queries on a random array" % (int(sizes.sum()), args.rate,
+                                                                                      args.duration),
+                       "requests": nreq, "queries": qtot, "admit_s": t_adm},
+            "served": {"queries_per_s": qtot / wall_s, "p50_ms": pct(lat_s, 50), "p99_ms": pct(lat_s, 99),
+                       "max_ms": float(lat_s.max() * 1e3), "batches": st["batches"], "wall_s": wall_s},
+            "one_request_per_call": {"queries_per_s": qtot / wall_f, "p50_ms": pct(lat_f, 50),
+                                     "p99_ms": pct(lat_f, 99), "max_ms": float(lat_f.max() * 1e3),
+                                     "wall_s": wall_f},
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     dist = Dist()
@@ -532,6 +660,8 @@ def main():
             run_reference(args, dist)
         elif args.workload == "multi":
             run_multi(args, dist)
+        elif args.workload == "served":
+            run_served(args, dist)
         else:
             run_ours(args, dist)
     finally:

@@ -234,8 +234,10 @@ typedef struct {
 rmq_status rmq_server_create(const rmq_server_opts *opts, rmq_server *out);
 
 /* Build and keep resident the plain-BbST state of device array A (borrowed,
- * like rmq_build); k = 0 picks it.  Waits for the build.  RMQ_ERR_BUDGET (and
- * nothing is built) when it does not fit the budget. */
+ * like rmq_build); k = 0 picks it.  The build runs on the server's own stream,
+ * so A must be completely written before the call (synchronize the stream
+ * that wrote it).  Waits for the build.  RMQ_ERR_BUDGET (and nothing is
+ * built) when it does not fit the budget. */
 rmq_status rmq_server_admit(rmq_server s, const int32_t *A, int64_t n, int32_t k, int32_t *id_out);
 
 /* Release an array's tables once no queued or running request uses it. */
