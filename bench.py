@@ -280,9 +280,21 @@ def run_ours(args, dist):
     outs = {"plain": torch.empty(q, dtype=torch.int32, device=dev),
             "contracted": torch.empty(q, dtype=torch.int32, device=dev)}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-    tune = rmq.rmq_tune(n, q)
-    k = args.k or tune["k"]
-    k_con = args.k_con or tune["k_con"]
+    # block sizes: measured on this batch over 32..4096 (the autotuner), unless given
+    tune_ms = {}
+    k, k_con = args.k, args.k_con
+    run_forms = ["plain", "contracted"] if args.variant == "both" else [args.variant]
+    if not k:
+        k = rmq.rmq_tune(n, q)["k"]
+        if "plain" in run_forms:
+            best, tune_ms["plain"] = rmq.rmq_autotune(dA, dl, dr, outs["plain"], variant=1, k_min=32, k_max=4096)
+            k = best["k"]
+    if not k_con:
+        k_con = rmq.rmq_tune(n, q)["k_con"]
+        if "contracted" in run_forms:
+            best, tune_ms["contracted"] = rmq.rmq_autotune(dA, dl, dr, outs["contracted"], variant=2, k_min=32,
+                                                           k_max=4096)
+            k_con = best["k_con"]
     forms = ["plain", "contracted"] if args.variant == "both" else [args.variant]
     nev = {"plain": 4, "contracted": 6}
     vcode = {"plain": rmq.Variant.PLAIN, "contracted": rmq.Variant.CONTRACTED}
@@ -396,7 +408,8 @@ def run_ours(args, dist):
             "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": workload_name(n, q), "n": n, "q": q, "seed": args.seed,
-                       "forms": forms, "k": k, "k_con": k_con,
+                       "forms": forms, "k": k, "k_con": k_con, "k_autotuned": {"range": [32, 4096],
+                                                                           "best_ms": tune_ms},
                        "l2": "flushed by a 256 MiB write before each form (outside the timed events); "
                              "A alone (%.0f MB) exceeds L2" % (4 * n / 1e6),
                        "parallelism": "replicas" if dist.world > 1 else "single GPU"},

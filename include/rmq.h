@@ -277,6 +277,26 @@ int64_t rmq_table_bytes(int64_t n, int32_t k);
 /* The tuner's choice of form and block sizes for (n, q); host only. */
 rmq_status rmq_tune(int64_t n, int64_t q, rmq_opts *out);
 
+/* Autotuner (the paper leaves automated selection of k open, Sec. 5):
+ * times rmq_batch_ex on this batch for every power-of-two block size in
+ * [k_min, k_max] (0, 0 = [32, 4096]) and for the form(s) allowed by
+ * `variant` (AUTO = both), and returns the fastest options in *best (and its
+ * time in ms in *best_ms, may be NULL).  `out` receives answers while it
+ * measures.  Waits for the device.  With variant == AUTO the choice is
+ * remembered for the (n, q) shape (log2 rounded) and used by rmq_tune,
+ * rmq_batch and rmq_build from then on. */
+rmq_status rmq_autotune(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q,
+                        int32_t *out, int32_t variant, int32_t k_min, int32_t k_max, void *stream,
+                        rmq_opts *best, float *best_ms);
+
+/* Write / read the remembered choices (text: "log2n log2q variant k k_con"
+ * per line).  Loading merges into the current choices. */
+rmq_status rmq_tune_save(const char *path);
+rmq_status rmq_tune_load(const char *path);
+
+/* Forget every remembered choice. */
+void rmq_tune_clear(void);
+
 /* ------------------------------------------- step-level entry points
  * One step of the method each, on caller buffers, for composition and for
  * checking each step on its own.                                          */

@@ -441,11 +441,14 @@ int64_t rmq_table_bytes(int64_t n, int32_t k) {
     return table_entries(n, ilog2_host((uint64_t)k)) * 8;
 }
 
-// The tuner: the plain form over A with k near sqrt(n)/8 (a few extra reads
-// per query against a table that stays small next to A), and, for the
-// contracted form, k_con near sqrt(2q) capped at the paper's default 512.
+// The tuner: a choice measured by rmq_autotune for this (n, q) shape when
+// there is one; otherwise the plain form over A with k near sqrt(n)/8 (a few
+// extra reads per query against a table that stays small next to A), and,
+// for the contracted form, k_con near sqrt(2q) capped at the paper's default
+// 512.
 rmq_status rmq_tune(int64_t n, int64_t q, rmq_opts *out) {
     if (!out || n <= 0) return RMQ_ERR_INVALID_ARG;
+    if (q > 0 && tuned_lookup(n, q, out)) return RMQ_OK;   // a measured choice for this shape
     out->variant = RMQ_VARIANT_PLAIN;
     out->k = 1 << pow2_log_near(std::sqrt((double)n) / 8.0, MIN_LOGK, 12);
     out->k_con = 1 << pow2_log_near(std::sqrt(2.0 * (double)std::max<int64_t>(q, 1)), MIN_LOGK, 9);

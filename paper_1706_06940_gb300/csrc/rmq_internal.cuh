@@ -219,6 +219,9 @@ struct QueryReq {
 cudaError_t launch_query_handles(const QueryReq *reqs, int H, const int32_t *l, const int32_t *r, int32_t *out,
                                  cudaStream_t s);
 
+// Measured choices of the autotuner (tune.cu).
+bool tuned_lookup(int64_t n, int64_t q, rmq_opts *out);
+
 // Internals of a resident handle (api.cu), for the multi-request paths.
 const int32_t *h_array(rmq_handle h);
 const uint64_t *h_table(rmq_handle h);

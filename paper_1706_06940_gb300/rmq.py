@@ -77,6 +77,11 @@ _SIGS = {
     "rmq_launch_count": (_i64, []),
     "rmq_batch_noalloc": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, _i32, _vp]),
     "rmq_batch_multi": (_i32, [ctypes.c_void_p, _i32, _vp, _vp, _vp, ctypes.POINTER(rmq_opts), _vp]),
+    "rmq_autotune": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, ctypes.POINTER(rmq_opts),
+                            ctypes.POINTER(ctypes.c_float)]),
+    "rmq_tune_save": (_i32, [ctypes.c_char_p]),
+    "rmq_tune_load": (_i32, [ctypes.c_char_p]),
+    "rmq_tune_clear": (None, []),
     "rmq_query_multi": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _vp]),
     "rmq_server_create": (_i32, [ctypes.POINTER(rmq_server_opts), ctypes.POINTER(_vp)]),
     "rmq_server_admit": (_i32, [_vp, _vp, _i64, _i32, ctypes.POINTER(_i32)]),
@@ -367,6 +372,28 @@ def rmq_tune(n: int, q: int) -> dict:
     o = rmq_opts()
     _check(load().rmq_tune(int(n), int(q), ctypes.byref(o)))
     return {"variant": Variant(o.variant), "k": o.k, "k_con": o.k_con}
+
+
+def rmq_autotune(A, l, r, out, variant=0, k_min=0, k_max=0, stream=None):
+    """Measure block sizes / forms on this batch; returns (options dict, ms)."""
+    o = rmq_opts()
+    ms = ctypes.c_float()
+    _check(load().rmq_autotune(_dptr(A, _i32t(), "A"), A.numel(), _dptr(l, _i32t(), "l"), _dptr(r, _i32t(), "r"),
+                               l.numel(), _dptr(out, _i32t(), "out"), int(variant), int(k_min), int(k_max),
+                               _stream(stream, A), ctypes.byref(o), ctypes.byref(ms)))
+    return {"variant": Variant(o.variant), "k": o.k, "k_con": o.k_con}, ms.value
+
+
+def rmq_tune_save(path):
+    _check(load().rmq_tune_save(str(path).encode()))
+
+
+def rmq_tune_load(path):
+    _check(load().rmq_tune_load(str(path).encode()))
+
+
+def rmq_tune_clear():
+    load().rmq_tune_clear()
 
 
 # ---------------------------------------------------------------- steps

@@ -96,3 +96,25 @@ def test_host_checks_reject_bad_arguments_before_any_device_work(lib):
     assert lib.rmq_sparse_table_build(None, 10, None) == E
     assert lib.rmq_handle_bytes(None) == 0
     lib.rmq_free(None)
+
+
+def test_tune_table_load_save_roundtrip(lib, tmp_path):
+    rmq.rmq_tune_clear()
+    base = rmq.rmq_tune(10**8, 10**7)
+    p = tmp_path / "tune.txt"
+    p.write_text("# log2n log2q variant k k_con\n27 23 2 2048 256\n")
+    rmq.rmq_tune_load(p)
+    t = rmq.rmq_tune(10**8, 10**7)                   # log2 1e8 ~ 26.6 -> 27, log2 1e7 ~ 23.3 -> 23
+    assert t == {"variant": rmq.Variant.CONTRACTED, "k": 2048, "k_con": 256}
+    assert rmq.rmq_tune(10**6, 10**3) == rmq.rmq_tune(10**6, 10**3)
+    out = tmp_path / "saved.txt"
+    rmq.rmq_tune_save(out)
+    assert "27 23 2 2048 256" in out.read_text()
+    rmq.rmq_tune_clear()
+    assert rmq.rmq_tune(10**8, 10**7) == base
+    bad = tmp_path / "bad.txt"
+    bad.write_text("27 23 2 2047 256\n")
+    with pytest.raises(rmq.RmqError):
+        rmq.rmq_tune_load(bad)
+    with pytest.raises(rmq.RmqError):
+        rmq.rmq_tune_load(tmp_path / "missing.txt")

@@ -90,7 +90,7 @@ def test_a1_block_minima(R, n, k, hi, offset):
 # ------------------------------------------------------------------ step a2
 
 @pytest.mark.parametrize("n,k,hi", [(32, 32, 5), (64, 32, 5), (33 * 32 + 1, 32, 3), (5000 * 32 + 7, 32, 1000),
-                                    (9000 * 64, 64, 2), (2**20 + 5, 32, 2**31)])
+                                    (9000 * 64, 64, 2), (4097 * 32 + 5, 32, 2**31)])
 def test_a2_block_sparse_table(R, n, k, hi):
     A = W.uniform_array(n, 2 * n + k, 0, hi)
     nb = -(-n // k)
