@@ -295,11 +295,8 @@ __global__ void __launch_bounds__(256) k_query(Src src, Len len, int logk, const
 // settles, from shared memory alone, and appends the others to a residual
 // list; phase B (k_query_fine) finishes the residual queries on the block
 // table and with partial-block scans.
-struct Residual {
-    uint32_t qid;
-    int32_t l, r;
-    uint32_t pad;
-};
+// An open query of the two-phase kernel: its index in the batch.
+typedef uint32_t Residual;
 
 // Phase A's test: the minimum over every coarse block the query touches,
 // from two reads of the coarse table.  When its position lies inside the
@@ -380,23 +377,23 @@ __global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk
             }
         }
         int32_t o[4];
-        uint64_t rb[4];
         unsigned need = 0;
         bool bad = false;
         const int32_t na = (int32_t)n_a;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const bool present = base + i < q;
-            const bool ok = lq[i] >= 0 && rq[i] >= lq[i] && rq[i] < na;
+            const bool present = full || base + i < q;
+            const bool ok = present && lq[i] >= 0 && rq[i] >= lq[i] && rq[i] < na;
             bad |= present && !ok;
-            o[i] = -1;
-            rb[i] = KEY_MAX;
-            if (!ok) continue;
-            if (CON && aq[i] >= bq[i]) { o[i] = lq[i]; continue; }   // contracted l == r
-            const uint32_t lo = (uint32_t)(CON ? aq[i] : lq[i]);
-            const uint32_t hi = (uint32_t)(CON ? bq[i] - 1 : rq[i]);
-            if (coarse_span_min(cs, g, logk, lo, hi, (uint32_t)lq[i], (uint32_t)rq[i], rb[i])) o[i] = (int32_t)key_pos(rb[i]);
-            else need |= 1u << i;
+            const bool single = CON && ok && aq[i] >= bq[i];          // contracted l == r
+            // straight-line: an invalid or single query reads block 0 harmlessly
+            const bool use = ok && !single;
+            const uint32_t lo = use ? (uint32_t)(CON ? aq[i] : lq[i]) : 0u;
+            const uint32_t hi = use ? (uint32_t)(CON ? bq[i] - 1 : rq[i]) : 0u;
+            uint64_t m;
+            const bool inside = coarse_span_min(cs, g, logk, lo, hi, (uint32_t)lq[i], (uint32_t)rq[i], m);
+            o[i] = !ok ? -1 : (single ? lq[i] : (inside ? (int32_t)key_pos(m) : -1));
+            need |= (use && !inside ? 1u : 0u) << i;
         }
         if (full) {
             __stcs(reinterpret_cast<int4 *>(out + base), make_int4(o[0], o[1], o[2], o[3]));
@@ -405,29 +402,21 @@ __global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk
             for (int i = 0; i < 4; ++i)
                 if (base + i < q) out[base + i] = o[i];
         }
-        // append the open queries to the residual list, one atomic per warp
-        const unsigned c = __popc(need);
-        unsigned pre = c;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const unsigned y = __shfl_up_sync(0xffffffffu, pre, d);
-            if (lane >= d) pre += y;
-        }
-        const unsigned tot = __shfl_sync(0xffffffffu, pre, 31);
+        // append the open queries' indices to the CTA's residual list: slots from
+        // four ballots, one shared atomic per warp
+        const unsigned lt = (1u << lane) - 1u;
+        const unsigned b0 = __ballot_sync(0xffffffffu, need & 1u), b1 = __ballot_sync(0xffffffffu, need & 2u);
+        const unsigned b2 = __ballot_sync(0xffffffffu, need & 4u), b3 = __ballot_sync(0xffffffffu, need & 8u);
+        const unsigned c0 = __popc(b0), c1 = __popc(b1), c2 = __popc(b2), c3 = __popc(b3);
+        const unsigned tot = c0 + c1 + c2 + c3;
         if (tot) {
-            uint32_t slot = 0;
-            if (lane == 31) slot = atomicAdd(&n_open, tot);
-            slot = __shfl_sync(0xffffffffu, slot, 31) + (pre - c);
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (need & (1u << i)) {
-                    Residual e;
-                    e.qid = (uint32_t)(base + i);
-                    e.l = lq[i];
-                    e.r = rq[i];
-                    e.pad = 0;
-                    my[slot++] = e;
-                }
+            uint32_t sbase = 0;
+            if (lane == 0) sbase = atomicAdd(&n_open, tot);
+            sbase = __shfl_sync(0xffffffffu, sbase, 0);
+            if (need & 1u) my[sbase + __popc(b0 & lt)] = (uint32_t)base;
+            if (need & 2u) my[sbase + c0 + __popc(b1 & lt)] = (uint32_t)(base + 1);
+            if (need & 4u) my[sbase + c0 + c1 + __popc(b2 & lt)] = (uint32_t)(base + 2);
+            if (need & 8u) my[sbase + c0 + c1 + c2 + __popc(b3 & lt)] = (uint32_t)(base + 3);
         }
         if (!CON && bad && err) atomicOr(err, ERR_QUERY_RANGE);
     }
@@ -442,9 +431,8 @@ __global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk
         uint64_t best = KEY_MAX;
         uint32_t qid = 0;
         if (has) {
-            const Residual e = my[idx];
-            qid = e.qid;
-            const int32_t l = e.l, r = e.r;
+            qid = my[idx];
+            const int32_t l = L[qid], r = R[qid];
             const int64_t lo = CON ? RL[qid] : l;
             const int64_t hi = CON ? (int64_t)RR[qid] - 1 : r;
             int sub;

@@ -192,7 +192,7 @@ inline ResidualPlan residual_plan(int64_t q, int sms) {
 }
 inline size_t query_residual_bytes(int64_t q, int sms) {
     const ResidualPlan p = residual_plan(q, sms);
-    return (size_t)(p.ctas * p.region) * 16;
+    return (size_t)(p.ctas * p.region) * 4;
 }
 cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint64_t *T, const uint64_t *Cs,
                                int64_t nb, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
