@@ -340,7 +340,7 @@ def run_ours(args, dist):
 
     # per-stage device times (ms), averaged over steps
     stage_names = {"plain": ["block_minima", "sparse_table", "queries"],
-                   "contracted": ["sort", "remap", "contract", "table_AQ", "queries"]}
+                   "contracted": ["mark", "rank", "contract", "table_AQ", "queries"]}
     stages = {f: {s: 0.0 for s in stage_names[f]} for f in forms}
     form_ms = {f: 0.0 for f in forms}
     for evs in all_evs:

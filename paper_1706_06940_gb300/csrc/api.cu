@@ -492,6 +492,18 @@ rmq_status rmq_rank_endpoints(const uint32_t *pos_sorted, const uint32_t *tag_so
     return cuda_status(rank_endpoints(pos_sorted, tag_sorted, q, P_out, m_dev, rank_l, rank_r, ws.p, s));
 }
 
+rmq_status rmq_endpoint_bitmap(const int32_t *l, const int32_t *r, int64_t q, int64_t n, uint32_t *BP,
+                               int64_t *m_dev, void *stream) {
+    if (!BP || !m_dev || n <= 0 || n > kMaxN || q < 0 || q > kMaxQ) return RMQ_ERR_INVALID_ARG;
+    if (q > 0 && (!l || !r)) return RMQ_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(BP) & 7) return RMQ_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    Workspace ws;
+    rmq_status st = ws.alloc(endpoint_bitmap_workspace_bytes(n), s);
+    if (st != RMQ_OK) return st;
+    return cuda_status(endpoint_bitmap(l, r, q, n, reinterpret_cast<uint2 *>(BP), m_dev, nullptr, ws.p, s));
+}
+
 rmq_status rmq_contract(const int32_t *A, int64_t n, const uint32_t *P, const int64_t *m_dev, int64_t m_max,
                         uint64_t *AQ, void *stream) {
     if (!A || !P || !m_dev || !AQ || n <= 0 || n > kMaxN || m_max < 0) return RMQ_ERR_INVALID_ARG;
@@ -499,7 +511,7 @@ rmq_status rmq_contract(const int32_t *A, int64_t n, const uint32_t *P, const in
     Workspace ws;
     rmq_status st = ws.alloc(contract_workspace_bytes(n), s);
     if (st != RMQ_OK) return st;
-    return cuda_status(contract(A, n, P, m_dev, AQ, ws.p, s));
+    return cuda_status(contract(A, n, P, m_dev, m_max, AQ, ws.p, s));
 }
 
 }  // extern "C"

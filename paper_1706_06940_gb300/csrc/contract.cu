@@ -326,66 +326,157 @@ __global__ void __launch_bounds__(kT) k_rank_scatter(const uint32_t *__restrict_
     }
 }
 
-// ----------------------------------------------------------- contraction
-// so[t] = (number of P_j < t * kATile) - 1: the segment open just before
-// tile t.  Segments that are open at some tile start span several tiles and
-// are combined with atomicMin, so they start at KEY_MAX here; all other
-// segments lie in one tile and are written exactly once, by a plain store.
-__global__ void __launch_bounds__(kT) k_con_prep(const uint32_t *__restrict__ P, const int64_t *m_dev, int64_t ntA,
-                                                 int32_t *__restrict__ so, uint64_t *__restrict__ H) {
-    const int64_t m = *m_dev;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= ntA; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t ts = t * kATile;
-        int64_t lo = 0, hi = m;  // first j with P[j] >= ts
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if ((int64_t)P[mid] < ts) lo = mid + 1;
-            else hi = mid;
+// ------------------------------------------------------- endpoint bitmap
+// The batch path replaces the comparison of endpoints by a bitmap over the
+// positions of A (a counting sort of keys drawn from [0, n)): bit p of the
+// bitmap is set when p is an endpoint.  The set bits, in increasing order,
+// are exactly the distinct sorted positions P of step 1, and the rank of an
+// endpoint is the number of set bits below it.  BP holds one uint2 per 32
+// positions (x = bit word, y = set bits in all earlier words), plus a final
+// entry (x = 0, y = m) so that every rank lookup stays in bounds.
+__device__ __forceinline__ void mark_bit(uint32_t *bw, uint32_t p) {
+    // fire-and-forget OR into word p / 32 (the .x field of its uint2)
+    asm volatile("red.global.or.b32 [%0], %1;" ::"l"(bw + 2 * (p >> 5)), "r"(1u << (p & 31)) : "memory");
+}
+
+// Marks both ends of every query.  An invalid query marks position 0 (the
+// pair (0, 0) of the sort) and raises the error word.
+__global__ void __launch_bounds__(kT) k_mark_endpoints(const int32_t *__restrict__ L, const int32_t *__restrict__ R,
+                                                       int64_t q, int64_t n, uint32_t *__restrict__ bw,
+                                                       unsigned *err) {
+    bool bad = false;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    auto mark = [&](int32_t l, int32_t r) {
+        const bool ok = l >= 0 && r >= l && (int64_t)r < n;
+        bad |= !ok;
+        mark_bit(bw, ok ? (uint32_t)l : 0u);
+        mark_bit(bw, ok ? (uint32_t)r : 0u);
+    };
+    int64_t done = 0;
+    if (((reinterpret_cast<uintptr_t>(L) | reinterpret_cast<uintptr_t>(R)) & 15) == 0) {
+        const int64_t nv = q / 4;
+        for (int64_t v = tid; v < nv; v += nthr) {
+            const int4 l4 = __ldcs(reinterpret_cast<const int4 *>(L) + v);
+            const int4 r4 = __ldcs(reinterpret_cast<const int4 *>(R) + v);
+            mark(l4.x, r4.x); mark(l4.y, r4.y); mark(l4.z, r4.z); mark(l4.w, r4.w);
         }
-        const int64_t s = lo - 1;
-        so[t] = (int32_t)s;
-        if (s >= 0 && s <= m - 2) H[s] = KEY_MAX;
+        done = nv * 4;
+    }
+    for (int64_t i = done + tid; i < q; i += nthr) mark(__ldcs(L + i), __ldcs(R + i));
+    if (bad) atomicOr(err, ERR_QUERY_RANGE);
+}
+
+// Marks given positions P[0 .. m) (the step-level contraction takes P).
+__global__ void __launch_bounds__(kT) k_mark_positions(const uint32_t *__restrict__ P, const int64_t *m_dev,
+                                                       uint32_t *__restrict__ bw) {
+    const int64_t m = *m_dev;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+        mark_bit(bw, P[j]);
+}
+
+// Rank counts: the exclusive scan of popc(BP[w].x) into BP[w].y, over the
+// nbp = ceil(n / 32) + 1 entries, in tiles of kTile entries (warp w of a CTA
+// owns 512 consecutive entries, lane-interleaved rows of 32).
+__global__ void __launch_bounds__(kT) k_bits_partial(const uint2 *__restrict__ BP, int64_t nbp,
+                                                     uint32_t *__restrict__ partial) {
+    __shared__ uint32_t wsum[kT / 32];
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    uint32_t c = 0;
+#pragma unroll
+    for (int i = 0; i < kIPT; ++i) {
+        const int64_t e = base + i * kT + threadIdx.x;
+        if (e < nbp) c += __popc(BP[e].x);
+    }
+    uint32_t total;
+    block_excl_scan(c, wsum, total);
+    if (threadIdx.x == 0) partial[blockIdx.x] = total;
+}
+
+// Also sets to KEY_MAX every A_Q entry that the contraction combines with
+// atomics: the segment open just before each tile of kATile cells (the
+// segment whose left end P_j lies below the tile, when j <= m - 2).
+__global__ void __launch_bounds__(kT) k_bits_final(uint2 *__restrict__ BP, int64_t nbp,
+                                                   const uint32_t *__restrict__ partial, const int64_t *m_dev,
+                                                   int64_t ntA, uint64_t *__restrict__ AQ) {
+    __shared__ uint32_t wsum[kT / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)w * (32 * kIPT);
+    uint32_t c[kIPT];
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kIPT; ++i) {
+        const int64_t e = base + i * 32 + lane;
+        c[i] = e < nbp ? __popc(BP[e].x) : 0u;
+        s += c[i];
+    }
+    s = __reduce_add_sync(0xffffffffu, s);
+    uint32_t total;
+    uint32_t run = block_excl_scan(lane == 0 ? s : 0u, wsum, total);
+    run = __shfl_sync(0xffffffffu, run, 0) + partial[blockIdx.x];
+    const int64_t m = *m_dev;
+#pragma unroll
+    for (int i = 0; i < kIPT; ++i) {
+        uint32_t x = c[i];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        const uint32_t ex = run + x - c[i];
+        const int64_t e = base + i * 32 + lane;
+        if (e < nbp) {
+            BP[e].y = ex;
+            if ((e & (kATile / 32 - 1)) == 0 && (e / (kATile / 32)) < ntA) {
+                const int64_t sg = (int64_t)ex - 1;
+                if (sg >= 0 && sg <= m - 2) AQ[sg] = KEY_MAX;
+            }
+        }
+        run += __shfl_sync(0xffffffffu, x, 31);
     }
 }
 
+// ----------------------------------------------------------- contraction
 __device__ __forceinline__ void emit_atomic(uint64_t *H, int64_t s, uint64_t v) {
     if (v < __ldcg(reinterpret_cast<const unsigned long long *>(H) + s))
         atomicMin(reinterpret_cast<unsigned long long *>(H) + s, (unsigned long long)v);
 }
 
 // One warp per tile of kATile = 1024 cells; lane L owns the 32 consecutive
-// cells [32L, 32L + 32) of the tile.  Segment j covers A[P_j .. P_{j+1}]; a
-// boundary cell P_j closes segment j-1 (it is its last cell) and opens
-// segment j.  The tile is read with coalesced 16-byte loads and handed to the
-// lanes through shared memory (swizzled so that neither side has bank
-// conflicts); the boundaries of the tile form a 1024-bit bitmap, one word per
-// lane.  The b-th boundary of the tile closes segment s_t + b, so every lane
-// writes the value of each segment it closes into slot b of a per-warp array;
-// a segmented min-scan over the lanes adds, to the first slot of each lane,
-// the part of that segment held by the lanes before it; the slots are then
-// stored to A_Q in order (coalesced).  Only the first segment (begun in an
-// earlier tile) and the one left open at the end are combined with atomics.
+// cells [32L, 32L + 32) of the tile, whose endpoint marks are exactly the
+// bitmap word BP[32t + L].x, and BP[32t + L].y - 1 is the segment open at the
+// lane's first cell.  Segment j covers A[P_j .. P_{j+1}]; a marked cell P_j
+// closes segment j-1 (it is its last cell) and opens segment j.  The tile is
+// read with coalesced 16-byte loads and handed to the lanes through shared
+// memory (swizzled so that neither side has bank conflicts).  Each lane walks
+// its 32 cells branch-free, keeping the running minimum of the open segment
+// and writing the value of each segment it closes into its slot of a per-warp
+// array; a segmented min-scan over the lanes adds, to the first slot of each
+// lane, the part of that segment held by the lanes before it; the slots are
+// then stored to A_Q in order (coalesced).  Only the first segment (begun in
+// an earlier tile) and the one left open at the end are combined with
+// atomics (those entries were set to KEY_MAX by k_bits_final).
 __device__ __forceinline__ int swz(int x) { return (x & ~7) | ((x & 7) ^ ((x >> 3) & 7)); }
 
-constexpr int kContractSmem = (kT / 32) * kATile * 8 + (kT / 32) * 32 * 4;   // slots (tile view) + bitmaps
+constexpr int kContractSmem = (kT / 32) * kATile * 8;   // per warp: the tile, then its slots
 
 template <bool VEC>
-__global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const uint32_t *__restrict__ P,
-                                                 const int64_t *m_dev, const int32_t *__restrict__ so, int64_t ntA,
-                                                 uint64_t *__restrict__ H) {
+__global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const uint2 *__restrict__ BP,
+                                                 const int64_t *m_dev, int64_t ntA, uint64_t *__restrict__ H) {
     extern __shared__ uint64_t csmem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint64_t *slot = csmem + (size_t)w * kATile;                      // 1024 slots per warp
     int4 *tile = reinterpret_cast<int4 *>(slot);                      // the same memory, first 4 KB
-    uint32_t *bm = reinterpret_cast<uint32_t *>(csmem + (size_t)(kT / 32) * kATile) + w * 32;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t m = *m_dev;
-    const int64_t nv = n / 4;  // vectors wholly inside [0, n)
+    const int64_t nv = n / 4;                // vectors wholly inside [0, n)
+    const int64_t nw = (n + 31) >> 5;        // bitmap words; BP[nw] is the end entry
     for (int64_t t = warp; t < ntA; t += nwarps) {
-        // the tile's cells are requested together with its segment numbers (one
+        // the tile's cells are requested together with its bitmap words (one
         // round trip); tiles outside [P_0, P_{m-1}] are skipped after the fact
-        const int64_t s_t = so[t], s_n = so[t + 1];
+        const int64_t wi = t * 32 + lane;
+        const uint2 e = __ldg(BP + (wi < nw ? wi : nw));
         const int64_t ts = t * kATile;
         int4 v[8];
 #pragma unroll
@@ -396,19 +487,24 @@ __global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const ui
                            : make_int4(__ldg(src.a + 4 * vi), __ldg(src.a + 4 * vi + 1), __ldg(src.a + 4 * vi + 2),
                                        __ldg(src.a + 4 * vi + 3));
             } else {
-                const int64_t e = 4 * vi;
-                v[u] = make_int4(e < n ? __ldg(src.a + e) : INT_MAX, e + 1 < n ? __ldg(src.a + e + 1) : INT_MAX,
-                                 e + 2 < n ? __ldg(src.a + e + 2) : INT_MAX, e + 3 < n ? __ldg(src.a + e + 3) : INT_MAX);
+                const int64_t c = 4 * vi;
+                v[u] = make_int4(c < n ? __ldg(src.a + c) : INT_MAX, c + 1 < n ? __ldg(src.a + c + 1) : INT_MAX,
+                                 c + 2 < n ? __ldg(src.a + c + 2) : INT_MAX, c + 3 < n ? __ldg(src.a + c + 3) : INT_MAX);
             }
         }
-        if (s_t == s_n && (s_t < 0 || s_t > m - 2)) continue;
-        if (s_t == s_n) {  // no boundary in the tile: one partial minimum of segment s_t
+        const uint32_t word = e.x;
+        const int64_t s_t = (int64_t)__shfl_sync(0xffffffffu, e.y, 0) - 1;      // open before the tile
+        const uint32_t nbits = __popc(word);
+        const uint32_t cnt = __reduce_add_sync(0xffffffffu, nbits);             // boundaries in the tile
+        const int64_t s_n = s_t + cnt;                                           // open after the tile
+        if (cnt == 0 && (s_t < 0 || s_t > m - 2)) continue;
+        if (cnt == 0) {  // no boundary in the tile: one partial minimum of segment s_t
             uint64_t best = KEY_MAX;
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const uint32_t e = (uint32_t)(ts + 4 * (u * 32 + lane));
-                best = kmin(best, kmin(kmin(make_key(v[u].x, e), make_key(v[u].y, e + 1)),
-                                       kmin(make_key(v[u].z, e + 2), make_key(v[u].w, e + 3))));
+                const uint32_t c = (uint32_t)(ts + 4 * (u * 32 + lane));
+                best = kmin(best, kmin(kmin(make_key(v[u].x, c), make_key(v[u].y, c + 1)),
+                                       kmin(make_key(v[u].z, c + 2), make_key(v[u].w, c + 3))));
             }
             best = warp_min(best);
             if (lane == 0) emit_atomic(H, s_t, best);
@@ -417,33 +513,8 @@ __global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const ui
         __syncwarp();  // the previous tile's slots are no longer read
 #pragma unroll
         for (int u = 0; u < 8; ++u) tile[swz(u * 32 + lane)] = v[u];
-        bm[lane] = 0;
         __syncwarp();
-        const int cnt = (int)(s_n - s_t);
-        for (int64_t j0 = s_t + 1; j0 <= s_n; j0 += 256) {
-            uint32_t pp[8];
-#pragma unroll
-            for (int x = 0; x < 8; ++x) {
-                const int64_t j = j0 + x * 32 + lane;
-                pp[x] = j <= s_n ? P[j] : 0xffffffffu;
-            }
-#pragma unroll
-            for (int x = 0; x < 8; ++x)
-                if (pp[x] != 0xffffffffu) {
-                    const uint32_t off = (uint32_t)((int64_t)pp[x] - ts);
-                    atomicOr(&bm[off >> 5], 1u << (off & 31));
-                }
-        }
-        __syncwarp();
-        const uint32_t word = bm[lane];
-        const uint32_t nbits = __popc(word);
-        uint32_t pre = nbits;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, pre, d);
-            if (lane >= d) pre += y;
-        }
-        pre -= nbits;
+        const uint32_t pre = e.y - (uint32_t)(s_t + 1);   // slot of this lane's first boundary
         int32_t vals[32];
 #pragma unroll
         for (int x = 0; x < 8; ++x) {
@@ -451,29 +522,28 @@ __global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const ui
             vals[4 * x] = q4.x; vals[4 * x + 1] = q4.y; vals[4 * x + 2] = q4.z; vals[4 * x + 3] = q4.w;
         }
         __syncwarp();  // the tile is read; its memory now holds the slots
-        // running minimum of the open segment as (value, cell); cells are met in
-        // increasing order, so a strict comparison keeps the leftmost
+        // running minimum of the open segment as (value, cell offset); cells
+        // are met in increasing order, so a strict comparison keeps the
+        // leftmost.  A marked cell is the last cell of the open segment (which
+        // is then written to its slot) and the first of the next one.
         const uint32_t cell0 = (uint32_t)(ts + 32 * lane);
-        int32_t cv = vals[0];
-        uint32_t cp = cell0;
+        int32_t cv = INT_MAX;
+        uint32_t cp = 0;
         uint32_t k = pre;
-        if (word & 1u) { slot[k++] = make_key(cv, cp); }
 #pragma unroll
-        for (int c = 1; c < 32; ++c) {
+        for (int c = 0; c < 32; ++c) {
             const int32_t vv = vals[c];
-            if (word & (1u << c)) {
-                // boundary cell: last cell of the open segment, first of the next
-                const bool keep = cv <= vv;
-                slot[k++] = make_key(keep ? cv : vv, keep ? cp : cell0 + c);
-                cv = vv;
-                cp = cell0 + c;
-            } else if (vv < cv) {
-                cv = vv;
-                cp = cell0 + c;
-            }
+            const bool lt = vv < cv;
+            const int32_t mv = lt ? vv : cv;
+            const uint32_t mp = lt ? (uint32_t)c : cp;
+            const bool b = (word >> c) & 1u;
+            if (b) slot[k] = make_key(mv, cell0 + mp);
+            k += b ? 1u : 0u;
+            cv = b ? vv : mv;
+            cp = b ? (uint32_t)c : mp;
         }
         bool f = nbits != 0;
-        uint64_t val = make_key(cv, cp);
+        uint64_t val = make_key(cv, cell0 + cp);
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const bool of = __shfl_up_sync(0xffffffffu, f, d);
@@ -488,7 +558,7 @@ __global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const ui
         if (nbits) slot[pre] = kmin(slot[pre], carry_in);
         const uint64_t tail = __shfl_sync(0xffffffffu, val, 31);
         __syncwarp();
-        for (int b = lane; b < cnt; b += 32) {
+        for (uint32_t b = lane; b < cnt; b += 32) {
             const int64_t sg = s_t + b;
             if (sg < 0 || sg > m - 2) continue;
             if (b == 0) emit_atomic(H, sg, slot[0]);
@@ -582,17 +652,29 @@ cudaError_t rank_endpoints(const uint32_t *pos, const uint32_t *tag, int64_t q, 
     return cudaGetLastError();
 }
 
-size_t contract_workspace_bytes(int64_t n) { return align256((cdiv(n, kATile) + 2) * 4); }
+int64_t bitmap_entries(int64_t n) { return cdiv(n, 32) + 1; }
 
-cudaError_t contract(const int32_t *A, int64_t n, const uint32_t *P, const int64_t *m_dev, uint64_t *AQ, void *ws,
-                     cudaStream_t s) {
+namespace {
+
+// BP[w].y = set bits in words before w, *m_dev = all set bits; A_Q entries
+// that the contraction combines with atomics are set to KEY_MAX (AQ may be
+// null when no contraction follows).  aux: scan_aux_words(tiles) words.
+cudaError_t bitmap_ranks(uint2 *BP, int64_t n, int64_t *m_dev, uint64_t *AQ, uint32_t *aux, cudaStream_t s) {
+    const int64_t nbp = bitmap_entries(n);
+    const int64_t tiles = cdiv(nbp, kTile);
+    k_bits_partial<<<(unsigned)tiles, kT, 0, s>>>(BP, nbp, aux);
+    k_scan_top<<<1, kT, 0, s>>>(aux, tiles, m_dev);   // tile counts scanned in place, total -> m
+    k_bits_final<<<(unsigned)tiles, kT, 0, s>>>(BP, nbp, aux, m_dev, AQ ? cdiv(n, kATile) : 0, AQ);
+    note_launches(3);
+    return cudaGetLastError();
+}
+
+size_t bitmap_aux_bytes(int64_t n) { return align256(cdiv(bitmap_entries(n), kTile) * 4); }
+
+cudaError_t contract_bitmap(const int32_t *A, int64_t n, const uint2 *BP, const int64_t *m_dev, uint64_t *AQ,
+                            cudaStream_t s) {
     const int64_t ntA = cdiv(n, kATile);
-    int32_t *so = static_cast<int32_t *>(ws);
     const DevInfo di = dev_info();
-    const int64_t pctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(ntA + 1, kT), (int64_t)di.sms * 8));
-    k_con_prep<<<(unsigned)pctas, kT, 0, s>>>(P, m_dev, ntA, so, AQ);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(ntA, kT / 32), (int64_t)di.sms * 3));
     SrcI32 src{A};
     static bool attr[64] = {false};
@@ -602,71 +684,105 @@ cudaError_t contract(const int32_t *A, int64_t n, const uint32_t *P, const int64
         attr[di.device] = true;
     }
     if ((reinterpret_cast<uintptr_t>(A) & 15) == 0)
-        k_contract<true><<<(unsigned)ctas, kT, kContractSmem, s>>>(src, n, P, m_dev, so, ntA, AQ);
+        k_contract<true><<<(unsigned)ctas, kT, kContractSmem, s>>>(src, n, BP, m_dev, ntA, AQ);
     else
-        k_contract<false><<<(unsigned)ctas, kT, kContractSmem, s>>>(src, n, P, m_dev, so, ntA, AQ);
-    note_launches(2);
+        k_contract<false><<<(unsigned)ctas, kT, kContractSmem, s>>>(src, n, BP, m_dev, ntA, AQ);
+    note_launches(1);
     return cudaGetLastError();
 }
 
+}  // namespace
+
+size_t endpoint_bitmap_workspace_bytes(int64_t n) { return bitmap_aux_bytes(n); }
+
+cudaError_t endpoint_bitmap(const int32_t *l, const int32_t *r, int64_t q, int64_t n, uint2 *BP, int64_t *m_dev,
+                            uint64_t *AQ, void *ws, cudaStream_t s, Stages *st) {
+    unsigned *err = err_word_ptr();
+    if (!err) return cudaErrorUnknown;
+    cudaError_t e = cudaMemsetAsync(BP, 0, (size_t)bitmap_entries(n) * sizeof(uint2), s);
+    if (e != cudaSuccess) return e;
+    const DevInfo di = dev_info();
+    const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(cdiv(q, 4), kT), (int64_t)di.sms * 8));
+    k_mark_endpoints<<<(unsigned)ctas, kT, 0, s>>>(l, r, q, n, reinterpret_cast<uint32_t *>(BP), err);
+    note_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (st) st->mark(s);
+    return bitmap_ranks(BP, n, m_dev, AQ, static_cast<uint32_t *>(ws), s);
+}
+
+size_t contract_workspace_bytes(int64_t n) {
+    return align256(bitmap_entries(n) * sizeof(uint2)) + align256(8) + bitmap_aux_bytes(n);
+}
+
+cudaError_t contract(const int32_t *A, int64_t n, const uint32_t *P, const int64_t *m_dev, int64_t m_max,
+                     uint64_t *AQ, void *ws, cudaStream_t s) {
+    // P -> bitmap -> ranks, then the same contraction as the batch path
+    Carver c{static_cast<char *>(ws)};
+    uint2 *BP = c.take<uint2>(bitmap_entries(n));
+    int64_t *m2 = c.take<int64_t>(1);
+    uint32_t *aux = reinterpret_cast<uint32_t *>(c.p + c.used);
+    cudaError_t e = cudaMemsetAsync(BP, 0, (size_t)bitmap_entries(n) * sizeof(uint2), s);
+    if (e != cudaSuccess) return e;
+    const DevInfo di = dev_info();
+    const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(std::max<int64_t>(m_max, 1), kT), (int64_t)di.sms * 8));
+    k_mark_positions<<<(unsigned)ctas, kT, 0, s>>>(P, m_dev, reinterpret_cast<uint32_t *>(BP));
+    note_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = bitmap_ranks(BP, n, m2, AQ, aux, s)) != cudaSuccess) return e;
+    return contract_bitmap(A, n, BP, m2, AQ, s);
+}
+
 size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con) {
-    const int64_t cnt = 2 * q;
-    const int64_t mq_max = std::max<int64_t>(cnt - 1, 1);
+    const int64_t mq_max = std::max<int64_t>(std::min<int64_t>(2 * q, n) - 1, 1);
     const int64_t nbq = cdiv(mq_max, 1ll << logk_con);
     const int64_t lv = coarse_geom(nbq).lc + 1;
     size_t b = 0;
-    b += align256(cnt * 4) * 2;                       // sorted endpoints
-    b += align256(cnt * 4);                           // P
+    b += align256(bitmap_entries(n) * sizeof(uint2));  // endpoint bitmap with rank counts
     b += align256(8);                                 // m
-    b += align256(q * 4) * 2;                         // ranks
     b += align256(mq_max * 8);                        // A_Q
     b += align256(nbq * lv * 8);                      // table over A_Q
     b += align256(kCoarseCap * 8);                    // its coarse summary
     b += align256(query_residual_bytes(q, dev_info().sms));  // residual list of the query
-    b += std::max({sort_workspace_bytes(q), rank_workspace_bytes(q), contract_workspace_bytes(n)});
+    b += bitmap_aux_bytes(n);
     return b;
 }
 
 cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q,
                            int32_t *out, int logk_con, void *ws, cudaStream_t s, Stages *st) {
-    const int64_t cnt = 2 * q;
-    const int64_t mq_max = std::max<int64_t>(cnt - 1, 1);
+    const int64_t mq_max = std::max<int64_t>(std::min<int64_t>(2 * q, n) - 1, 1);
     const int64_t nbq = cdiv(mq_max, 1ll << logk_con);
     const int64_t lv = coarse_geom(nbq).lc + 1;
     Carver c{static_cast<char *>(ws)};
-    uint32_t *sk = c.take<uint32_t>(cnt), *sv = c.take<uint32_t>(cnt);
-    uint32_t *P = c.take<uint32_t>(cnt);
+    uint2 *BP = c.take<uint2>(bitmap_entries(n));
     int64_t *m_dev = c.take<int64_t>(1);
-    int32_t *ra = c.take<int32_t>(q), *rb = c.take<int32_t>(q);
     uint64_t *AQ = c.take<uint64_t>(mq_max);
     uint64_t *T = c.take<uint64_t>(nbq * lv);
     uint64_t *Cs = c.take<uint64_t>(kCoarseCap);
     char *resw = c.take<char>(query_residual_bytes(q, dev_info().sms));
-    void *scratch = c.p + c.used;
+    uint32_t *aux = reinterpret_cast<uint32_t *>(c.p + c.used);
     cudaError_t e;
     Stages none;
     if (!st) st = &none;
+    const DevInfo di = dev_info();
     st->mark(s);
-    if ((e = sort_endpoints(l, r, q, n, sk, sv, scratch, 0, s)) != cudaSuccess) return e;                 // step 1
+    // step 1: the endpoint bitmap (marks), then the rank counts
+    if ((e = endpoint_bitmap(l, r, q, n, BP, m_dev, AQ, aux, s, st)) != cudaSuccess) return e;
     st->mark(s);
-    if ((e = rank_endpoints(sk, sv, q, P, m_dev, ra, rb, scratch, s)) != cudaSuccess) return e;           // step 1
-    st->mark(s);
-    if ((e = contract(A, n, P, m_dev, AQ, scratch, s)) != cudaSuccess) return e;                          // step 2
+    if ((e = contract_bitmap(A, n, BP, m_dev, AQ, s)) != cudaSuccess) return e;                            // step 2
     st->mark(s);
     const Len lenq{0, m_dev};
     if ((e = launch_block_minima_u64(AQ, lenq, mq_max, logk_con, T, s)) != cudaSuccess) return e;         // step 3
     if ((e = launch_sparse_table(T, lenq, logk_con, nbq, s, Cs)) != cudaSuccess) return e;                // step 3
     st->mark(s);
-    const DevInfo di = dev_info();
     const bool vecq = ((reinterpret_cast<uintptr_t>(l) | reinterpret_cast<uintptr_t>(r) |
                         reinterpret_cast<uintptr_t>(out)) & 15) == 0;
     SrcU64 src{AQ};
     const ResidualPlan rp = residual_plan(q, di.sms);                                                    // step 4
     Residual *res = reinterpret_cast<Residual *>(resw);
     if (vecq)
-        k_query_two<SrcU64, true, true, true><<<(unsigned)rp.ctas, kT, 0, s>>>(src, lenq, logk_con, T, Cs, l, r, ra, rb, n, out, q, res, rp.region, nullptr);
+        k_query_two<SrcU64, true, true, true><<<(unsigned)rp.ctas, kT, 0, s>>>(src, lenq, logk_con, T, Cs, l, r, BP, n, out, q, res, rp.region, nullptr);
     else
-        k_query_two<SrcU64, true, false, true><<<(unsigned)rp.ctas, kT, 0, s>>>(src, lenq, logk_con, T, Cs, l, r, ra, rb, n, out, q, res, rp.region, nullptr);
+        k_query_two<SrcU64, true, false, true><<<(unsigned)rp.ctas, kT, 0, s>>>(src, lenq, logk_con, T, Cs, l, r, BP, n, out, q, res, rp.region, nullptr);
     note_launches(1);
     e = cudaGetLastError();
     st->mark(s);

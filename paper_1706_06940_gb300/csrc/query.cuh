@@ -178,16 +178,12 @@ __device__ __forceinline__ void load_coarse(uint64_t *cs, const uint64_t *__rest
 // shared memory; then every thread takes 4 queries at a time (16-byte loads
 // of l and r when aligned): coarse resolution from shared memory, block-table
 // lookups only for the parts the coarse level leaves open, and finally the
-// warp-cooperative partial-block scans.
-//   plain (CON = false): the source is A; query i covers [l_i, r_i].
-//   contracted (CON = true): the source is A_Q; query i covers
-//     A_Q[a_i .. b_i - 1] with a_i = RL[i], b_i = RR[i]; a_i == b_i means
-//     l_i == r_i and the answer is l_i.
-template <class Src, bool CON, bool VECQ, bool VEC>
+// warp-cooperative partial-block scans.  Plain form: the source is A and
+// query i covers [l_i, r_i].
+template <class Src, bool VECQ, bool VEC>
 __global__ void __launch_bounds__(256) k_query(Src src, Len len, int logk, const uint64_t *__restrict__ T,
                                                 const uint64_t *__restrict__ Cs, const int32_t *__restrict__ L,
-                                                const int32_t *__restrict__ R, const int32_t *__restrict__ RL,
-                                                const int32_t *__restrict__ RR, int64_t n_a,
+                                                const int32_t *__restrict__ R, int64_t n_a,
                                                 int32_t *__restrict__ out, int64_t q, unsigned *err) {
     __shared__ uint64_t cs[kCoarseCap];
     const int64_t n = len.get();
@@ -201,19 +197,13 @@ __global__ void __launch_bounds__(256) k_query(Src src, Len len, int logk, const
     for (int64_t wb = warp * 128; wb < q; wb += nwarps * 128) {
         const int64_t base = wb + lane * 4;
         const bool full = VECQ && base + 3 < q;
-        int32_t lq[4], rq[4], aq[4], bq[4];
+        int32_t lq[4], rq[4];
         bool present[4];
         if (full) {
             const int4 x0 = __ldcs(reinterpret_cast<const int4 *>(L + base));
             const int4 x1 = __ldcs(reinterpret_cast<const int4 *>(R + base));
             lq[0] = x0.x; lq[1] = x0.y; lq[2] = x0.z; lq[3] = x0.w;
             rq[0] = x1.x; rq[1] = x1.y; rq[2] = x1.z; rq[3] = x1.w;
-            if (CON) {
-                const int4 x2 = __ldcs(reinterpret_cast<const int4 *>(RL + base));
-                const int4 x3 = __ldcs(reinterpret_cast<const int4 *>(RR + base));
-                aq[0] = x2.x; aq[1] = x2.y; aq[2] = x2.z; aq[3] = x2.w;
-                bq[0] = x3.x; bq[1] = x3.y; bq[2] = x3.z; bq[3] = x3.w;
-            }
 #pragma unroll
             for (int i = 0; i < 4; ++i) present[i] = true;
         } else {
@@ -222,10 +212,6 @@ __global__ void __launch_bounds__(256) k_query(Src src, Len len, int logk, const
                 present[i] = base + i < q;
                 lq[i] = present[i] ? __ldcs(L + base + i) : 0;
                 rq[i] = present[i] ? __ldcs(R + base + i) : 0;
-                if (CON) {
-                    aq[i] = present[i] ? __ldcs(RL + base + i) : 0;
-                    bq[i] = present[i] ? __ldcs(RR + base + i) : 0;
-                }
             }
         }
         uint64_t best[4];
@@ -238,9 +224,8 @@ __global__ void __launch_bounds__(256) k_query(Src src, Len len, int logk, const
             bad |= present[i] && !ok[i];
             hl[i] = hr[i] = false;
             best[i] = KEY_MAX;
-            const int64_t lo = CON ? aq[i] : lq[i];
-            const int64_t hi = CON ? (int64_t)bq[i] - 1 : rq[i];
-            if (!ok[i] || hi < lo) continue;
+            const int64_t lo = lq[i], hi = rq[i];
+            if (!ok[i]) continue;
             const uint32_t la = (uint32_t)lq[i], ra = (uint32_t)rq[i];
             int sub;
             best[i] = resolve_coarse(cs, g, logk, (uint32_t)lo, (uint32_t)hi, la, ra, sub);
@@ -275,8 +260,7 @@ __global__ void __launch_bounds__(256) k_query(Src src, Len len, int logk, const
         int32_t o[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const bool single = CON && ok[i] && aq[i] >= bq[i];
-            o[i] = !ok[i] ? -1 : (single ? lq[i] : (int32_t)key_pos(best[i]));
+            o[i] = ok[i] ? (int32_t)key_pos(best[i]) : -1;
         }
         if (full) {
             __stcs(reinterpret_cast<int4 *>(out + base), make_int4(o[0], o[1], o[2], o[3]));
@@ -285,7 +269,7 @@ __global__ void __launch_bounds__(256) k_query(Src src, Len len, int logk, const
             for (int i = 0; i < 4; ++i)
                 if (present[i]) out[base + i] = o[i];
         }
-        if (!CON && bad && err) atomicOr(err, ERR_QUERY_RANGE);
+        if (bad && err) atomicOr(err, ERR_QUERY_RANGE);
     }
 }
 
@@ -312,11 +296,24 @@ __device__ __forceinline__ bool coarse_span_min(const uint64_t *cs, const Coarse
     return p >= la && p <= ra;
 }
 
+// Rank of a marked position p in the endpoint bitmap: the number of distinct
+// endpoint positions below p, i.e. the index of p in the sorted list P.
+// BP[w].x is bit word w (bit b set: position 32w + b is an endpoint) and
+// BP[w].y the number of set bits in the words before w.
+__device__ __forceinline__ uint32_t bitmap_rank(const uint2 *__restrict__ BP, uint32_t p) {
+    const uint2 e = __ldg(BP + (p >> 5));
+    return e.y + __popc(e.x & ((1u << (p & 31)) - 1u));
+}
+
+//   plain (CON = false): the source is A; query i covers [l_i, r_i].
+//   contracted (CON = true): the source is A_Q; query i covers
+//     A_Q[a_i .. b_i - 1] with a_i, b_i the ranks of l_i, r_i in the
+//     endpoint bitmap BP; a_i == b_i means l_i == r_i and the answer is l_i.
 template <class Src, bool CON, bool VECQ, bool VEC>
 __global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk, const uint64_t *__restrict__ T,
                                                     const uint64_t *__restrict__ Cs,
                                                     const int32_t *__restrict__ L, const int32_t *__restrict__ R,
-                                                    const int32_t *__restrict__ RL, const int32_t *__restrict__ RR,
+                                                    const uint2 *__restrict__ BP,
                                                     int64_t n_a, int32_t *__restrict__ out, int64_t q,
                                                     Residual *__restrict__ res, int64_t region, unsigned *err) {
     // Phase A: each CTA answers the queries the coarse table settles and
@@ -336,32 +333,24 @@ __global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    // the next step's l, r (and ranks) are loaded before the current step is
-    // processed, so every warp keeps a batch of loads in flight
+    // the next step's l, r are loaded before the current step is processed, so
+    // every warp keeps a batch of loads in flight
     const int64_t stride = nwarps * 128;
-    int4 p0 = make_int4(0, 0, 0, 0), p1 = p0, p2 = p0, p3 = p0;
+    int4 p0 = make_int4(0, 0, 0, 0), p1 = p0;
     auto fetch = [&](int64_t b) {
         if (VECQ && b + 3 < q) {
             p0 = __ldcs(reinterpret_cast<const int4 *>(L + b));
             p1 = __ldcs(reinterpret_cast<const int4 *>(R + b));
-            if (CON) {
-                p2 = __ldcs(reinterpret_cast<const int4 *>(RL + b));
-                p3 = __ldcs(reinterpret_cast<const int4 *>(RR + b));
-            }
         }
     };
     fetch(warp * 128 + lane * 4);
     for (int64_t wb = warp * 128; wb < q; wb += stride) {
         const int64_t base = wb + lane * 4;
         const bool full = VECQ && base + 3 < q;
-        int32_t lq[4], rq[4], aq[4], bq[4];
+        int32_t lq[4], rq[4];
         if (full) {
             lq[0] = p0.x; lq[1] = p0.y; lq[2] = p0.z; lq[3] = p0.w;
             rq[0] = p1.x; rq[1] = p1.y; rq[2] = p1.z; rq[3] = p1.w;
-            if (CON) {
-                aq[0] = p2.x; aq[1] = p2.y; aq[2] = p2.z; aq[3] = p2.w;
-                bq[0] = p3.x; bq[1] = p3.y; bq[2] = p3.z; bq[3] = p3.w;
-            }
         }
         fetch(base + stride);
         if (!full) {
@@ -370,20 +359,26 @@ __global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk
                 const bool p = base + i < q;
                 lq[i] = p ? __ldcs(L + base + i) : 0;
                 rq[i] = p ? __ldcs(R + base + i) : -1;   // absent: reads as invalid
-                if (CON) {
-                    aq[i] = p ? __ldcs(RL + base + i) : 0;
-                    bq[i] = p ? __ldcs(RR + base + i) : 0;
-                }
+            }
+        }
+        const int32_t na = (int32_t)n_a;
+        bool okq[4];
+        int32_t aq[4], bq[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            okq[i] = lq[i] >= 0 && rq[i] >= lq[i] && rq[i] < na;
+            if (CON) {   // ranks of the ends (an invalid query reads position 0)
+                aq[i] = (int32_t)bitmap_rank(BP, okq[i] ? (uint32_t)lq[i] : 0u);
+                bq[i] = (int32_t)bitmap_rank(BP, okq[i] ? (uint32_t)rq[i] : 0u);
             }
         }
         int32_t o[4];
         unsigned need = 0;
         bool bad = false;
-        const int32_t na = (int32_t)n_a;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const bool present = full || base + i < q;
-            const bool ok = present && lq[i] >= 0 && rq[i] >= lq[i] && rq[i] < na;
+            const bool ok = present && okq[i];
             bad |= present && !ok;
             const bool single = CON && ok && aq[i] >= bq[i];          // contracted l == r
             // straight-line: an invalid or single query reads block 0 harmlessly
@@ -433,8 +428,8 @@ __global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk
         if (has) {
             qid = my[idx];
             const int32_t l = L[qid], r = R[qid];
-            const int64_t lo = CON ? RL[qid] : l;
-            const int64_t hi = CON ? (int64_t)RR[qid] - 1 : r;
+            const int64_t lo = CON ? (int64_t)bitmap_rank(BP, (uint32_t)l) : l;
+            const int64_t hi = CON ? (int64_t)bitmap_rank(BP, (uint32_t)r) - 1 : r;
             int sub;
             best = resolve_coarse(cs, g, logk, (uint32_t)lo, (uint32_t)hi, (uint32_t)l, (uint32_t)r, sub);
             if (sub == SUB_WHOLE) {

@@ -105,6 +105,7 @@ _SIGS = {
     "rmq_sort_endpoints": (_i32, [_vp, _vp, _i64, _i64, _vp, _vp, _vp]),
     "rmq_rank_endpoints": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]),
     "rmq_contract": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, _vp]),
+    "rmq_endpoint_bitmap": (_i32, [_vp, _vp, _i64, _i64, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -416,6 +417,13 @@ def rmq_sort_endpoints(l, r, n, pos_out, tag_out, stream=None):
 def rmq_rank_endpoints(pos_sorted, tag_sorted, q, P_out, m_dev, rank_l, rank_r, stream=None):
     _check(load().rmq_rank_endpoints(_dptr(pos_sorted), _dptr(tag_sorted), int(q), _dptr(P_out),
                                      _dptr(m_dev), _dptr(rank_l), _dptr(rank_r), _stream(stream, pos_sorted)))
+
+
+def rmq_endpoint_bitmap(l, r, n, BP, m_dev, stream=None):
+    """BP: int32/uint32 tensor of 2 * (ceil(n / 32) + 1) words (pairs: bit word,
+    set bits before it); m_dev: one int64 on the device."""
+    _check(load().rmq_endpoint_bitmap(_dptr(l, _i32t(), "l"), _dptr(r, _i32t(), "r"), l.numel(), int(n),
+                                      _dptr(BP, None, "BP"), _dptr(m_dev, None, "m_dev"), _stream(stream, l)))
 
 
 def rmq_contract(A, P, m_dev, m_max, AQ, stream=None):

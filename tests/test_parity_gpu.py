@@ -237,7 +237,63 @@ def test_a5_rank_endpoints(R, n, q):
     assert np.array_equal(rb.cpu().numpy(), rb_want)
 
 
+def bitmap_ranks_host(BP, pos):
+    """Rank of each position from the (word, count) pairs: count + popcount
+    of the word's bits below the position."""
+    w = BP[0::2].view(np.uint32)
+    c = BP[1::2].view(np.uint32).astype(np.int64)
+    idx = pos >> 5
+    below = w[idx] & ((np.uint32(1) << (pos & 31).astype(np.uint32)) - np.uint32(1))
+    pc = np.array([bin(int(x)).count("1") for x in below], dtype=np.int64)
+    return c[idx] + pc
+
+
+@pytest.mark.parametrize("n,q", [(1, 3), (33, 1000), (1024, 5000), (100_000, 1), (100_000, 9_999),
+                                 (1_000_003, 70_000), (2**27 + 3, 5000)])
+def test_a4_a5_endpoint_bitmap(R, n, q):
+    """The batch path's step 1: the set bits are the oracle's P, the rank of
+    every endpoint is the oracle's rank, and m is the number of distinct
+    positions."""
+    l, r = W.uniform_queries(n, q, 11 * q + n)
+    l[: q // 10] = r[: q // 10]
+    nbp = -(-n // 32) + 1
+    BP = torch.full((2 * nbp,), -1, dtype=torch.int32, device=DEV)
+    m = torch.zeros(1, dtype=torch.int64, device=DEV)
+    R.rmq_endpoint_bitmap(dev(l), dev(r), n, BP, m)
+    torch.cuda.synchronize()
+    assert R.rmq_stream_status() == R.Status.OK
+    bp = BP.cpu().numpy()
+    wp, wt = oracle.sort_endpoints(l, r)
+    P_want, ra_want, rb_want = oracle.rank_endpoints(wp, wt, q)
+    bits = np.unpackbits(np.ascontiguousarray(bp[0::2]).view(np.uint8), bitorder="little")
+    assert np.array_equal(np.nonzero(bits)[0].astype(np.uint32), P_want)
+    assert int(m.item()) == len(P_want) and bp[-1] == len(P_want) and bp[-2] == 0
+    assert np.array_equal(bitmap_ranks_host(bp, l.astype(np.int64)), ra_want)
+    assert np.array_equal(bitmap_ranks_host(bp, r.astype(np.int64)), rb_want)
+
+
+def test_a4_endpoint_bitmap_invalid_queries_mark_zero(R):
+    n, q = 10_000, 300
+    l, r = W.uniform_queries(n, q, 99)
+    l[5], r[5] = 7, 3            # l > r
+    r[9] = n                     # r out of range
+    nbp = -(-n // 32) + 1
+    BP = torch.zeros(2 * nbp, dtype=torch.int32, device=DEV)
+    m = torch.zeros(1, dtype=torch.int64, device=DEV)
+    R.rmq_endpoint_bitmap(dev(l), dev(r), n, BP, m)
+    torch.cuda.synchronize()
+    assert R.rmq_stream_status() == R.Status.ERR_QUERY_RANGE
+    wl, wr = l.copy(), r.copy()
+    wl[[5, 9]] = 0
+    wr[[5, 9]] = 0
+    P_want = np.unique(np.concatenate([wl, wr])).astype(np.uint32)
+    bits = np.unpackbits(np.ascontiguousarray(BP.cpu().numpy()[0::2]).view(np.uint8), bitorder="little")
+    assert np.array_equal(np.nonzero(bits)[0].astype(np.uint32), P_want)
+    assert int(m.item()) == len(P_want)
+
+
 @pytest.mark.parametrize("n,q,hi", [(5, 2, 3), (1000, 1, 5), (5000, 3, 5), (100_000, 50_000, 1000),
+                                    (3000, 10_000, 5), (70_000, 1, 2**31),
                                     (1_000_003, 2_000, 2**31), (1_000_003, 300_000, 3),
                                     (2_000_000, 20, 2**31)])
 @pytest.mark.parametrize("offset", [0, 1])
