@@ -456,13 +456,38 @@ __device__ __forceinline__ void emit_atomic(uint64_t *H, int64_t s, uint64_t v) 
 // then stored to A_Q in order (coalesced).  Only the first segment (begun in
 // an earlier tile) and the one left open at the end are combined with
 // atomics (those entries were set to KEY_MAX by k_bits_final).
+// With T0 given, the kernel also folds every segment value into level 0 of
+// the block table over A_Q (Sec. 3.1 step 3: T0[j] = min of A_Q over block j
+// of 2^logk_q entries) with one atomicMin per block and 32 slots; T0 starts
+// at KEY_MAX.  Partial values of a straddling segment fold in as well, which
+// leaves the minimum unchanged.
 __device__ __forceinline__ int swz(int x) { return (x & ~7) | ((x & 7) ^ ((x >> 3) & 7)); }
 
 constexpr int kContractSmem = (kT / 32) * kATile * 8;   // per warp: the tile, then its slots
 
+// Folds key v of A_Q entry sg into T0[sg >> logk_q], for the lanes with
+// `has`.  Called by the whole warp; the lanes' blocks are non-decreasing, and
+// each distinct block costs two 32-bit warp reductions and one atomic.
+__device__ __forceinline__ void fold_block_min(uint64_t *T0, int logk_q, bool has, int64_t sg, uint64_t v) {
+    const uint32_t blk = has ? (uint32_t)(sg >> logk_q) : 0u;
+    const uint32_t hi = (uint32_t)(v >> 32), lo = (uint32_t)v;
+    unsigned rest = __ballot_sync(0xffffffffu, has);
+    while (rest) {
+        const int leader = __ffs(rest) - 1;
+        const uint32_t b = __shfl_sync(0xffffffffu, blk, leader);
+        const bool in = has && blk == b;
+        rest &= ~__ballot_sync(0xffffffffu, in);
+        const uint32_t mh = __reduce_min_sync(0xffffffffu, in ? hi : 0xffffffffu);
+        const uint32_t ml = __reduce_min_sync(0xffffffffu, in && hi == mh ? lo : 0xffffffffu);
+        if ((threadIdx.x & 31) == leader)
+            atomicMin(reinterpret_cast<unsigned long long *>(T0) + b, ((unsigned long long)mh << 32) | ml);
+    }
+}
+
 template <bool VEC>
 __global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const uint2 *__restrict__ BP,
-                                                 const int64_t *m_dev, int64_t ntA, uint64_t *__restrict__ H) {
+                                                 const int64_t *m_dev, int64_t ntA, uint64_t *__restrict__ H,
+                                                 uint64_t *__restrict__ T0, int logk_q) {
     extern __shared__ uint64_t csmem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint64_t *slot = csmem + (size_t)w * kATile;                      // 1024 slots per warp
@@ -507,7 +532,10 @@ __global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const ui
                                        kmin(make_key(v[u].z, c + 2), make_key(v[u].w, c + 3))));
             }
             best = warp_min(best);
-            if (lane == 0) emit_atomic(H, s_t, best);
+            if (lane == 0) {
+                emit_atomic(H, s_t, best);
+                if (T0) atomicMin(reinterpret_cast<unsigned long long *>(T0) + (s_t >> logk_q), (unsigned long long)best);
+            }
             continue;
         }
         __syncwarp();  // the previous tile's slots are no longer read
@@ -558,13 +586,21 @@ __global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const ui
         if (nbits) slot[pre] = kmin(slot[pre], carry_in);
         const uint64_t tail = __shfl_sync(0xffffffffu, val, 31);
         __syncwarp();
-        for (uint32_t b = lane; b < cnt; b += 32) {
+        for (uint32_t b0 = 0; b0 < cnt; b0 += 32) {
+            const uint32_t b = b0 + lane;
             const int64_t sg = s_t + b;
-            if (sg < 0 || sg > m - 2) continue;
-            if (b == 0) emit_atomic(H, sg, slot[0]);
-            else H[sg] = slot[b];
+            const bool has = b < cnt && sg >= 0 && sg <= m - 2;
+            const uint64_t v = has ? slot[b] : KEY_MAX;
+            if (has) {
+                if (b == 0) emit_atomic(H, sg, v);
+                else st_stream_u64(H + sg, v);
+            }
+            if (T0) fold_block_min(T0, logk_q, has, sg, v);
         }
-        if (lane == 0 && s_n >= 0 && s_n <= m - 2) emit_atomic(H, s_n, tail);
+        if (lane == 0 && s_n >= 0 && s_n <= m - 2) {
+            emit_atomic(H, s_n, tail);
+            if (T0) atomicMin(reinterpret_cast<unsigned long long *>(T0) + (s_n >> logk_q), (unsigned long long)tail);
+        }
     }
 }
 
@@ -672,7 +708,7 @@ cudaError_t bitmap_ranks(uint2 *BP, int64_t n, int64_t *m_dev, uint64_t *AQ, uin
 size_t bitmap_aux_bytes(int64_t n) { return align256(cdiv(bitmap_entries(n), kTile) * 4); }
 
 cudaError_t contract_bitmap(const int32_t *A, int64_t n, const uint2 *BP, const int64_t *m_dev, uint64_t *AQ,
-                            cudaStream_t s) {
+                            uint64_t *T0, int logk_q, cudaStream_t s) {
     const int64_t ntA = cdiv(n, kATile);
     const DevInfo di = dev_info();
     const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(ntA, kT / 32), (int64_t)di.sms * 3));
@@ -684,9 +720,9 @@ cudaError_t contract_bitmap(const int32_t *A, int64_t n, const uint2 *BP, const 
         attr[di.device] = true;
     }
     if ((reinterpret_cast<uintptr_t>(A) & 15) == 0)
-        k_contract<true><<<(unsigned)ctas, kT, kContractSmem, s>>>(src, n, BP, m_dev, ntA, AQ);
+        k_contract<true><<<(unsigned)ctas, kT, kContractSmem, s>>>(src, n, BP, m_dev, ntA, AQ, T0, logk_q);
     else
-        k_contract<false><<<(unsigned)ctas, kT, kContractSmem, s>>>(src, n, BP, m_dev, ntA, AQ);
+        k_contract<false><<<(unsigned)ctas, kT, kContractSmem, s>>>(src, n, BP, m_dev, ntA, AQ, T0, logk_q);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -729,7 +765,7 @@ cudaError_t contract(const int32_t *A, int64_t n, const uint32_t *P, const int64
     note_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = bitmap_ranks(BP, n, m2, AQ, aux, s)) != cudaSuccess) return e;
-    return contract_bitmap(A, n, BP, m2, AQ, s);
+    return contract_bitmap(A, n, BP, m2, AQ, nullptr, 0, s);
 }
 
 size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con) {
@@ -742,7 +778,7 @@ size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con) {
     b += align256(mq_max * 8);                        // A_Q
     b += align256(nbq * lv * 8);                      // table over A_Q
     b += align256(kCoarseCap * 8);                    // its coarse summary
-    b += align256(query_residual_bytes(q, dev_info().sms));  // residual list of the query
+    b += align256(query_residual_bytes(q, dev_info().sms, kQueryCtasPerSmCon));  // residual list of the query
     b += bitmap_aux_bytes(n);
     return b;
 }
@@ -758,7 +794,7 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     uint64_t *AQ = c.take<uint64_t>(mq_max);
     uint64_t *T = c.take<uint64_t>(nbq * lv);
     uint64_t *Cs = c.take<uint64_t>(kCoarseCap);
-    char *resw = c.take<char>(query_residual_bytes(q, dev_info().sms));
+    char *resw = c.take<char>(query_residual_bytes(q, dev_info().sms, kQueryCtasPerSmCon));
     uint32_t *aux = reinterpret_cast<uint32_t *>(c.p + c.used);
     cudaError_t e;
     Stages none;
@@ -768,16 +804,17 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     // step 1: the endpoint bitmap (marks), then the rank counts
     if ((e = endpoint_bitmap(l, r, q, n, BP, m_dev, AQ, aux, s, st)) != cudaSuccess) return e;
     st->mark(s);
-    if ((e = contract_bitmap(A, n, BP, m_dev, AQ, s)) != cudaSuccess) return e;                            // step 2
+    // step 2, with level 0 of step 3 folded in
+    if ((e = cudaMemsetAsync(T, 0xff, (size_t)nbq * 8, s)) != cudaSuccess) return e;
+    if ((e = contract_bitmap(A, n, BP, m_dev, AQ, T, logk_con, s)) != cudaSuccess) return e;
     st->mark(s);
     const Len lenq{0, m_dev};
-    if ((e = launch_block_minima_u64(AQ, lenq, mq_max, logk_con, T, s)) != cudaSuccess) return e;         // step 3
     if ((e = launch_sparse_table(T, lenq, logk_con, nbq, s, Cs)) != cudaSuccess) return e;                // step 3
     st->mark(s);
     const bool vecq = ((reinterpret_cast<uintptr_t>(l) | reinterpret_cast<uintptr_t>(r) |
                         reinterpret_cast<uintptr_t>(out)) & 15) == 0;
     SrcU64 src{AQ};
-    const ResidualPlan rp = residual_plan(q, di.sms);                                                    // step 4
+    const ResidualPlan rp = residual_plan(q, di.sms, kQueryCtasPerSmCon);                                                    // step 4
     Residual *res = reinterpret_cast<Residual *>(resw);
     if (vecq)
         k_query_two<SrcU64, true, true, true><<<(unsigned)rp.ctas, kT, 0, s>>>(src, lenq, logk_con, T, Cs, l, r, BP, n, out, q, res, rp.region, nullptr);

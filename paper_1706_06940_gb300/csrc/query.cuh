@@ -310,7 +310,7 @@ __device__ __forceinline__ uint32_t bitmap_rank(const uint2 *__restrict__ BP, ui
 //     A_Q[a_i .. b_i - 1] with a_i, b_i the ranks of l_i, r_i in the
 //     endpoint bitmap BP; a_i == b_i means l_i == r_i and the answer is l_i.
 template <class Src, bool CON, bool VECQ, bool VEC>
-__global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk, const uint64_t *__restrict__ T,
+__global__ void __launch_bounds__(256, CON ? 3 : 4) k_query_two(Src src, Len len, int logk, const uint64_t *__restrict__ T,
                                                     const uint64_t *__restrict__ Cs,
                                                     const int32_t *__restrict__ L, const int32_t *__restrict__ R,
                                                     const uint2 *__restrict__ BP,
@@ -333,45 +333,62 @@ __global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    // the next step's l, r are loaded before the current step is processed, so
-    // every warp keeps a batch of loads in flight
+    // Phase A is software-pipelined over the warp's steps of 128 queries (4
+    // per lane): l, r of the step after next are in flight while a step is
+    // processed, and for the contracted form the bitmap entries that give the
+    // ranks of the next step are gathered one step ahead.
     const int64_t stride = nwarps * 128;
-    int4 p0 = make_int4(0, 0, 0, 0), p1 = p0;
-    auto fetch = [&](int64_t b) {
+    const int32_t na = (int32_t)n_a;
+    auto load_lr = [&](int64_t b, int4 &xl, int4 &xr) {
         if (VECQ && b + 3 < q) {
-            p0 = __ldcs(reinterpret_cast<const int4 *>(L + b));
-            p1 = __ldcs(reinterpret_cast<const int4 *>(R + b));
+            xl = __ldcs(reinterpret_cast<const int4 *>(L + b));
+            xr = __ldcs(reinterpret_cast<const int4 *>(R + b));
+        } else {   // ragged or absent: an absent query reads as invalid (r = -1)
+            xl.x = b < q ? __ldcs(L + b) : 0;         xr.x = b < q ? __ldcs(R + b) : -1;
+            xl.y = b + 1 < q ? __ldcs(L + b + 1) : 0; xr.y = b + 1 < q ? __ldcs(R + b + 1) : -1;
+            xl.z = b + 2 < q ? __ldcs(L + b + 2) : 0; xr.z = b + 2 < q ? __ldcs(R + b + 2) : -1;
+            xl.w = b + 3 < q ? __ldcs(L + b + 3) : 0; xr.w = b + 3 < q ? __ldcs(R + b + 3) : -1;
         }
     };
-    fetch(warp * 128 + lane * 4);
+    auto valid = [&](int32_t l, int32_t r) { return l >= 0 && r >= l && r < na; };
+    auto gather = [&](const int4 &xl, const int4 &xr, uint2 (&ge)[8]) {
+        if (!CON) return;
+        const int32_t ls[4] = {xl.x, xl.y, xl.z, xl.w}, rs[4] = {xr.x, xr.y, xr.z, xr.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {   // an invalid query reads position 0
+            const bool ok = valid(ls[i], rs[i]);
+            ge[2 * i] = __ldg(BP + ((ok ? (uint32_t)ls[i] : 0u) >> 5));
+            ge[2 * i + 1] = __ldg(BP + ((ok ? (uint32_t)rs[i] : 0u) >> 5));
+        }
+    };
+    int4 cl, cr, nl, nr;
+    uint2 cg[8], ng[8];
+    const int64_t first = warp * 128 + lane * 4;
+    load_lr(first, cl, cr);
+    load_lr(first + stride, nl, nr);
+    gather(cl, cr, cg);
     for (int64_t wb = warp * 128; wb < q; wb += stride) {
         const int64_t base = wb + lane * 4;
         const bool full = VECQ && base + 3 < q;
-        int32_t lq[4], rq[4];
-        if (full) {
-            lq[0] = p0.x; lq[1] = p0.y; lq[2] = p0.z; lq[3] = p0.w;
-            rq[0] = p1.x; rq[1] = p1.y; rq[2] = p1.z; rq[3] = p1.w;
-        }
-        fetch(base + stride);
-        if (!full) {
+        const int32_t lq[4] = {cl.x, cl.y, cl.z, cl.w}, rq[4] = {cr.x, cr.y, cr.z, cr.w};
+        int32_t aq[4], bq[4];
+        if (CON) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const bool p = base + i < q;
-                lq[i] = p ? __ldcs(L + base + i) : 0;
-                rq[i] = p ? __ldcs(R + base + i) : -1;   // absent: reads as invalid
+                const uint32_t pl = valid(lq[i], rq[i]) ? (uint32_t)lq[i] : 0u;
+                const uint32_t pr = valid(lq[i], rq[i]) ? (uint32_t)rq[i] : 0u;
+                aq[i] = (int32_t)(cg[2 * i].y + __popc(cg[2 * i].x & ((1u << (pl & 31)) - 1u)));
+                bq[i] = (int32_t)(cg[2 * i + 1].y + __popc(cg[2 * i + 1].x & ((1u << (pr & 31)) - 1u)));
             }
         }
-        const int32_t na = (int32_t)n_a;
+        // next step's gathers and the step after next's l, r go out now
+        if (wb + stride < q) gather(nl, nr, ng);
+        cl = nl;
+        cr = nr;
+        if (wb + 2 * stride < q) load_lr(base + 2 * stride, nl, nr);
         bool okq[4];
-        int32_t aq[4], bq[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            okq[i] = lq[i] >= 0 && rq[i] >= lq[i] && rq[i] < na;
-            if (CON) {   // ranks of the ends (an invalid query reads position 0)
-                aq[i] = (int32_t)bitmap_rank(BP, okq[i] ? (uint32_t)lq[i] : 0u);
-                bq[i] = (int32_t)bitmap_rank(BP, okq[i] ? (uint32_t)rq[i] : 0u);
-            }
-        }
+        for (int i = 0; i < 4; ++i) okq[i] = valid(lq[i], rq[i]);
         int32_t o[4];
         unsigned need = 0;
         bool bad = false;
@@ -414,6 +431,10 @@ __global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk
             if (need & 8u) my[sbase + c0 + c1 + c2 + __popc(b3 & lt)] = (uint32_t)(base + 3);
         }
         if (!CON && bad && err) atomicOr(err, ERR_QUERY_RANGE);
+        if (CON) {
+#pragma unroll
+            for (int x = 0; x < 8; ++x) cg[x] = ng[x];
+        }
     }
     __syncthreads();  // n_open is final and the region's entries are visible to the CTA
     const int64_t cnt = n_open;

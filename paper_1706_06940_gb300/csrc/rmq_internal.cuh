@@ -67,18 +67,31 @@ __host__ __device__ __forceinline__ Coarse coarse_geom(int64_t nb) {
     }
 }
 
-// Streaming 128-bit load that does not allocate in L1 (data read once).
+// L2 policy for data touched once: its lines are the first to be evicted,
+// so streams of A or A_Q do not push small resident structures (tables, the
+// endpoint bitmap) out of L2.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// Streaming 128-bit load: no L1 allocation, evict-first in L2 (read once).
 __device__ __forceinline__ int4 ld_stream_v4(const int4 *p) {
     int4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p), "l"(l2_evict_first()));
     return v;
 }
 __device__ __forceinline__ ulonglong2 ld_stream_v2u64(const ulonglong2 *p) {
     ulonglong2 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v2.u64 {%0,%1}, [%2];"
-                 : "=l"(v.x), "=l"(v.y) : "l"(p));
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u64 {%0,%1}, [%2], %3;"
+                 : "=l"(v.x), "=l"(v.y) : "l"(p), "l"(l2_evict_first()));
     return v;
+}
+// Store of data the next kernel streams once.
+__device__ __forceinline__ void st_stream_u64(uint64_t *p, uint64_t v) {
+    asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(l2_evict_first()) : "memory");
 }
 
 // ---------------------------------------------------------------- sources
@@ -180,18 +193,21 @@ struct ResidualPlan {
     int64_t ctas;    // phase-A CTAs
     int64_t region;  // entries per CTA region
 };
-inline ResidualPlan residual_plan(int64_t q, int sms) {
+// The contracted form's query gathers bitmap entries one step ahead and runs
+// kQueryCtasPerSmCon CTAs per SM (<= 85 registers).
+constexpr int kQueryCtasPerSmCon = 3;
+inline ResidualPlan residual_plan(int64_t q, int sms, int per_sm = kQueryCtasPerSm) {
     const int64_t batches = (q + 127) / 128;                     // 4 queries x 32 lanes per warp step
     int64_t ctas = (batches + 7) / 8;
-    const int64_t cap = (int64_t)sms * kQueryCtasPerSm;          // one wave: every CTA resident at once
+    const int64_t cap = (int64_t)sms * per_sm;                   // one wave: every CTA resident at once
     if (ctas > cap) ctas = cap;
     if (ctas < 1) ctas = 1;
     const int64_t warps = ctas * 8;
     const int64_t per_warp = (batches + warps - 1) / warps;       // warp steps per warp
     return ResidualPlan{ctas, per_warp * 8 * 128};
 }
-inline size_t query_residual_bytes(int64_t q, int sms) {
-    const ResidualPlan p = residual_plan(q, sms);
+inline size_t query_residual_bytes(int64_t q, int sms, int per_sm = kQueryCtasPerSm) {
+    const ResidualPlan p = residual_plan(q, sms, per_sm);
     return (size_t)(p.ctas * p.region) * 4;
 }
 cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint64_t *T, const uint64_t *Cs,
