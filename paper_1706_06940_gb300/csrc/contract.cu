@@ -396,9 +396,13 @@ __global__ void __launch_bounds__(kT) k_bits_partial(const uint2 *__restrict__ B
 // Also sets to KEY_MAX every A_Q entry that the contraction combines with
 // atomics: the segment open just before each tile of kATile cells (the
 // segment whose left end P_j lies below the tile, when j <= m - 2).
+// With CP given, also writes the coarse index of the query over A_Q with
+// blocks of 2^logk_q entries: CP (where each coarse block of A_Q begins) and
+// CB (the coarse block at each bucket start).
 __global__ void __launch_bounds__(kT) k_bits_final(uint2 *__restrict__ BP, int64_t nbp,
                                                    const uint32_t *__restrict__ partial, const int64_t *m_dev,
-                                                   int64_t ntA, uint64_t *__restrict__ AQ) {
+                                                   int64_t ntA, uint64_t *__restrict__ AQ, int64_t n, int logk_q,
+                                                   uint32_t *__restrict__ CP, uint16_t *__restrict__ CB) {
     __shared__ uint32_t wsum[kT / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)w * (32 * kIPT);
@@ -415,6 +419,14 @@ __global__ void __launch_bounds__(kT) k_bits_final(uint2 *__restrict__ BP, int64
     uint32_t run = block_excl_scan(lane == 0 ? s : 0u, wsum, total);
     run = __shfl_sync(0xffffffffu, run, 0) + partial[blockIdx.x];
     const int64_t m = *m_dev;
+    // coarse geometry of the table over A_Q (m - 1 entries)
+    const int64_t nbq = m >= 2 ? (m - 2 + (1ll << logk_q)) >> logk_q : 0;
+    const bool index = CP != nullptr && nbq > 0;
+    const Coarse g = coarse_geom(nbq > 0 ? nbq : 1);
+    const int sh = logk_q + g.lc;
+    const int bs = bucket_shift(n);
+    const int64_t nbk = bucket_count(n);
+    if (index && blockIdx.x == 0 && threadIdx.x == 0) CB[nbk] = (uint16_t)(g.nbc - 1);
 #pragma unroll
     for (int i = 0; i < kIPT; ++i) {
         uint32_t x = c[i];
@@ -430,6 +442,23 @@ __global__ void __launch_bounds__(kT) k_bits_final(uint2 *__restrict__ BP, int64
             if ((e & (kATile / 32 - 1)) == 0 && (e / (kATile / 32)) < ntA) {
                 const int64_t sg = (int64_t)ex - 1;
                 if (sg >= 0 && sg <= m - 2) AQ[sg] = KEY_MAX;
+            }
+            if (index && e < nbp - 1) {
+                const uint32_t word = BP[e].x;
+                // a coarse block of A_Q begins at the (j 2^sh)-th mark
+                const int64_t j = ((int64_t)ex + (1ll << sh) - 1) >> sh;
+                const int64_t t = (j << sh) - (int64_t)ex;
+                if (j < g.nbc && t < (int64_t)c[i]) {
+                    uint32_t w = word;
+                    for (int64_t d = 0; d < t; ++d) w &= w - 1u;   // drop the t lower marks
+                    CP[j] = (uint32_t)(e * 32 + __ffs(w) - 1);
+                }
+                // bucket start: the last coarse block that begins at or before it
+                if (((e << 5) & ((1ll << bs) - 1)) == 0) {
+                    const int64_t upto = (int64_t)ex + (word & 1u);   // marks <= 32e
+                    const int64_t cb = upto >= 1 ? (upto - 1) >> sh : 0;
+                    CB[(e << 5) >> bs] = (uint16_t)(cb < g.nbc - 1 ? cb : g.nbc - 1);
+                }
             }
         }
         run += __shfl_sync(0xffffffffu, x, 31);
@@ -695,12 +724,13 @@ namespace {
 // BP[w].y = set bits in words before w, *m_dev = all set bits; A_Q entries
 // that the contraction combines with atomics are set to KEY_MAX (AQ may be
 // null when no contraction follows).  aux: scan_aux_words(tiles) words.
-cudaError_t bitmap_ranks(uint2 *BP, int64_t n, int64_t *m_dev, uint64_t *AQ, uint32_t *aux, cudaStream_t s) {
+cudaError_t bitmap_ranks(uint2 *BP, int64_t n, int64_t *m_dev, uint64_t *AQ, uint32_t *aux, cudaStream_t s,
+                         int logk_q = 0, uint32_t *CP = nullptr, uint16_t *CB = nullptr) {
     const int64_t nbp = bitmap_entries(n);
     const int64_t tiles = cdiv(nbp, kTile);
     k_bits_partial<<<(unsigned)tiles, kT, 0, s>>>(BP, nbp, aux);
     k_scan_top<<<1, kT, 0, s>>>(aux, tiles, m_dev);   // tile counts scanned in place, total -> m
-    k_bits_final<<<(unsigned)tiles, kT, 0, s>>>(BP, nbp, aux, m_dev, AQ ? cdiv(n, kATile) : 0, AQ);
+    k_bits_final<<<(unsigned)tiles, kT, 0, s>>>(BP, nbp, aux, m_dev, AQ ? cdiv(n, kATile) : 0, AQ, n, logk_q, CP, CB);
     note_launches(3);
     return cudaGetLastError();
 }
@@ -732,7 +762,8 @@ cudaError_t contract_bitmap(const int32_t *A, int64_t n, const uint2 *BP, const 
 size_t endpoint_bitmap_workspace_bytes(int64_t n) { return bitmap_aux_bytes(n); }
 
 cudaError_t endpoint_bitmap(const int32_t *l, const int32_t *r, int64_t q, int64_t n, uint2 *BP, int64_t *m_dev,
-                            uint64_t *AQ, void *ws, cudaStream_t s, Stages *st) {
+                            uint64_t *AQ, void *ws, cudaStream_t s, Stages *st, int logk_q, uint32_t *CP,
+                            uint16_t *CB) {
     unsigned *err = err_word_ptr();
     if (!err) return cudaErrorUnknown;
     cudaError_t e = cudaMemsetAsync(BP, 0, (size_t)bitmap_entries(n) * sizeof(uint2), s);
@@ -743,7 +774,7 @@ cudaError_t endpoint_bitmap(const int32_t *l, const int32_t *r, int64_t q, int64
     note_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (st) st->mark(s);
-    return bitmap_ranks(BP, n, m_dev, AQ, static_cast<uint32_t *>(ws), s);
+    return bitmap_ranks(BP, n, m_dev, AQ, static_cast<uint32_t *>(ws), s, logk_q, CP, CB);
 }
 
 size_t contract_workspace_bytes(int64_t n) {
@@ -778,6 +809,7 @@ size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con) {
     b += align256(mq_max * 8);                        // A_Q
     b += align256(nbq * lv * 8);                      // table over A_Q
     b += align256(kCoarseCap * 8);                    // its coarse summary
+    b += align256(kCoarseBlocksMax * 4) + align256((kBucketsMax + 1) * 2);   // coarse index
     b += align256(query_residual_bytes(q, dev_info().sms, kQueryCtasPerSmCon));  // residual list of the query
     b += bitmap_aux_bytes(n);
     return b;
@@ -794,6 +826,8 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     uint64_t *AQ = c.take<uint64_t>(mq_max);
     uint64_t *T = c.take<uint64_t>(nbq * lv);
     uint64_t *Cs = c.take<uint64_t>(kCoarseCap);
+    uint32_t *CP = c.take<uint32_t>(kCoarseBlocksMax);
+    uint16_t *CB = c.take<uint16_t>(kBucketsMax + 1);
     char *resw = c.take<char>(query_residual_bytes(q, dev_info().sms, kQueryCtasPerSmCon));
     uint32_t *aux = reinterpret_cast<uint32_t *>(c.p + c.used);
     cudaError_t e;
@@ -802,7 +836,7 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     const DevInfo di = dev_info();
     st->mark(s);
     // step 1: the endpoint bitmap (marks), then the rank counts
-    if ((e = endpoint_bitmap(l, r, q, n, BP, m_dev, AQ, aux, s, st)) != cudaSuccess) return e;
+    if ((e = endpoint_bitmap(l, r, q, n, BP, m_dev, AQ, aux, s, st, logk_con, CP, CB)) != cudaSuccess) return e;
     st->mark(s);
     // step 2, with level 0 of step 3 folded in
     if ((e = cudaMemsetAsync(T, 0xff, (size_t)nbq * 8, s)) != cudaSuccess) return e;
@@ -817,9 +851,9 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     const ResidualPlan rp = residual_plan(q, di.sms, kQueryCtasPerSmCon);                                                    // step 4
     Residual *res = reinterpret_cast<Residual *>(resw);
     if (vecq)
-        k_query_two<SrcU64, true, true, true><<<(unsigned)rp.ctas, kT, 0, s>>>(src, lenq, logk_con, T, Cs, l, r, BP, n, out, q, res, rp.region, nullptr);
+        k_query_two<SrcU64, true, true, true><<<(unsigned)rp.ctas, kT, 0, s>>>(src, lenq, logk_con, T, Cs, l, r, BP, CP, CB, n, out, q, res, rp.region, nullptr);
     else
-        k_query_two<SrcU64, true, false, true><<<(unsigned)rp.ctas, kT, 0, s>>>(src, lenq, logk_con, T, Cs, l, r, BP, n, out, q, res, rp.region, nullptr);
+        k_query_two<SrcU64, true, false, true><<<(unsigned)rp.ctas, kT, 0, s>>>(src, lenq, logk_con, T, Cs, l, r, BP, CP, CB, n, out, q, res, rp.region, nullptr);
     note_launches(1);
     e = cudaGetLastError();
     st->mark(s);

@@ -282,18 +282,24 @@ __global__ void __launch_bounds__(256) k_query(Src src, Len len, int logk, const
 // An open query of the two-phase kernel: its index in the batch.
 typedef uint32_t Residual;
 
-// Phase A's test: the minimum over every coarse block the query touches,
+// Phase A's test: the minimum over the coarse blocks BL .. BR the query touches,
 // from two reads of the coarse table.  When its position lies inside the
 // query it is the answer; this settles most queries of a long batch.
-__device__ __forceinline__ bool coarse_span_min(const uint64_t *cs, const Coarse &g, int logk, uint32_t lo, uint32_t hi,
-                                                uint32_t la, uint32_t ra, uint64_t &m) {
-    const int sh = logk + g.lc;
-    const uint32_t BL = lo >> sh, BR = hi >> sh;
+__device__ __forceinline__ bool coarse_blocks_min(const uint64_t *cs, const Coarse &g, uint32_t BL, uint32_t BR,
+                                                  uint32_t la, uint32_t ra, uint64_t &m) {
     const int t = 31 - __clz((int)(BR - BL + 1));
     const uint64_t *row = cs + (uint32_t)t * (uint32_t)g.nbc;
     m = kmin(row[BL], row[BR + 1 - (1u << t)]);
     const uint32_t p = key_pos(m);
     return p >= la && p <= ra;
+}
+
+// The same test for a range [lo, hi] of the source, its coarse blocks taken
+// from the indices.
+__device__ __forceinline__ bool coarse_span_min(const uint64_t *cs, const Coarse &g, int logk, uint32_t lo, uint32_t hi,
+                                                uint32_t la, uint32_t ra, uint64_t &m) {
+    const int sh = logk + g.lc;
+    return coarse_blocks_min(cs, g, lo >> sh, hi >> sh, la, ra, m);
 }
 
 // Rank of a marked position p in the endpoint bitmap: the number of distinct
@@ -305,15 +311,33 @@ __device__ __forceinline__ uint32_t bitmap_rank(const uint2 *__restrict__ BP, ui
     return e.y + __popc(e.x & ((1u << (p & 31)) - 1u));
 }
 
+// Coarse block of A_Q holding the A_Q entry that begins at the last mark
+// <= p (p >= P_0): the last j with CP[j] <= p, searched between the bucket
+// bounds CB[p >> bs] and CB[(p >> bs) + 1] (usually equal or adjacent).
+__device__ __forceinline__ uint32_t coarse_of(const uint32_t *cp, const uint16_t *cb, int bs, uint32_t p) {
+    const uint32_t i = p >> bs;
+    uint32_t lo = cb[i], hi = cb[i + 1];
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (cp[mid] <= p) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 //   plain (CON = false): the source is A; query i covers [l_i, r_i].
 //   contracted (CON = true): the source is A_Q; query i covers
 //     A_Q[a_i .. b_i - 1] with a_i, b_i the ranks of l_i, r_i in the
 //     endpoint bitmap BP; a_i == b_i means l_i == r_i and the answer is l_i.
+//     Phase A needs only the coarse blocks of a_i and b_i - 1, which the
+//     coarse index (CP, CB) gives from l_i and r_i - 1; the ranks themselves
+//     are looked up in BP for the queries left to phase B.
 template <class Src, bool CON, bool VECQ, bool VEC>
-__global__ void __launch_bounds__(256, CON ? 3 : 4) k_query_two(Src src, Len len, int logk, const uint64_t *__restrict__ T,
+__global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk, const uint64_t *__restrict__ T,
                                                     const uint64_t *__restrict__ Cs,
                                                     const int32_t *__restrict__ L, const int32_t *__restrict__ R,
-                                                    const uint2 *__restrict__ BP,
+                                                    const uint2 *__restrict__ BP, const uint32_t *__restrict__ CP,
+                                                    const uint16_t *__restrict__ CB,
                                                     int64_t n_a, int32_t *__restrict__ out, int64_t q,
                                                     Residual *__restrict__ res, int64_t region, unsigned *err) {
     // Phase A: each CTA answers the queries the coarse table settles and
@@ -322,6 +346,8 @@ __global__ void __launch_bounds__(256, CON ? 3 : 4) k_query_two(Src src, Len len
     // CTA then finishes its residual queries, with the coarse table still in
     // shared memory.
     __shared__ uint64_t cs[kCoarseCap];
+    __shared__ uint32_t cp[CON ? kCoarseBlocksMax : 1];
+    __shared__ uint16_t cb[CON ? kBucketsMax : 1];
     __shared__ uint32_t n_open;
     if (threadIdx.x == 0) n_open = 0;
     Residual *my = res + (int64_t)blockIdx.x * region;
@@ -329,81 +355,67 @@ __global__ void __launch_bounds__(256, CON ? 3 : 4) k_query_two(Src src, Len len
     const int64_t nb = (n + (1ll << logk) - 1) >> logk;
     const Coarse g = coarse_geom(nb);
     load_coarse(cs, Cs, (int)(g.nbc * g.lvc));
+    const int bs = CON ? bucket_shift(n_a) : 0;
+    if (CON && nb > 0) {
+        for (int i = threadIdx.x; i < g.nbc; i += blockDim.x) cp[i] = __ldg(CP + i);
+        const int nbk = (int)bucket_count(n_a);
+        for (int i = threadIdx.x; i <= nbk; i += blockDim.x) cb[i] = __ldg(CB + i);
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    // Phase A is software-pipelined over the warp's steps of 128 queries (4
-    // per lane): l, r of the step after next are in flight while a step is
-    // processed, and for the contracted form the bitmap entries that give the
-    // ranks of the next step are gathered one step ahead.
+    // the next step's l, r are loaded before the current step is processed, so
+    // every warp keeps a batch of loads in flight
     const int64_t stride = nwarps * 128;
-    const int32_t na = (int32_t)n_a;
-    auto load_lr = [&](int64_t b, int4 &xl, int4 &xr) {
+    int4 p0 = make_int4(0, 0, 0, 0), p1 = p0;
+    auto fetch = [&](int64_t b) {
         if (VECQ && b + 3 < q) {
-            xl = __ldcs(reinterpret_cast<const int4 *>(L + b));
-            xr = __ldcs(reinterpret_cast<const int4 *>(R + b));
-        } else {   // ragged or absent: an absent query reads as invalid (r = -1)
-            xl.x = b < q ? __ldcs(L + b) : 0;         xr.x = b < q ? __ldcs(R + b) : -1;
-            xl.y = b + 1 < q ? __ldcs(L + b + 1) : 0; xr.y = b + 1 < q ? __ldcs(R + b + 1) : -1;
-            xl.z = b + 2 < q ? __ldcs(L + b + 2) : 0; xr.z = b + 2 < q ? __ldcs(R + b + 2) : -1;
-            xl.w = b + 3 < q ? __ldcs(L + b + 3) : 0; xr.w = b + 3 < q ? __ldcs(R + b + 3) : -1;
+            p0 = __ldcs(reinterpret_cast<const int4 *>(L + b));
+            p1 = __ldcs(reinterpret_cast<const int4 *>(R + b));
         }
     };
-    auto valid = [&](int32_t l, int32_t r) { return l >= 0 && r >= l && r < na; };
-    auto gather = [&](const int4 &xl, const int4 &xr, uint2 (&ge)[8]) {
-        if (!CON) return;
-        const int32_t ls[4] = {xl.x, xl.y, xl.z, xl.w}, rs[4] = {xr.x, xr.y, xr.z, xr.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {   // an invalid query reads position 0
-            const bool ok = valid(ls[i], rs[i]);
-            ge[2 * i] = __ldg(BP + ((ok ? (uint32_t)ls[i] : 0u) >> 5));
-            ge[2 * i + 1] = __ldg(BP + ((ok ? (uint32_t)rs[i] : 0u) >> 5));
-        }
-    };
-    int4 cl, cr, nl, nr;
-    uint2 cg[8], ng[8];
-    const int64_t first = warp * 128 + lane * 4;
-    load_lr(first, cl, cr);
-    load_lr(first + stride, nl, nr);
-    gather(cl, cr, cg);
+    fetch(warp * 128 + lane * 4);
+    const int32_t na = (int32_t)n_a;
     for (int64_t wb = warp * 128; wb < q; wb += stride) {
         const int64_t base = wb + lane * 4;
         const bool full = VECQ && base + 3 < q;
-        const int32_t lq[4] = {cl.x, cl.y, cl.z, cl.w}, rq[4] = {cr.x, cr.y, cr.z, cr.w};
-        int32_t aq[4], bq[4];
-        if (CON) {
+        int32_t lq[4], rq[4];
+        if (full) {
+            lq[0] = p0.x; lq[1] = p0.y; lq[2] = p0.z; lq[3] = p0.w;
+            rq[0] = p1.x; rq[1] = p1.y; rq[2] = p1.z; rq[3] = p1.w;
+        }
+        fetch(base + stride);
+        if (!full) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const uint32_t pl = valid(lq[i], rq[i]) ? (uint32_t)lq[i] : 0u;
-                const uint32_t pr = valid(lq[i], rq[i]) ? (uint32_t)rq[i] : 0u;
-                aq[i] = (int32_t)(cg[2 * i].y + __popc(cg[2 * i].x & ((1u << (pl & 31)) - 1u)));
-                bq[i] = (int32_t)(cg[2 * i + 1].y + __popc(cg[2 * i + 1].x & ((1u << (pr & 31)) - 1u)));
+                const bool p = base + i < q;
+                lq[i] = p ? __ldcs(L + base + i) : 0;
+                rq[i] = p ? __ldcs(R + base + i) : -1;   // absent: reads as invalid
             }
         }
-        // next step's gathers and the step after next's l, r go out now
-        if (wb + stride < q) gather(nl, nr, ng);
-        cl = nl;
-        cr = nr;
-        if (wb + 2 * stride < q) load_lr(base + 2 * stride, nl, nr);
-        bool okq[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) okq[i] = valid(lq[i], rq[i]);
         int32_t o[4];
         unsigned need = 0;
         bool bad = false;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const bool present = full || base + i < q;
-            const bool ok = present && okq[i];
+            const bool ok = present && lq[i] >= 0 && rq[i] >= lq[i] && rq[i] < na;
             bad |= present && !ok;
-            const bool single = CON && ok && aq[i] >= bq[i];          // contracted l == r
+            const bool single = CON && ok && lq[i] == rq[i];          // contracted a == b
             // straight-line: an invalid or single query reads block 0 harmlessly
             const bool use = ok && !single;
-            const uint32_t lo = use ? (uint32_t)(CON ? aq[i] : lq[i]) : 0u;
-            const uint32_t hi = use ? (uint32_t)(CON ? bq[i] - 1 : rq[i]) : 0u;
+            uint32_t BL, BR;
+            if (CON) {
+                BL = use ? coarse_of(cp, cb, bs, (uint32_t)lq[i]) : 0u;
+                BR = use ? coarse_of(cp, cb, bs, (uint32_t)rq[i] - 1u) : 0u;
+            } else {
+                const int sh = logk + g.lc;
+                BL = use ? (uint32_t)lq[i] >> sh : 0u;
+                BR = use ? (uint32_t)rq[i] >> sh : 0u;
+            }
             uint64_t m;
-            const bool inside = coarse_span_min(cs, g, logk, lo, hi, (uint32_t)lq[i], (uint32_t)rq[i], m);
+            const bool inside = coarse_blocks_min(cs, g, BL, BR, (uint32_t)lq[i], (uint32_t)rq[i], m);
             o[i] = !ok ? -1 : (single ? lq[i] : (inside ? (int32_t)key_pos(m) : -1));
             need |= (use && !inside ? 1u : 0u) << i;
         }
@@ -431,10 +443,6 @@ __global__ void __launch_bounds__(256, CON ? 3 : 4) k_query_two(Src src, Len len
             if (need & 8u) my[sbase + c0 + c1 + c2 + __popc(b3 & lt)] = (uint32_t)(base + 3);
         }
         if (!CON && bad && err) atomicOr(err, ERR_QUERY_RANGE);
-        if (CON) {
-#pragma unroll
-            for (int x = 0; x < 8; ++x) cg[x] = ng[x];
-        }
     }
     __syncthreads();  // n_open is final and the region's entries are visible to the CTA
     const int64_t cnt = n_open;

@@ -28,7 +28,7 @@ cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint
         const ResidualPlan rp = residual_plan(q, di.sms);
         Residual *res = static_cast<Residual *>(res_ws);
 #define RMQ_LQ2(VQ, V) \
-    k_query_two<SrcI32, false, VQ, V><<<(unsigned)rp.ctas, kThreads, 0, s>>>(src, len, logk, T, Cs, l, r, nullptr, n, out, q, res, rp.region, err)
+    k_query_two<SrcI32, false, VQ, V><<<(unsigned)rp.ctas, kThreads, 0, s>>>(src, len, logk, T, Cs, l, r, nullptr, nullptr, nullptr, n, out, q, res, rp.region, err)
         if (vecq && vec) RMQ_LQ2(true, true);
         else if (vecq) RMQ_LQ2(true, false);
         else if (vec) RMQ_LQ2(false, true);

@@ -193,9 +193,21 @@ struct ResidualPlan {
     int64_t ctas;    // phase-A CTAs
     int64_t region;  // entries per CTA region
 };
-// The contracted form's query gathers bitmap entries one step ahead and runs
-// kQueryCtasPerSmCon CTAs per SM (<= 85 registers).
-constexpr int kQueryCtasPerSmCon = 3;
+// Coarse index of the contracted form: CP[j] = P_{j 2^sh}, the position in A
+// where coarse block j of A_Q begins (sh = logk_con + lc), and for buckets of
+// 2^s positions, CB[i] = the last coarse block that begins at or before
+// position i 2^s (0 if none); CB[nbk] = nbc - 1.  A query's coarse blocks
+// follow from l and r through these two small arrays, without its ranks.
+// nbc * lvc <= kCoarseCap implies nbc <= 455.
+constexpr int kCoarseBlocksMax = 512;
+constexpr int kBucketsMax = 2048;
+__host__ __device__ inline int bucket_shift(int64_t n) {
+    int s = 5;
+    while (((n - 1) >> s) + 1 >= kBucketsMax) ++s;
+    return s;
+}
+__host__ __device__ inline int64_t bucket_count(int64_t n) { return ((n - 1) >> bucket_shift(n)) + 1; }
+constexpr int kQueryCtasPerSmCon = 4;
 inline ResidualPlan residual_plan(int64_t q, int sms, int per_sm = kQueryCtasPerSm) {
     const int64_t batches = (q + 127) / 128;                     // 4 queries x 32 lanes per warp step
     int64_t ctas = (batches + 7) / 8;
@@ -263,7 +275,8 @@ cudaError_t contract(const int32_t *A, int64_t n, const uint32_t *P, const int64
 int64_t bitmap_entries(int64_t n);
 size_t endpoint_bitmap_workspace_bytes(int64_t n);
 cudaError_t endpoint_bitmap(const int32_t *l, const int32_t *r, int64_t q, int64_t n, uint2 *BP, int64_t *m_dev,
-                            uint64_t *AQ, void *ws, cudaStream_t s, Stages *st = nullptr);
+                            uint64_t *AQ, void *ws, cudaStream_t s, Stages *st = nullptr, int logk_q = 0,
+                            uint32_t *CP = nullptr, uint16_t *CB = nullptr);
 size_t contract_workspace_bytes(int64_t n);
 
 }  // namespace rmq
