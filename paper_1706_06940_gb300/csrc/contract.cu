@@ -399,26 +399,40 @@ __global__ void __launch_bounds__(kT) k_bits_partial(const uint2 *__restrict__ B
 // With CP given, also writes the coarse index of the query over A_Q with
 // blocks of 2^logk_q entries: CP (where each coarse block of A_Q begins) and
 // CB (the coarse block at each bucket start).
+// The tile's offset and the total m come from the tile counts of
+// k_bits_partial (every CTA adds up the counts of the tiles before it);
+// block 0 stores m.
 __global__ void __launch_bounds__(kT) k_bits_final(uint2 *__restrict__ BP, int64_t nbp,
-                                                   const uint32_t *__restrict__ partial, const int64_t *m_dev,
+                                                   const uint32_t *__restrict__ partial, int64_t *m_dev,
                                                    int64_t ntA, uint64_t *__restrict__ AQ, int64_t n, int logk_q,
                                                    uint32_t *__restrict__ CP, uint16_t *__restrict__ CB) {
     __shared__ uint32_t wsum[kT / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)w * (32 * kIPT);
-    uint32_t c[kIPT];
+    uint32_t c[kIPT], words[kIPT];
     uint32_t s = 0;
 #pragma unroll
     for (int i = 0; i < kIPT; ++i) {
         const int64_t e = base + i * 32 + lane;
-        c[i] = e < nbp ? __popc(BP[e].x) : 0u;
+        words[i] = e < nbp ? BP[e].x : 0u;
+        c[i] = __popc(words[i]);
         s += c[i];
     }
+    uint32_t before = 0, all = 0;
+    for (int64_t i = threadIdx.x; i < gridDim.x; i += kT) {
+        const uint32_t v = __ldg(partial + i);
+        all += v;
+        before += i < blockIdx.x ? v : 0u;
+    }
+    uint32_t tile_off, m32;
+    block_excl_scan(before, wsum, tile_off);
+    block_excl_scan(all, wsum, m32);
     s = __reduce_add_sync(0xffffffffu, s);
     uint32_t total;
     uint32_t run = block_excl_scan(lane == 0 ? s : 0u, wsum, total);
-    run = __shfl_sync(0xffffffffu, run, 0) + partial[blockIdx.x];
-    const int64_t m = *m_dev;
+    run = __shfl_sync(0xffffffffu, run, 0) + tile_off;
+    const int64_t m = m32;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *m_dev = m;
     // coarse geometry of the table over A_Q (m - 1 entries)
     const int64_t nbq = m >= 2 ? (m - 2 + (1ll << logk_q)) >> logk_q : 0;
     const bool index = CP != nullptr && nbq > 0;
@@ -444,7 +458,7 @@ __global__ void __launch_bounds__(kT) k_bits_final(uint2 *__restrict__ BP, int64
                 if (sg >= 0 && sg <= m - 2) AQ[sg] = KEY_MAX;
             }
             if (index && e < nbp - 1) {
-                const uint32_t word = BP[e].x;
+                const uint32_t word = words[i];
                 // a coarse block of A_Q begins at the (j 2^sh)-th mark
                 const int64_t j = ((int64_t)ex + (1ll << sh) - 1) >> sh;
                 const int64_t t = (j << sh) - (int64_t)ex;
@@ -485,45 +499,21 @@ __device__ __forceinline__ void emit_atomic(uint64_t *H, int64_t s, uint64_t v) 
 // then stored to A_Q in order (coalesced).  Only the first segment (begun in
 // an earlier tile) and the one left open at the end are combined with
 // atomics (those entries were set to KEY_MAX by k_bits_final).
-// With T0 given, the kernel also folds every segment value into level 0 of
-// the block table over A_Q (Sec. 3.1 step 3: T0[j] = min of A_Q over block j
-// of 2^logk_q entries) with one atomicMin per block and 32 slots; T0 starts
-// at KEY_MAX.  Partial values of a straddling segment fold in as well, which
-// leaves the minimum unchanged.
 __device__ __forceinline__ int swz(int x) { return (x & ~7) | ((x & 7) ^ ((x >> 3) & 7)); }
 
 constexpr int kContractSmem = (kT / 32) * kATile * 8;   // per warp: the tile, then its slots
 
-// Folds key v of A_Q entry sg into T0[sg >> logk_q], for the lanes with
-// `has`.  Called by the whole warp; the lanes' blocks are non-decreasing, and
-// each distinct block costs two 32-bit warp reductions and one atomic.
-__device__ __forceinline__ void fold_block_min(uint64_t *T0, int logk_q, bool has, int64_t sg, uint64_t v) {
-    const uint32_t blk = has ? (uint32_t)(sg >> logk_q) : 0u;
-    const uint32_t hi = (uint32_t)(v >> 32), lo = (uint32_t)v;
-    unsigned rest = __ballot_sync(0xffffffffu, has);
-    while (rest) {
-        const int leader = __ffs(rest) - 1;
-        const uint32_t b = __shfl_sync(0xffffffffu, blk, leader);
-        const bool in = has && blk == b;
-        rest &= ~__ballot_sync(0xffffffffu, in);
-        const uint32_t mh = __reduce_min_sync(0xffffffffu, in ? hi : 0xffffffffu);
-        const uint32_t ml = __reduce_min_sync(0xffffffffu, in && hi == mh ? lo : 0xffffffffu);
-        if ((threadIdx.x & 31) == leader)
-            atomicMin(reinterpret_cast<unsigned long long *>(T0) + b, ((unsigned long long)mh << 32) | ml);
-    }
-}
-
 template <bool VEC>
 __global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const uint2 *__restrict__ BP,
-                                                 const int64_t *m_dev, int64_t ntA, uint64_t *__restrict__ H,
-                                                 uint64_t *__restrict__ T0, int logk_q) {
+                                                 const int64_t *m_dev, int64_t ntA, uint64_t *__restrict__ H) {
     extern __shared__ uint64_t csmem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint64_t *slot = csmem + (size_t)w * kATile;                      // 1024 slots per warp
     int4 *tile = reinterpret_cast<int4 *>(slot);                      // the same memory, first 4 KB
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t m = *m_dev;
+    const int32_t m = (int32_t)*m_dev;       // m <= n < 2^31: segment numbers fit in 32 bits
+    const int64_t nfull = n / kATile;        // tiles wholly inside [0, n)
     const int64_t nv = n / 4;                // vectors wholly inside [0, n)
     const int64_t nw = (n + 31) >> 5;        // bitmap words; BP[nw] is the end entry
     for (int64_t t = warp; t < ntA; t += nwarps) {
@@ -533,24 +523,31 @@ __global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const ui
         const uint2 e = __ldg(BP + (wi < nw ? wi : nw));
         const int64_t ts = t * kATile;
         int4 v[8];
+        if (VEC && t < nfull) {
+            const int4 *tp = reinterpret_cast<const int4 *>(src.a) + ts / 4 + lane;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int64_t vi = ts / 4 + u * 32 + lane;
-            if (vi < nv) {
-                v[u] = VEC ? ld_stream_v4(reinterpret_cast<const int4 *>(src.a) + vi)
-                           : make_int4(__ldg(src.a + 4 * vi), __ldg(src.a + 4 * vi + 1), __ldg(src.a + 4 * vi + 2),
-                                       __ldg(src.a + 4 * vi + 3));
-            } else {
-                const int64_t c = 4 * vi;
-                v[u] = make_int4(c < n ? __ldg(src.a + c) : INT_MAX, c + 1 < n ? __ldg(src.a + c + 1) : INT_MAX,
-                                 c + 2 < n ? __ldg(src.a + c + 2) : INT_MAX, c + 3 < n ? __ldg(src.a + c + 3) : INT_MAX);
+            for (int u = 0; u < 8; ++u) v[u] = ld_stream_v4(tp + u * 32);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t vi = ts / 4 + u * 32 + lane;
+                if (vi < nv) {
+                    v[u] = VEC ? ld_stream_v4(reinterpret_cast<const int4 *>(src.a) + vi)
+                               : make_int4(__ldg(src.a + 4 * vi), __ldg(src.a + 4 * vi + 1),
+                                           __ldg(src.a + 4 * vi + 2), __ldg(src.a + 4 * vi + 3));
+                } else {
+                    const int64_t c = 4 * vi;
+                    v[u] = make_int4(c < n ? __ldg(src.a + c) : INT_MAX, c + 1 < n ? __ldg(src.a + c + 1) : INT_MAX,
+                                     c + 2 < n ? __ldg(src.a + c + 2) : INT_MAX,
+                                     c + 3 < n ? __ldg(src.a + c + 3) : INT_MAX);
+                }
             }
         }
         const uint32_t word = e.x;
-        const int64_t s_t = (int64_t)__shfl_sync(0xffffffffu, e.y, 0) - 1;      // open before the tile
+        const int32_t s_t = (int32_t)__shfl_sync(0xffffffffu, e.y, 0) - 1;      // open before the tile
         const uint32_t nbits = __popc(word);
-        const uint32_t cnt = __reduce_add_sync(0xffffffffu, nbits);             // boundaries in the tile
-        const int64_t s_n = s_t + cnt;                                           // open after the tile
+        const int32_t cnt = (int32_t)__reduce_add_sync(0xffffffffu, nbits);     // boundaries in the tile
+        const int32_t s_n = s_t + cnt;                                           // open after the tile
         if (cnt == 0 && (s_t < 0 || s_t > m - 2)) continue;
         if (cnt == 0) {  // no boundary in the tile: one partial minimum of segment s_t
             uint64_t best = KEY_MAX;
@@ -561,10 +558,7 @@ __global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const ui
                                        kmin(make_key(v[u].z, c + 2), make_key(v[u].w, c + 3))));
             }
             best = warp_min(best);
-            if (lane == 0) {
-                emit_atomic(H, s_t, best);
-                if (T0) atomicMin(reinterpret_cast<unsigned long long *>(T0) + (s_t >> logk_q), (unsigned long long)best);
-            }
+            if (lane == 0) emit_atomic(H, s_t, best);
             continue;
         }
         __syncwarp();  // the previous tile's slots are no longer read
@@ -615,21 +609,13 @@ __global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const ui
         if (nbits) slot[pre] = kmin(slot[pre], carry_in);
         const uint64_t tail = __shfl_sync(0xffffffffu, val, 31);
         __syncwarp();
-        for (uint32_t b0 = 0; b0 < cnt; b0 += 32) {
-            const uint32_t b = b0 + lane;
-            const int64_t sg = s_t + b;
-            const bool has = b < cnt && sg >= 0 && sg <= m - 2;
-            const uint64_t v = has ? slot[b] : KEY_MAX;
-            if (has) {
-                if (b == 0) emit_atomic(H, sg, v);
-                else st_stream_u64(H + sg, v);
-            }
-            if (T0) fold_block_min(T0, logk_q, has, sg, v);
+        for (int32_t b = lane; b < cnt; b += 32) {
+            const int32_t sg = s_t + b;
+            if (sg < 0 || sg > m - 2) continue;
+            if (b == 0) emit_atomic(H, sg, slot[0]);
+            else H[sg] = slot[b];
         }
-        if (lane == 0 && s_n >= 0 && s_n <= m - 2) {
-            emit_atomic(H, s_n, tail);
-            if (T0) atomicMin(reinterpret_cast<unsigned long long *>(T0) + (s_n >> logk_q), (unsigned long long)tail);
-        }
+        if (lane == 0 && s_n >= 0 && s_n <= m - 2) emit_atomic(H, s_n, tail);
     }
 }
 
@@ -729,16 +715,15 @@ cudaError_t bitmap_ranks(uint2 *BP, int64_t n, int64_t *m_dev, uint64_t *AQ, uin
     const int64_t nbp = bitmap_entries(n);
     const int64_t tiles = cdiv(nbp, kTile);
     k_bits_partial<<<(unsigned)tiles, kT, 0, s>>>(BP, nbp, aux);
-    k_scan_top<<<1, kT, 0, s>>>(aux, tiles, m_dev);   // tile counts scanned in place, total -> m
     k_bits_final<<<(unsigned)tiles, kT, 0, s>>>(BP, nbp, aux, m_dev, AQ ? cdiv(n, kATile) : 0, AQ, n, logk_q, CP, CB);
-    note_launches(3);
+    note_launches(2);
     return cudaGetLastError();
 }
 
 size_t bitmap_aux_bytes(int64_t n) { return align256(cdiv(bitmap_entries(n), kTile) * 4); }
 
 cudaError_t contract_bitmap(const int32_t *A, int64_t n, const uint2 *BP, const int64_t *m_dev, uint64_t *AQ,
-                            uint64_t *T0, int logk_q, cudaStream_t s) {
+                            cudaStream_t s) {
     const int64_t ntA = cdiv(n, kATile);
     const DevInfo di = dev_info();
     const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(ntA, kT / 32), (int64_t)di.sms * 3));
@@ -750,9 +735,9 @@ cudaError_t contract_bitmap(const int32_t *A, int64_t n, const uint2 *BP, const 
         attr[di.device] = true;
     }
     if ((reinterpret_cast<uintptr_t>(A) & 15) == 0)
-        k_contract<true><<<(unsigned)ctas, kT, kContractSmem, s>>>(src, n, BP, m_dev, ntA, AQ, T0, logk_q);
+        k_contract<true><<<(unsigned)ctas, kT, kContractSmem, s>>>(src, n, BP, m_dev, ntA, AQ);
     else
-        k_contract<false><<<(unsigned)ctas, kT, kContractSmem, s>>>(src, n, BP, m_dev, ntA, AQ, T0, logk_q);
+        k_contract<false><<<(unsigned)ctas, kT, kContractSmem, s>>>(src, n, BP, m_dev, ntA, AQ);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -796,7 +781,7 @@ cudaError_t contract(const int32_t *A, int64_t n, const uint32_t *P, const int64
     note_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = bitmap_ranks(BP, n, m2, AQ, aux, s)) != cudaSuccess) return e;
-    return contract_bitmap(A, n, BP, m2, AQ, nullptr, 0, s);
+    return contract_bitmap(A, n, BP, m2, AQ, s);
 }
 
 size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con) {
@@ -838,11 +823,10 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     // step 1: the endpoint bitmap (marks), then the rank counts
     if ((e = endpoint_bitmap(l, r, q, n, BP, m_dev, AQ, aux, s, st, logk_con, CP, CB)) != cudaSuccess) return e;
     st->mark(s);
-    // step 2, with level 0 of step 3 folded in
-    if ((e = cudaMemsetAsync(T, 0xff, (size_t)nbq * 8, s)) != cudaSuccess) return e;
-    if ((e = contract_bitmap(A, n, BP, m_dev, AQ, T, logk_con, s)) != cudaSuccess) return e;
+    if ((e = contract_bitmap(A, n, BP, m_dev, AQ, s)) != cudaSuccess) return e;             // step 2
     st->mark(s);
     const Len lenq{0, m_dev};
+    if ((e = launch_block_minima_u64(AQ, lenq, mq_max, logk_con, T, s)) != cudaSuccess) return e;         // step 3
     if ((e = launch_sparse_table(T, lenq, logk_con, nbq, s, Cs)) != cudaSuccess) return e;                // step 3
     st->mark(s);
     const bool vecq = ((reinterpret_cast<uintptr_t>(l) | reinterpret_cast<uintptr_t>(r) |
