@@ -67,31 +67,17 @@ __host__ __device__ __forceinline__ Coarse coarse_geom(int64_t nb) {
     }
 }
 
-// L2 policy for data touched once: its lines are the first to be evicted,
-// so streams of A or A_Q do not push small resident structures (tables, the
-// endpoint bitmap) out of L2.
-__device__ __forceinline__ uint64_t l2_evict_first() {
-    uint64_t pol;
-    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-
-// Streaming 128-bit load: no L1 allocation, evict-first in L2 (read once).
+// Streaming 128-bit load that does not allocate in L1 (data read once).
 __device__ __forceinline__ int4 ld_stream_v4(const int4 *p) {
     int4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p), "l"(l2_evict_first()));
+    asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
     return v;
 }
 __device__ __forceinline__ ulonglong2 ld_stream_v2u64(const ulonglong2 *p) {
     ulonglong2 v;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u64 {%0,%1}, [%2], %3;"
-                 : "=l"(v.x), "=l"(v.y) : "l"(p), "l"(l2_evict_first()));
+    asm volatile("ld.global.nc.L1::no_allocate.v2.u64 {%0,%1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p));
     return v;
-}
-// Store of data the next kernel streams once.
-__device__ __forceinline__ void st_stream_u64(uint64_t *p, uint64_t v) {
-    asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(l2_evict_first()) : "memory");
 }
 
 // ---------------------------------------------------------------- sources
