@@ -157,18 +157,17 @@ rmq_status batch_plain(const int32_t *A, int64_t n, const int32_t *l, const int3
     const int64_t nb = cdiv(n, 1ll << logk);
     Workspace ws;
     const int64_t te = two_level_entries(nb);
-    rmq_status st = ws.alloc((size_t)(te + kCoarseCap) * 8 + query_residual_bytes(q, dev_info().sms), s);
+    rmq_status st = ws.alloc((size_t)te * 8 + query_residual_bytes(q, dev_info().sms), s);
     if (st != RMQ_OK) return st;
     uint64_t *T = static_cast<uint64_t *>(ws.p);
-    uint64_t *Cs = T + te;
-    void *res = Cs + kCoarseCap;
+    void *res = T + te;
     cudaError_t e;
     sg->mark(s);
     if ((e = launch_block_minima_i32(A, n, logk, T, s)) != cudaSuccess) return cuda_status(e);
     sg->mark(s);
-    if ((e = launch_sparse_table(T, Len{n, nullptr}, logk, nb, s, Cs)) != cudaSuccess) return cuda_status(e);
+    if ((e = launch_sparse_table(T, Len{n, nullptr}, logk, nb, s, true)) != cudaSuccess) return cuda_status(e);
     sg->mark(s);
-    e = launch_query_plain(A, n, logk, T, Cs, nb, l, r, q, out, res, s);
+    e = launch_query_plain(A, n, logk, T, nullptr, nb, l, r, q, out, res, s);
     sg->mark(s);
     return cuda_status(e);
 }
@@ -341,7 +340,7 @@ rmq_status rmq_build(const int32_t *A, int64_t n, const rmq_opts *opts, void *st
     cudaStream_t s = as_stream(stream);
     h->Cs = h->T + te;
     if ((e = launch_block_minima_i32(A, n, logk, h->T, s)) != cudaSuccess ||
-        (e = launch_sparse_table(h->T, Len{n, nullptr}, logk, h->nb, s, h->Cs)) != cudaSuccess) {
+        (e = launch_sparse_table(h->T, Len{n, nullptr}, logk, h->nb, s, true, h->Cs)) != cudaSuccess) {
         cudaFree(h->T);
         delete h;
         return cuda_status(e);

@@ -15,12 +15,11 @@ constexpr int kThreads = 256;
 // Warp per block (k / EPV >= 32 vectors): every lane reads k/(32*EPV)
 // consecutive-lane 16-byte vectors (coalesced, streaming), keeps the minimum
 // packed key, and a shuffle reduction gives the block minimum.  UNR vectors
-// are loaded before any is used to keep enough bytes in flight.  With `rev`
+// are loaded before any is used to keep enough bytes in flight.  With REV
 // the blocks are visited from the end (a sequence just written is then read
 // while its most recent part is still in L2).
-template <class Src, int UNR, bool VEC>
-__global__ void __launch_bounds__(kThreads) k_block_min_warp(Src src, Len len, int logk, uint64_t *__restrict__ T0,
-                                                             bool rev) {
+template <class Src, int UNR, bool VEC, bool REV>
+__global__ void __launch_bounds__(kThreads) k_block_min_warp(Src src, Len len, int logk, uint64_t *__restrict__ T0) {
     constexpr int EPV = Src::EPV;
     const int64_t n = len.get();
     const int64_t K = 1ll << logk;
@@ -32,7 +31,7 @@ __global__ void __launch_bounds__(kThreads) k_block_min_warp(Src src, Len len, i
     const int vpb = (int)(K / EPV);
     const int vpl = vpb >> 5;
     for (int64_t bi = warp; bi < nfull; bi += nwarps) {
-        const int64_t b = rev ? nfull - 1 - bi : bi;
+        const int64_t b = REV ? nfull - 1 - bi : bi;
         const int64_t v0 = b * vpb + lane;
         uint64_t best = KEY_MAX;
         for (int u = 0; u < vpl; u += UNR) {
@@ -57,9 +56,8 @@ __global__ void __launch_bounds__(kThreads) k_block_min_warp(Src src, Len len, i
 
 // Small blocks (k / EPV < 32 vectors): G = k/EPV lanes per block, 32/G blocks
 // per warp row, 4 rows in flight; the reduction is a width-G shuffle.
-template <class Src, bool VEC>
-__global__ void __launch_bounds__(kThreads) k_block_min_group(Src src, Len len, int logk, uint64_t *__restrict__ T0,
-                                                              bool rev) {
+template <class Src, bool VEC, bool REV>
+__global__ void __launch_bounds__(kThreads) k_block_min_group(Src src, Len len, int logk, uint64_t *__restrict__ T0) {
     constexpr int EPV = Src::EPV;
     const int64_t n = len.get();
     const int64_t K = 1ll << logk;
@@ -72,7 +70,7 @@ __global__ void __launch_bounds__(kThreads) k_block_min_group(Src src, Len len, 
     const int64_t nvec = nfull * G;
     const int64_t last = nvec > 0 ? ((nvec - 1) >> 7) << 7 : 0;
     for (int64_t bi = warp * 128; bi < nvec; bi += nwarps * 128) {
-        const int64_t base = rev ? last - bi : bi;
+        const int64_t base = REV ? last - bi : bi;
         uint64_t best[4];
 #pragma unroll
         for (int x = 0; x < 4; ++x) {
@@ -100,9 +98,8 @@ __global__ void __launch_bounds__(kThreads) k_block_min_group(Src src, Len len, 
     }
 }
 
-template <class Src, bool VEC>
-cudaError_t block_min_dispatch(Src src, Len len, int64_t n_max, int logk, uint64_t *T0, cudaStream_t s,
-                               bool rev = false) {
+template <class Src, bool VEC, bool REV>
+cudaError_t block_min_dispatch(Src src, Len len, int64_t n_max, int logk, uint64_t *T0, cudaStream_t s) {
     constexpr int EPV = Src::EPV;
     const DevInfo di = dev_info();
     const int64_t K = 1ll << logk;
@@ -112,14 +109,14 @@ cudaError_t block_min_dispatch(Src src, Len len, int64_t n_max, int logk, uint64
     if (vpb >= 32) {
         const int64_t ctas = std::min<int64_t>(cdiv(nb, kThreads / 32), (int64_t)di.sms * 8);
         const int vpl = vpb / 32;
-        if (vpl >= 8) k_block_min_warp<Src, 8, VEC><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0, rev);
-        else if (vpl >= 4) k_block_min_warp<Src, 4, VEC><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0, rev);
-        else if (vpl >= 2) k_block_min_warp<Src, 2, VEC><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0, rev);
-        else k_block_min_warp<Src, 1, VEC><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0, rev);
+        if (vpl >= 8) k_block_min_warp<Src, 8, VEC, REV><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0);
+        else if (vpl >= 4) k_block_min_warp<Src, 4, VEC, REV><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0);
+        else if (vpl >= 2) k_block_min_warp<Src, 2, VEC, REV><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0);
+        else k_block_min_warp<Src, 1, VEC, REV><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0);
     } else {
         const int64_t nvec = nb * vpb;
         const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(nvec, 128 * (kThreads / 32)), (int64_t)di.sms * 8));
-        k_block_min_group<Src, VEC><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0, rev);
+        k_block_min_group<Src, VEC, REV><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0);
     }
     note_launches(1);
     return cudaGetLastError();
@@ -130,13 +127,13 @@ cudaError_t block_min_dispatch(Src src, Len len, int64_t n_max, int logk, uint64
 cudaError_t launch_block_minima_i32(const int32_t *A, int64_t n, int logk, uint64_t *T0, cudaStream_t s) {
     SrcI32 src{A};
     Len len{n, nullptr};
-    if ((reinterpret_cast<uintptr_t>(A) & 15) == 0) return block_min_dispatch<SrcI32, true>(src, len, n, logk, T0, s);
-    return block_min_dispatch<SrcI32, false>(src, len, n, logk, T0, s);
+    if ((reinterpret_cast<uintptr_t>(A) & 15) == 0) return block_min_dispatch<SrcI32, true, false>(src, len, n, logk, T0, s);
+    return block_min_dispatch<SrcI32, false, false>(src, len, n, logk, T0, s);
 }
 
 cudaError_t launch_block_minima_u64(const uint64_t *AQ, Len len, int64_t n_max, int logk, uint64_t *T0,
                                     cudaStream_t s) {
-    return block_min_dispatch<SrcU64, true>(SrcU64{AQ}, len, n_max, logk, T0, s, true);
+    return block_min_dispatch<SrcU64, true, true>(SrcU64{AQ}, len, n_max, logk, T0, s);
 }
 
 }  // namespace rmq

@@ -793,7 +793,6 @@ size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con) {
     b += align256(8);                                 // m
     b += align256(mq_max * 8);                        // A_Q
     b += align256(nbq * lv * 8);                      // table over A_Q
-    b += align256(kCoarseCap * 8);                    // its coarse summary
     b += align256(kCoarseBlocksMax * 4) + align256((kBucketsMax + 1) * 2);   // coarse index
     b += align256(query_residual_bytes(q, dev_info().sms, kQueryCtasPerSmCon));  // residual list of the query
     b += bitmap_aux_bytes(n);
@@ -810,7 +809,6 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     int64_t *m_dev = c.take<int64_t>(1);
     uint64_t *AQ = c.take<uint64_t>(mq_max);
     uint64_t *T = c.take<uint64_t>(nbq * lv);
-    uint64_t *Cs = c.take<uint64_t>(kCoarseCap);
     uint32_t *CP = c.take<uint32_t>(kCoarseBlocksMax);
     uint16_t *CB = c.take<uint16_t>(kBucketsMax + 1);
     char *resw = c.take<char>(query_residual_bytes(q, dev_info().sms, kQueryCtasPerSmCon));
@@ -827,7 +825,7 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     st->mark(s);
     const Len lenq{0, m_dev};
     if ((e = launch_block_minima_u64(AQ, lenq, mq_max, logk_con, T, s)) != cudaSuccess) return e;         // step 3
-    if ((e = launch_sparse_table(T, lenq, logk_con, nbq, s, Cs)) != cudaSuccess) return e;                // step 3
+    if ((e = launch_sparse_table(T, lenq, logk_con, nbq, s, true)) != cudaSuccess) return e;              // step 3
     st->mark(s);
     const bool vecq = ((reinterpret_cast<uintptr_t>(l) | reinterpret_cast<uintptr_t>(r) |
                         reinterpret_cast<uintptr_t>(out)) & 15) == 0;
@@ -835,9 +833,9 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     const ResidualPlan rp = residual_plan(q, di.sms, kQueryCtasPerSmCon);                                                    // step 4
     Residual *res = reinterpret_cast<Residual *>(resw);
     if (vecq)
-        k_query_two<SrcU64, true, true, true><<<(unsigned)rp.ctas, kT, 0, s>>>(src, lenq, logk_con, T, Cs, l, r, BP, CP, CB, n, out, q, res, rp.region, nullptr);
+        k_query_two<SrcU64, true, true, true><<<(unsigned)rp.ctas, kT, 0, s>>>(src, lenq, logk_con, T, nullptr, l, r, BP, CP, CB, n, out, q, res, rp.region, nullptr);
     else
-        k_query_two<SrcU64, true, false, true><<<(unsigned)rp.ctas, kT, 0, s>>>(src, lenq, logk_con, T, Cs, l, r, BP, CP, CB, n, out, q, res, rp.region, nullptr);
+        k_query_two<SrcU64, true, false, true><<<(unsigned)rp.ctas, kT, 0, s>>>(src, lenq, logk_con, T, nullptr, l, r, BP, CP, CB, n, out, q, res, rp.region, nullptr);
     note_launches(1);
     e = cudaGetLastError();
     st->mark(s);

@@ -157,6 +157,33 @@ __device__ __forceinline__ void warp_drain_scans(const Src &src, int64_t n, bool
     }
 }
 
+// Build the coarse table in shared memory from level lc of the block table
+// (Sec. 3.3's upper level): level 0 holds the coarse block minima (the last,
+// partial coarse block from two overlapping lookups of a lower level), the
+// levels above come by doubling.  Ends with a barrier.
+__device__ __forceinline__ void build_coarse(uint64_t *cs, const uint64_t *__restrict__ T, int64_t nb, const Coarse &g) {
+    const unsigned long long *Tu = reinterpret_cast<const unsigned long long *>(T);
+    for (int J = threadIdx.x; J < g.nbc; J += blockDim.x) {
+        uint64_t v;
+        if (J < g.nbc_full) {
+            v = __ldg(Tu + (int64_t)g.lc * nb + ((int64_t)J << g.lc));
+        } else {
+            const int64_t s0 = (int64_t)J << g.lc;
+            const int tt = ilog2_dev((uint64_t)(nb - s0));
+            v = kmin(__ldg(Tu + (int64_t)tt * nb + s0), __ldg(Tu + (int64_t)tt * nb + nb - (1ll << tt)));
+        }
+        cs[J] = v;
+    }
+    __syncthreads();
+    for (int t = 1; t < g.lvc; ++t) {
+        const int half = 1 << (t - 1), cnt = (int)g.nbc - (1 << t) + 1;
+        uint64_t *cur = cs + t * (int)g.nbc;
+        const uint64_t *prev = cur - g.nbc;
+        for (int J = threadIdx.x; J < cnt; J += blockDim.x) cur[J] = kmin(prev[J], prev[J + half]);
+        __syncthreads();
+    }
+}
+
 // Copy the coarse table into shared memory: every thread issues all its loads
 // before any store, so the copy costs one round trip to L2.
 __device__ __forceinline__ void load_coarse(uint64_t *cs, const uint64_t *__restrict__ Cs, int total) {
@@ -354,7 +381,9 @@ __global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk
     const int64_t n = len.get();
     const int64_t nb = (n + (1ll << logk) - 1) >> logk;
     const Coarse g = coarse_geom(nb);
-    load_coarse(cs, Cs, (int)(g.nbc * g.lvc));
+    // the coarse table: copied when the caller keeps one, else built here
+    if (Cs) load_coarse(cs, Cs, (int)(g.nbc * g.lvc));
+    else if (nb > 0) build_coarse(cs, T, nb, g);
     const int bs = CON ? bucket_shift(n_a) : 0;
     if (CON && nb > 0) {
         for (int i = threadIdx.x; i < g.nbc; i += blockDim.x) cp[i] = __ldg(CP + i);

@@ -164,11 +164,12 @@ cudaError_t launch_block_minima_u64(const uint64_t *AQ, Len len, int64_t n_max, 
                                     cudaStream_t s);
 // The table's block count is nb = ceil(len / 2^logk), read on the device from
 // `len`; nb_max bounds it on the host and sizes the launches.
-// Cs == nullptr: every level 1 .. floor(log2 nb) of the block table.
-// Cs != nullptr: the two-level layout -- levels 1 .. lc of the block table and
-//   the coarse table (kCoarseCap entries) in Cs.
+// two_level == false: every level 1 .. floor(log2 nb) of the block table.
+// two_level == true: the two-level layout -- levels 1 .. lc of the block
+//   table; with Cs, also the coarse table (kCoarseCap entries) in Cs (else
+//   each query CTA builds it in shared memory from level lc).
 cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, cudaStream_t s,
-                                uint64_t *Cs = nullptr);
+                                bool two_level = false, uint64_t *Cs = nullptr);
 // Entries of the two-level block table (levels 0 .. lc) for nb blocks.
 inline int64_t two_level_entries(int64_t nb) { return nb < 1 ? 0 : nb * (coarse_geom(nb).lc + 1); }
 // Two-phase query: kQueryCtasPerSm CTAs per SM; each CTA owns a region of the

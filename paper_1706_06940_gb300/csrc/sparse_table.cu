@@ -102,8 +102,8 @@ constexpr int kLV1 = 6, kS1 = 64;     // later rounds: 6 levels, 32 residues x 6
 
 }  // namespace
 
-cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, cudaStream_t s, uint64_t *Cs) {
-    const bool two = Cs != nullptr;
+cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, cudaStream_t s, bool two,
+                                uint64_t *Cs) {
     if (nb_max < 1) return cudaSuccess;
     const int top = two ? coarse_geom(nb_max).lc : (nb_max >= 2 ? ilog2_host((uint64_t)nb_max) : 0);
     static bool attr_done[64] = {false};
@@ -134,7 +134,7 @@ cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, 
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    if (two) {
+    if (two && Cs) {
         k_coarse_table<<<1, 1024, 0, s>>>(T, len, logk, Cs);
         note_launches(1);
         return cudaGetLastError();
