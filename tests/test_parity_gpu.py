@@ -272,6 +272,33 @@ def test_a4_a5_endpoint_bitmap(R, n, q):
     assert np.array_equal(bitmap_ranks_host(bp, r.astype(np.int64)), rb_want)
 
 
+def test_a4_endpoint_bitmap_clustered_endpoints(R):
+    """Endpoints crowded into a few thousand positions (many marks per bit
+    word, most contracted segments empty of interior cells) plus a few spread
+    out: P, ranks and answers match the oracle."""
+    n, q = 1_000_000, 100_000
+    rng = np.random.default_rng(77)
+    a = rng.integers(0, 3000, size=(q, 2))
+    l, r = a.min(axis=1).astype(np.int32), a.max(axis=1).astype(np.int32)
+    l[:50] = rng.integers(0, n, size=50)         # a few elsewhere
+    r[:50] = np.maximum(l[:50], rng.integers(0, n, size=50)).astype(np.int32)
+    nbp = -(-n // 32) + 1
+    BP = torch.full((2 * nbp,), -1, dtype=torch.int32, device=DEV)
+    m = torch.zeros(1, dtype=torch.int64, device=DEV)
+    R.rmq_endpoint_bitmap(dev(l), dev(r), n, BP, m)
+    torch.cuda.synchronize()
+    bp = BP.cpu().numpy()
+    wp, wt = oracle.sort_endpoints(l, r)
+    P_want, ra_want, rb_want = oracle.rank_endpoints(wp, wt, q)
+    bits = np.unpackbits(np.ascontiguousarray(bp[0::2]).view(np.uint8), bitorder="little")
+    assert np.array_equal(np.nonzero(bits)[0].astype(np.uint32), P_want)
+    assert int(m.item()) == len(P_want)
+    assert np.array_equal(bitmap_ranks_host(bp, l.astype(np.int64)), ra_want)
+    assert np.array_equal(bitmap_ranks_host(bp, r.astype(np.int64)), rb_want)
+    A = W.uniform_array(n, 78)
+    check(R, A, l, r, want=oracle.rmq_sparse_table(A, l, r), variants=(R.Variant.CONTRACTED,), kcons=(0, 32))
+
+
 def test_a4_endpoint_bitmap_invalid_queries_mark_zero(R):
     n, q = 10_000, 300
     l, r = W.uniform_queries(n, q, 99)
