@@ -157,17 +157,16 @@ rmq_status batch_plain(const int32_t *A, int64_t n, const int32_t *l, const int3
     const int64_t nb = cdiv(n, 1ll << logk);
     Workspace ws;
     const int64_t te = two_level_entries(nb);
-    rmq_status st = ws.alloc((size_t)te * 8 + query_residual_bytes(q, dev_info().sms), s);
+    rmq_status st = ws.alloc((size_t)te * 8, s);
     if (st != RMQ_OK) return st;
     uint64_t *T = static_cast<uint64_t *>(ws.p);
-    void *res = T + te;
     cudaError_t e;
     sg->mark(s);
     if ((e = launch_block_minima_i32(A, n, logk, T, s)) != cudaSuccess) return cuda_status(e);
     sg->mark(s);
     if ((e = launch_sparse_table(T, Len{n, nullptr}, logk, nb, s, true)) != cudaSuccess) return cuda_status(e);
     sg->mark(s);
-    e = launch_query_plain(A, n, logk, T, nullptr, nb, l, r, q, out, res, s);
+    e = launch_query_plain(A, n, logk, T, nullptr, l, r, q, out, s);
     sg->mark(s);
     return cuda_status(e);
 }
@@ -353,11 +352,7 @@ rmq_status rmq_query(rmq_handle h, const int32_t *l, const int32_t *r, int64_t q
     if (!h || q < 0 || q > kMaxQ) return RMQ_ERR_INVALID_ARG;
     if (q == 0) return RMQ_OK;
     if (!l || !r || !out) return RMQ_ERR_INVALID_ARG;
-    cudaStream_t s = as_stream(stream);
-    Workspace ws;
-    rmq_status st = ws.alloc(query_residual_bytes(q, dev_info().sms), s);
-    if (st != RMQ_OK) return st;
-    return cuda_status(launch_query_plain(h->A, h->n, h->logk, h->T, h->Cs, h->nb, l, r, q, out, ws.p, s));
+    return cuda_status(launch_query_plain(h->A, h->n, h->logk, h->T, h->Cs, l, r, q, out, as_stream(stream)));
 }
 
 rmq_status rmq_query_multi(const rmq_handle *hs, const int64_t *q_counts, int32_t H, const int32_t *l,

@@ -794,7 +794,6 @@ size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con) {
     b += align256(mq_max * 8);                        // A_Q
     b += align256(nbq * lv * 8);                      // table over A_Q
     b += align256(kCoarseBlocksMax * 4) + align256((kBucketsMax + 1) * 2);   // coarse index
-    b += align256(query_residual_bytes(q, dev_info().sms, kQueryCtasPerSmCon));  // residual list of the query
     b += bitmap_aux_bytes(n);
     return b;
 }
@@ -811,7 +810,6 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     uint64_t *T = c.take<uint64_t>(nbq * lv);
     uint32_t *CP = c.take<uint32_t>(kCoarseBlocksMax);
     uint16_t *CB = c.take<uint16_t>(kBucketsMax + 1);
-    char *resw = c.take<char>(query_residual_bytes(q, dev_info().sms, kQueryCtasPerSmCon));
     uint32_t *aux = reinterpret_cast<uint32_t *>(c.p + c.used);
     cudaError_t e;
     Stages none;
@@ -830,12 +828,11 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     const bool vecq = ((reinterpret_cast<uintptr_t>(l) | reinterpret_cast<uintptr_t>(r) |
                         reinterpret_cast<uintptr_t>(out)) & 15) == 0;
     SrcU64 src{AQ};
-    const ResidualPlan rp = residual_plan(q, di.sms, kQueryCtasPerSmCon);                                                    // step 4
-    Residual *res = reinterpret_cast<Residual *>(resw);
+    const int64_t qctas = query_ctas(q, di.sms);                                                        // step 4
     if (vecq)
-        k_query_two<SrcU64, true, true, true><<<(unsigned)rp.ctas, kT, 0, s>>>(src, lenq, logk_con, T, nullptr, l, r, BP, CP, CB, n, out, q, res, rp.region, nullptr);
+        k_query_two<SrcU64, true, true, true><<<(unsigned)qctas, kT, 0, s>>>(src, lenq, logk_con, T, nullptr, l, r, BP, CP, CB, n, out, q, nullptr);
     else
-        k_query_two<SrcU64, true, false, true><<<(unsigned)rp.ctas, kT, 0, s>>>(src, lenq, logk_con, T, nullptr, l, r, BP, CP, CB, n, out, q, res, rp.region, nullptr);
+        k_query_two<SrcU64, true, false, true><<<(unsigned)qctas, kT, 0, s>>>(src, lenq, logk_con, T, nullptr, l, r, BP, CP, CB, n, out, q, nullptr);
     note_launches(1);
     e = cudaGetLastError();
     st->mark(s);

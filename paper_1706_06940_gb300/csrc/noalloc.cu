@@ -81,7 +81,7 @@ extern "C" rmq_status rmq_batch_noalloc(const int32_t *A, int64_t n, const int32
     if (launch_block_minima_i32(A, n, logk, T, s) != cudaSuccess) return RMQ_ERR_CUDA;
     uint64_t *Cs = T + RMQ_NOALLOC_TABLE_ENTRIES;
     if (launch_sparse_table(T, Len{n, nullptr}, logk, nb, s, true, Cs) != cudaSuccess) return RMQ_ERR_CUDA;
-    if (launch_query_plain(A, n, logk, T, Cs, nb, l, r, q, out, nullptr, s) != cudaSuccess) return RMQ_ERR_CUDA;
+    if (launch_query_plain(A, n, logk, T, Cs, l, r, q, out, s) != cudaSuccess) return RMQ_ERR_CUDA;
     return RMQ_OK;
 }
 #pragma GCC visibility pop

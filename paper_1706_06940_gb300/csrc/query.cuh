@@ -201,113 +201,9 @@ __device__ __forceinline__ void load_coarse(uint64_t *cs, const uint64_t *__rest
     }
 }
 
-// Query kernel, both forms.  Each CTA first copies the coarse summary into
-// shared memory; then every thread takes 4 queries at a time (16-byte loads
-// of l and r when aligned): coarse resolution from shared memory, block-table
-// lookups only for the parts the coarse level leaves open, and finally the
-// warp-cooperative partial-block scans.  Plain form: the source is A and
-// query i covers [l_i, r_i].
-template <class Src, bool VECQ, bool VEC>
-__global__ void __launch_bounds__(256) k_query(Src src, Len len, int logk, const uint64_t *__restrict__ T,
-                                                const uint64_t *__restrict__ Cs, const int32_t *__restrict__ L,
-                                                const int32_t *__restrict__ R, int64_t n_a,
-                                                int32_t *__restrict__ out, int64_t q, unsigned *err) {
-    __shared__ uint64_t cs[kCoarseCap];
-    const int64_t n = len.get();
-    const int64_t nb = (n + (1ll << logk) - 1) >> logk;
-    const Coarse g = coarse_geom(nb);
-    load_coarse(cs, Cs, (int)(g.nbc * g.lvc));
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t wb = warp * 128; wb < q; wb += nwarps * 128) {
-        const int64_t base = wb + lane * 4;
-        const bool full = VECQ && base + 3 < q;
-        int32_t lq[4], rq[4];
-        bool present[4];
-        if (full) {
-            const int4 x0 = __ldcs(reinterpret_cast<const int4 *>(L + base));
-            const int4 x1 = __ldcs(reinterpret_cast<const int4 *>(R + base));
-            lq[0] = x0.x; lq[1] = x0.y; lq[2] = x0.z; lq[3] = x0.w;
-            rq[0] = x1.x; rq[1] = x1.y; rq[2] = x1.z; rq[3] = x1.w;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) present[i] = true;
-        } else {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                present[i] = base + i < q;
-                lq[i] = present[i] ? __ldcs(L + base + i) : 0;
-                rq[i] = present[i] ? __ldcs(R + base + i) : 0;
-            }
-        }
-        uint64_t best[4];
-        Pending pl[4], pr[4];
-        bool hl[4], hr[4], ok[4];
-        bool bad = false;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            ok[i] = present[i] && lq[i] >= 0 && rq[i] >= lq[i] && (int64_t)rq[i] < n_a;
-            bad |= present[i] && !ok[i];
-            hl[i] = hr[i] = false;
-            best[i] = KEY_MAX;
-            const int64_t lo = lq[i], hi = rq[i];
-            if (!ok[i]) continue;
-            const uint32_t la = (uint32_t)lq[i], ra = (uint32_t)rq[i];
-            int sub;
-            best[i] = resolve_coarse(cs, g, logk, (uint32_t)lo, (uint32_t)hi, la, ra, sub);
-            if (sub == SUB_WHOLE) {
-                best[i] = resolve_query(T, nb, logk, lo, hi, la, ra, pl[i], pr[i], hl[i], hr[i]);
-            } else if (sub != SUB_NONE) {
-                Pending unused;
-                bool unused_flag = false;
-                const int sh = logk + g.lc;
-                if (sub & SUB_LEFT) {
-                    const int64_t end_l = (((lo >> sh) + 1) << sh) - 1;
-                    best[i] = kmin(best[i], resolve_query(T, nb, logk, lo, end_l, la, 0xffffffffu, pl[i], unused,
-                                                          hl[i], unused_flag));
-                }
-                if (sub & SUB_RIGHT) {
-                    // the right part's only possible scan is its right partial block,
-                    // recorded in the first slot when the part lies in one block
-                    const int64_t start_r = (hi >> sh) << sh;
-                    Pending a, b;
-                    bool ha = false, hb = false;
-                    best[i] = kmin(best[i], resolve_query(T, nb, logk, start_r, hi, 0u, ra, a, b, ha, hb));
-                    if (ha) { pr[i] = a; hr[i] = true; }
-                    if (hb) { pr[i] = b; hr[i] = true; }
-                }
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            warp_drain_scans<Src, VEC>(src, n, hl[i], pl[i], best[i]);
-            warp_drain_scans<Src, VEC>(src, n, hr[i], pr[i], best[i]);
-        }
-        int32_t o[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            o[i] = ok[i] ? (int32_t)key_pos(best[i]) : -1;
-        }
-        if (full) {
-            __stcs(reinterpret_cast<int4 *>(out + base), make_int4(o[0], o[1], o[2], o[3]));
-        } else {
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (present[i]) out[base + i] = o[i];
-        }
-        if (bad && err) atomicOr(err, ERR_QUERY_RANGE);
-    }
-}
-
-// ---------------------------------------------------------------- two phases
-// The batch paths split the query kernel in two so that the common case runs
-// lean: phase A (k_query_coarse) answers every query the coarse summary
-// settles, from shared memory alone, and appends the others to a residual
-// list; phase B (k_query_fine) finishes the residual queries on the block
-// table and with partial-block scans.
-// An open query of the two-phase kernel: its index in the batch.
-typedef uint32_t Residual;
+// ------------------------------------------------------------ query kernel
+// Phase A settles most queries from the coarse table in shared memory alone;
+// phase B finishes the others on the block table and with edge scans.
 
 // Phase A's test: the minimum over the coarse blocks BL .. BR the query touches,
 // from two reads of the coarse table.  When its position lies inside the
@@ -352,6 +248,56 @@ __device__ __forceinline__ uint32_t coarse_of(const uint32_t *cp, const uint16_t
     return lo;
 }
 
+// Phase B of the query kernel for `take` (<= 32) queued queries whose indices
+// are at q_ids: each lane resolves one on the fine table, then the warp runs
+// the edge scans.
+template <class Src, bool CON, bool VEC>
+__device__ __forceinline__ void resolve_queued(const Src src, int64_t n, int logk, const uint64_t *__restrict__ T,
+                                            int64_t nb, const uint64_t *cs, const Coarse g,
+                                            const int32_t *__restrict__ L, const int32_t *__restrict__ R,
+                                            const uint2 *__restrict__ BP, int32_t *__restrict__ out,
+                                            const uint32_t *q_ids, int take) {
+    const int lane = threadIdx.x & 31;
+    const int sh = logk + g.lc;
+    const bool has = lane < take;
+    Pending pl, pr;
+    bool hl = false, hr = false;
+    uint64_t best = KEY_MAX;
+    uint32_t qid = 0;
+    if (has) {
+        qid = q_ids[lane];
+        const int32_t l = L[qid], r = R[qid];
+        const int64_t lo = CON ? (int64_t)bitmap_rank(BP, (uint32_t)l) : l;
+        const int64_t hi = CON ? (int64_t)bitmap_rank(BP, (uint32_t)r) - 1 : r;
+        int sub;
+        best = resolve_coarse(cs, g, logk, (uint32_t)lo, (uint32_t)hi, (uint32_t)l, (uint32_t)r, sub);
+        if (sub == SUB_WHOLE) {
+            best = resolve_query(T, nb, logk, lo, hi, (uint32_t)l, (uint32_t)r, pl, pr, hl, hr);
+        } else if (sub != SUB_NONE) {
+            Pending unused;
+            bool unused_flag = false;
+            if (sub & SUB_LEFT) {
+                const int64_t end_l = (((lo >> sh) + 1) << sh) - 1;
+                best = kmin(best, resolve_query(T, nb, logk, lo, end_l, (uint32_t)l, 0xffffffffu, pl, unused, hl,
+                                                unused_flag));
+            }
+            if (sub & SUB_RIGHT) {
+                // a part inside one block records its scan in the first slot
+                const int64_t start_r = (hi >> sh) << sh;
+                Pending a, b;
+                bool ha = false, hb = false;
+                best = kmin(best, resolve_query(T, nb, logk, start_r, hi, 0u, (uint32_t)r, a, b, ha, hb));
+                if (ha) { pr = a; hr = true; }
+                if (hb) { pr = b; hr = true; }
+            }
+        }
+    }
+    warp_drain_scans<Src, VEC>(src, n, hl, pl, best);
+    warp_drain_scans<Src, VEC>(src, n, hr, pr, best);
+    if (has) out[qid] = (int32_t)key_pos(best);
+    __syncwarp();
+}
+
 //   plain (CON = false): the source is A; query i covers [l_i, r_i].
 //   contracted (CON = true): the source is A_Q; query i covers
 //     A_Q[a_i .. b_i - 1] with a_i, b_i the ranks of l_i, r_i in the
@@ -366,18 +312,16 @@ __global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk
                                                     const uint2 *__restrict__ BP, const uint32_t *__restrict__ CP,
                                                     const uint16_t *__restrict__ CB,
                                                     int64_t n_a, int32_t *__restrict__ out, int64_t q,
-                                                    Residual *__restrict__ res, int64_t region, unsigned *err) {
-    // Phase A: each CTA answers the queries the coarse table settles and
-    // appends the others to its own region of `region` entries of the residual
-    // list (counted in shared memory, no global atomics).  Phase B: the same
-    // CTA then finishes its residual queries, with the coarse table still in
-    // shared memory.
+                                                    unsigned *err) {
+    // Phase A answers the queries the coarse table settles.  Each warp queues
+    // the others (their indices) in its own shared-memory queue, and as soon
+    // as 32 are queued it resolves them (phase B: fine table and edge scans),
+    // so the latency of that work overlaps the streaming of other warps.
+    constexpr int kQueue = 160;   // a step adds at most 128
     __shared__ uint64_t cs[kCoarseCap];
     __shared__ uint32_t cp[CON ? kCoarseBlocksMax : 1];
     __shared__ uint16_t cb[CON ? kBucketsMax : 1];
-    __shared__ uint32_t n_open;
-    if (threadIdx.x == 0) n_open = 0;
-    Residual *my = res + (int64_t)blockIdx.x * region;
+    __shared__ uint32_t queue[8][kQueue];
     const int64_t n = len.get();
     const int64_t nb = (n + (1ll << logk) - 1) >> logk;
     const Coarse g = coarse_geom(nb);
@@ -392,6 +336,13 @@ __global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    uint32_t *my = queue[threadIdx.x >> 5];
+    int nq = 0;   // queued (warp-uniform)
+    const int sh = logk + g.lc;
+    auto resolve = [&](int take) {
+        resolve_queued<Src, CON, VEC>(src, n, logk, T, nb, cs, g, L, R, BP, out, my + nq - take, take);
+        nq -= take;
+    };
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     // the next step's l, r are loaded before the current step is processed, so
@@ -439,7 +390,6 @@ __global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk
                 BL = use ? coarse_of(cp, cb, bs, (uint32_t)lq[i]) : 0u;
                 BR = use ? coarse_of(cp, cb, bs, (uint32_t)rq[i] - 1u) : 0u;
             } else {
-                const int sh = logk + g.lc;
                 BL = use ? (uint32_t)lq[i] >> sh : 0u;
                 BR = use ? (uint32_t)rq[i] >> sh : 0u;
             }
@@ -455,66 +405,23 @@ __global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk
             for (int i = 0; i < 4; ++i)
                 if (base + i < q) out[base + i] = o[i];
         }
-        // append the open queries' indices to the CTA's residual list: slots from
-        // four ballots, one shared atomic per warp
+        // queue the open queries' indices: slots from four ballots
         const unsigned lt = (1u << lane) - 1u;
         const unsigned b0 = __ballot_sync(0xffffffffu, need & 1u), b1 = __ballot_sync(0xffffffffu, need & 2u);
         const unsigned b2 = __ballot_sync(0xffffffffu, need & 4u), b3 = __ballot_sync(0xffffffffu, need & 8u);
-        const unsigned c0 = __popc(b0), c1 = __popc(b1), c2 = __popc(b2), c3 = __popc(b3);
-        const unsigned tot = c0 + c1 + c2 + c3;
-        if (tot) {
-            uint32_t sbase = 0;
-            if (lane == 0) sbase = atomicAdd(&n_open, tot);
-            sbase = __shfl_sync(0xffffffffu, sbase, 0);
-            if (need & 1u) my[sbase + __popc(b0 & lt)] = (uint32_t)base;
-            if (need & 2u) my[sbase + c0 + __popc(b1 & lt)] = (uint32_t)(base + 1);
-            if (need & 4u) my[sbase + c0 + c1 + __popc(b2 & lt)] = (uint32_t)(base + 2);
-            if (need & 8u) my[sbase + c0 + c1 + c2 + __popc(b3 & lt)] = (uint32_t)(base + 3);
+        const int c0 = __popc(b0), c1 = __popc(b1), c2 = __popc(b2), c3 = __popc(b3);
+        if (c0 + c1 + c2 + c3) {
+            if (need & 1u) my[nq + __popc(b0 & lt)] = (uint32_t)base;
+            if (need & 2u) my[nq + c0 + __popc(b1 & lt)] = (uint32_t)(base + 1);
+            if (need & 4u) my[nq + c0 + c1 + __popc(b2 & lt)] = (uint32_t)(base + 2);
+            if (need & 8u) my[nq + c0 + c1 + c2 + __popc(b3 & lt)] = (uint32_t)(base + 3);
+            nq += c0 + c1 + c2 + c3;
+            __syncwarp();
+            while (nq >= 32) resolve(32);
         }
         if (!CON && bad && err) atomicOr(err, ERR_QUERY_RANGE);
     }
-    __syncthreads();  // n_open is final and the region's entries are visible to the CTA
-    const int64_t cnt = n_open;
-    const int sh = logk + g.lc;
-    for (int64_t wb = (threadIdx.x >> 5) * 32; wb < cnt; wb += (blockDim.x >> 5) * 32) {
-        const int64_t idx = wb + lane;
-        const bool has = idx < cnt;
-        Pending pl, pr;
-        bool hl = false, hr = false;
-        uint64_t best = KEY_MAX;
-        uint32_t qid = 0;
-        if (has) {
-            qid = my[idx];
-            const int32_t l = L[qid], r = R[qid];
-            const int64_t lo = CON ? (int64_t)bitmap_rank(BP, (uint32_t)l) : l;
-            const int64_t hi = CON ? (int64_t)bitmap_rank(BP, (uint32_t)r) - 1 : r;
-            int sub;
-            best = resolve_coarse(cs, g, logk, (uint32_t)lo, (uint32_t)hi, (uint32_t)l, (uint32_t)r, sub);
-            if (sub == SUB_WHOLE) {
-                best = resolve_query(T, nb, logk, lo, hi, (uint32_t)l, (uint32_t)r, pl, pr, hl, hr);
-            } else if (sub != SUB_NONE) {
-                Pending unused;
-                bool unused_flag = false;
-                if (sub & SUB_LEFT) {
-                    const int64_t end_l = (((lo >> sh) + 1) << sh) - 1;
-                    best = kmin(best, resolve_query(T, nb, logk, lo, end_l, (uint32_t)l, 0xffffffffu, pl, unused, hl,
-                                                    unused_flag));
-                }
-                if (sub & SUB_RIGHT) {
-                    // a part inside one block records its scan in the first slot
-                    const int64_t start_r = (hi >> sh) << sh;
-                    Pending a, b;
-                    bool ha = false, hb = false;
-                    best = kmin(best, resolve_query(T, nb, logk, start_r, hi, 0u, (uint32_t)r, a, b, ha, hb));
-                    if (ha) { pr = a; hr = true; }
-                    if (hb) { pr = b; hr = true; }
-                }
-            }
-        }
-        warp_drain_scans<Src, VEC>(src, n, hl, pl, best);
-        warp_drain_scans<Src, VEC>(src, n, hr, pr, best);
-        if (has) out[qid] = (int32_t)key_pos(best);
-    }
+    if (nq > 0) resolve(nq);
 }
 
 }  // namespace rmq

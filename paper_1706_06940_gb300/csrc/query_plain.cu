@@ -1,5 +1,5 @@
 // query_plain.cu -- query answering of plain BbST (Sec. 3.1 step 4 over
-// blocks of A, Sec. 3.2).
+// blocks of A, Sec. 3.2, with the coarse level of Sec. 3.3).
 #include <algorithm>
 
 #include "query.cuh"
@@ -11,11 +11,9 @@ namespace {
 constexpr int kThreads = 256;
 }  // namespace
 
-// The kernel is the generic k_query of query.cuh over the int32 source.
+// The kernel is the generic k_query_two of query.cuh over the int32 source.
 cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint64_t *T, const uint64_t *Cs,
-                               int64_t nb, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
-                               void *res_ws, cudaStream_t s) {
-    (void)nb;
+                               const int32_t *l, const int32_t *r, int64_t q, int32_t *out, cudaStream_t s) {
     if (q <= 0) return cudaSuccess;
     const DevInfo di = dev_info();
     const bool vecq = ((reinterpret_cast<uintptr_t>(l) | reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
@@ -24,27 +22,14 @@ cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint
     if (!err) return cudaErrorUnknown;
     SrcI32 src{A};
     const Len len{n, nullptr};
-    if (res_ws) {
-        const ResidualPlan rp = residual_plan(q, di.sms);
-        Residual *res = static_cast<Residual *>(res_ws);
+    const int64_t ctas = query_ctas(q, di.sms);
 #define RMQ_LQ2(VQ, V) \
-    k_query_two<SrcI32, false, VQ, V><<<(unsigned)rp.ctas, kThreads, 0, s>>>(src, len, logk, T, Cs, l, r, nullptr, nullptr, nullptr, n, out, q, res, rp.region, err)
-        if (vecq && vec) RMQ_LQ2(true, true);
-        else if (vecq) RMQ_LQ2(true, false);
-        else if (vec) RMQ_LQ2(false, true);
-        else RMQ_LQ2(false, false);
+    k_query_two<SrcI32, false, VQ, V><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T, Cs, l, r, nullptr, nullptr, nullptr, n, out, q, err)
+    if (vecq && vec) RMQ_LQ2(true, true);
+    else if (vecq) RMQ_LQ2(true, false);
+    else if (vec) RMQ_LQ2(false, true);
+    else RMQ_LQ2(false, false);
 #undef RMQ_LQ2
-        note_launches(1);
-        return cudaGetLastError();
-    }
-    const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(q, 128 * (kThreads / 32)), (int64_t)di.sms * 2));
-#define RMQ_LQ(VQ, V) \
-    k_query<SrcI32, VQ, V><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T, Cs, l, r, n, out, q, err)
-    if (vecq && vec) RMQ_LQ(true, true);
-    else if (vecq) RMQ_LQ(true, false);
-    else if (vec) RMQ_LQ(false, true);
-    else RMQ_LQ(false, false);
-#undef RMQ_LQ
     note_launches(1);
     return cudaGetLastError();
 }

@@ -172,14 +172,16 @@ cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, 
                                 bool two_level = false, uint64_t *Cs = nullptr);
 // Entries of the two-level block table (levels 0 .. lc) for nb blocks.
 inline int64_t two_level_entries(int64_t nb) { return nb < 1 ? 0 : nb * (coarse_geom(nb).lc + 1); }
-// Two-phase query: kQueryCtasPerSm CTAs per SM; each CTA owns a region of the
-// residual list sized for every query it can see.
-// With res_ws == nullptr the query runs as one fused kernel that needs no scratch.
-constexpr int kQueryCtasPerSm = 4;    // resident CTAs per SM (32 KB shared memory, <= 64 registers)
-struct ResidualPlan {
-    int64_t ctas;    // phase-A CTAs
-    int64_t region;  // entries per CTA region
-};
+// Query kernel: kQueryCtasPerSm CTAs per SM (<= 43 KB shared memory, <= 64
+// registers), one wave, 8 warps of 128 queries per step.
+constexpr int kQueryCtasPerSm = 4;
+inline int64_t query_ctas(int64_t q, int sms) {
+    const int64_t steps = (q + 127) / 128;
+    int64_t ctas = (steps + 7) / 8;
+    const int64_t cap = (int64_t)sms * kQueryCtasPerSm;
+    if (ctas > cap) ctas = cap;
+    return ctas < 1 ? 1 : ctas;
+}
 // Coarse index of the contracted form: CP[j] = P_{j 2^sh}, the position in A
 // where coarse block j of A_Q begins (sh = logk_con + lc), and for buckets of
 // 2^s positions, CB[i] = the last coarse block that begins at or before
@@ -194,24 +196,10 @@ __host__ __device__ inline int bucket_shift(int64_t n) {
     return s;
 }
 __host__ __device__ inline int64_t bucket_count(int64_t n) { return ((n - 1) >> bucket_shift(n)) + 1; }
-constexpr int kQueryCtasPerSmCon = 4;
-inline ResidualPlan residual_plan(int64_t q, int sms, int per_sm = kQueryCtasPerSm) {
-    const int64_t batches = (q + 127) / 128;                     // 4 queries x 32 lanes per warp step
-    int64_t ctas = (batches + 7) / 8;
-    const int64_t cap = (int64_t)sms * per_sm;                   // one wave: every CTA resident at once
-    if (ctas > cap) ctas = cap;
-    if (ctas < 1) ctas = 1;
-    const int64_t warps = ctas * 8;
-    const int64_t per_warp = (batches + warps - 1) / warps;       // warp steps per warp
-    return ResidualPlan{ctas, per_warp * 8 * 128};
-}
-inline size_t query_residual_bytes(int64_t q, int sms, int per_sm = kQueryCtasPerSm) {
-    const ResidualPlan p = residual_plan(q, sms, per_sm);
-    return (size_t)(p.ctas * p.region) * 4;
-}
+// Plain-form query over a two-level table; Cs == nullptr: the coarse table is
+// built by every query CTA from level lc of T.
 cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint64_t *T, const uint64_t *Cs,
-                               int64_t nb, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
-                               void *res_ws, cudaStream_t s);
+                               const int32_t *l, const int32_t *r, int64_t q, int32_t *out, cudaStream_t s);
 
 // Many arrays in one persistent launch (multi.cu).
 constexpr int kMultiMax = 1024;   // arrays per launch (their descriptors travel as a kernel parameter)
