@@ -340,30 +340,50 @@ __device__ __forceinline__ void mark_bit(uint32_t *bw, uint32_t p) {
 }
 
 // Marks both ends of every query.  An invalid query marks position 0 (the
-// pair (0, 0) of the sort) and raises the error word.
+// pair (0, 0) of the sort) and raises the error word.  The warp moves in
+// steps of 32 consecutive vectors (4 queries per lane).  Endpoints that crowd
+// into few bit words (many queries sharing an end) would serialise their
+// reductions on one address; when neighbouring lanes of the warp hit the same
+// word, each lane first reads the word and skips the reduction if its bit is
+// already set.
 __global__ void __launch_bounds__(kT) k_mark_endpoints(const int32_t *__restrict__ L, const int32_t *__restrict__ R,
                                                        int64_t q, int64_t n, uint32_t *__restrict__ bw,
                                                        unsigned *err) {
     bool bad = false;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-    auto mark = [&](int32_t l, int32_t r) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    auto mark1 = [&](bool has, uint32_t p) {
+        const uint32_t w = has ? (p >> 5) : 0xffffffffu - (uint32_t)lane;   // an absent end shares no word
+        const bool crowded = __any_sync(0xffffffffu, __shfl_xor_sync(0xffffffffu, w, 1) == w);
+        if (!has) return;
+        const uint32_t bit = 1u << (p & 31);
+        if (crowded && (__ldcg(bw + 2 * (size_t)w) & bit)) return;
+        mark_bit(bw, p);
+    };
+    auto mark = [&](bool has, int32_t l, int32_t r) {
         const bool ok = l >= 0 && r >= l && (int64_t)r < n;
-        bad |= !ok;
-        mark_bit(bw, ok ? (uint32_t)l : 0u);
-        mark_bit(bw, ok ? (uint32_t)r : 0u);
+        bad |= has && !ok;
+        mark1(has, ok ? (uint32_t)l : 0u);
+        mark1(has, ok ? (uint32_t)r : 0u);
     };
     int64_t done = 0;
     if (((reinterpret_cast<uintptr_t>(L) | reinterpret_cast<uintptr_t>(R)) & 15) == 0) {
         const int64_t nv = q / 4;
-        for (int64_t v = tid; v < nv; v += nthr) {
-            const int4 l4 = __ldcs(reinterpret_cast<const int4 *>(L) + v);
-            const int4 r4 = __ldcs(reinterpret_cast<const int4 *>(R) + v);
-            mark(l4.x, r4.x); mark(l4.y, r4.y); mark(l4.z, r4.z); mark(l4.w, r4.w);
+        for (int64_t v0 = warp * 32; v0 < nv; v0 += nwarps * 32) {
+            const int64_t v = v0 + lane;
+            const bool has = v < nv;
+            const int4 l4 = has ? __ldcs(reinterpret_cast<const int4 *>(L) + v) : make_int4(0, 0, 0, 0);
+            const int4 r4 = has ? __ldcs(reinterpret_cast<const int4 *>(R) + v) : make_int4(0, 0, 0, 0);
+            mark(has, l4.x, r4.x); mark(has, l4.y, r4.y); mark(has, l4.z, r4.z); mark(has, l4.w, r4.w);
         }
         done = nv * 4;
     }
-    for (int64_t i = done + tid; i < q; i += nthr) mark(__ldcs(L + i), __ldcs(R + i));
+    for (int64_t i0 = done + warp * 32; i0 < q; i0 += nwarps * 32) {
+        const int64_t i = i0 + lane;
+        const bool has = i < q;
+        mark(has, has ? __ldcs(L + i) : 0, has ? __ldcs(R + i) : 0);
+    }
     if (bad) atomicOr(err, ERR_QUERY_RANGE);
 }
 
