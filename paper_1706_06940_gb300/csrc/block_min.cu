@@ -20,6 +20,7 @@ constexpr int kThreads = 256;
 // while its most recent part is still in L2).
 template <class Src, int UNR, bool VEC, bool REV>
 __global__ void __launch_bounds__(kThreads) k_block_min_warp(Src src, Len len, int logk, uint64_t *__restrict__ T0) {
+    pdl_wait();
     constexpr int EPV = Src::EPV;
     const int64_t n = len.get();
     const int64_t K = 1ll << logk;
@@ -58,6 +59,7 @@ __global__ void __launch_bounds__(kThreads) k_block_min_warp(Src src, Len len, i
 // per warp row, 4 rows in flight; the reduction is a width-G shuffle.
 template <class Src, bool VEC, bool REV>
 __global__ void __launch_bounds__(kThreads) k_block_min_group(Src src, Len len, int logk, uint64_t *__restrict__ T0) {
+    pdl_wait();
     constexpr int EPV = Src::EPV;
     const int64_t n = len.get();
     const int64_t K = 1ll << logk;
@@ -109,14 +111,14 @@ cudaError_t block_min_dispatch(Src src, Len len, int64_t n_max, int logk, uint64
     if (vpb >= 32) {
         const int64_t ctas = std::min<int64_t>(cdiv(nb, kThreads / 32), (int64_t)di.sms * 8);
         const int vpl = vpb / 32;
-        if (vpl >= 8) k_block_min_warp<Src, 8, VEC, REV><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0);
-        else if (vpl >= 4) k_block_min_warp<Src, 4, VEC, REV><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0);
-        else if (vpl >= 2) k_block_min_warp<Src, 2, VEC, REV><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0);
-        else k_block_min_warp<Src, 1, VEC, REV><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0);
+        if (vpl >= 8) launch_pdl(k_block_min_warp<Src, 8, VEC, REV>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0);
+        else if (vpl >= 4) launch_pdl(k_block_min_warp<Src, 4, VEC, REV>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0);
+        else if (vpl >= 2) launch_pdl(k_block_min_warp<Src, 2, VEC, REV>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0);
+        else launch_pdl(k_block_min_warp<Src, 1, VEC, REV>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0);
     } else {
         const int64_t nvec = nb * vpb;
         const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(nvec, 128 * (kThreads / 32)), (int64_t)di.sms * 8));
-        k_block_min_group<Src, VEC, REV><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T0);
+        launch_pdl(k_block_min_group<Src, VEC, REV>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0);
     }
     note_launches(1);
     return cudaGetLastError();

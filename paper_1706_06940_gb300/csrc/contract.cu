@@ -349,6 +349,7 @@ __device__ __forceinline__ void mark_bit(uint32_t *bw, uint32_t p) {
 __global__ void __launch_bounds__(kT) k_mark_endpoints(const int32_t *__restrict__ L, const int32_t *__restrict__ R,
                                                        int64_t q, int64_t n, uint32_t *__restrict__ bw,
                                                        unsigned *err) {
+    pdl_wait();
     bool bad = false;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -400,6 +401,7 @@ __global__ void __launch_bounds__(kT) k_mark_positions(const uint32_t *__restric
 // owns 512 consecutive entries, lane-interleaved rows of 32).
 __global__ void __launch_bounds__(kT) k_bits_partial(const uint2 *__restrict__ BP, int64_t nbp,
                                                      uint32_t *__restrict__ partial) {
+    pdl_wait();
     __shared__ uint32_t wsum[kT / 32];
     const int64_t base = (int64_t)blockIdx.x * kTile;
     uint32_t c = 0;
@@ -426,6 +428,7 @@ __global__ void __launch_bounds__(kT) k_bits_final(uint2 *__restrict__ BP, int64
                                                    const uint32_t *__restrict__ partial, int64_t *m_dev,
                                                    int64_t ntA, uint64_t *__restrict__ AQ, int64_t n, int logk_q,
                                                    uint32_t *__restrict__ CP, uint16_t *__restrict__ CB) {
+    pdl_wait();
     __shared__ uint32_t wsum[kT / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)w * (32 * kIPT);
@@ -526,6 +529,7 @@ constexpr int kContractSmem = (kT / 32) * kATile * 8;   // per warp: the tile, t
 template <bool VEC>
 __global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const uint2 *__restrict__ BP,
                                                  const int64_t *m_dev, int64_t ntA, uint64_t *__restrict__ H) {
+    pdl_wait();
     extern __shared__ uint64_t csmem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint64_t *slot = csmem + (size_t)w * kATile;                      // 1024 slots per warp
@@ -734,8 +738,8 @@ cudaError_t bitmap_ranks(uint2 *BP, int64_t n, int64_t *m_dev, uint64_t *AQ, uin
                          int logk_q = 0, uint32_t *CP = nullptr, uint16_t *CB = nullptr) {
     const int64_t nbp = bitmap_entries(n);
     const int64_t tiles = cdiv(nbp, kTile);
-    k_bits_partial<<<(unsigned)tiles, kT, 0, s>>>(BP, nbp, aux);
-    k_bits_final<<<(unsigned)tiles, kT, 0, s>>>(BP, nbp, aux, m_dev, AQ ? cdiv(n, kATile) : 0, AQ, n, logk_q, CP, CB);
+    launch_pdl(k_bits_partial, (unsigned)tiles, kT, 0, s, BP, nbp, aux);
+    launch_pdl(k_bits_final, (unsigned)tiles, kT, 0, s, BP, nbp, aux, m_dev, AQ ? cdiv(n, kATile) : 0, AQ, n, logk_q, CP, CB);
     note_launches(2);
     return cudaGetLastError();
 }
@@ -755,9 +759,9 @@ cudaError_t contract_bitmap(const int32_t *A, int64_t n, const uint2 *BP, const 
         attr[di.device] = true;
     }
     if ((reinterpret_cast<uintptr_t>(A) & 15) == 0)
-        k_contract<true><<<(unsigned)ctas, kT, kContractSmem, s>>>(src, n, BP, m_dev, ntA, AQ);
+        launch_pdl(k_contract<true>, (unsigned)ctas, kT, kContractSmem, s, src, n, BP, m_dev, ntA, AQ);
     else
-        k_contract<false><<<(unsigned)ctas, kT, kContractSmem, s>>>(src, n, BP, m_dev, ntA, AQ);
+        launch_pdl(k_contract<false>, (unsigned)ctas, kT, kContractSmem, s, src, n, BP, m_dev, ntA, AQ);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -775,7 +779,7 @@ cudaError_t endpoint_bitmap(const int32_t *l, const int32_t *r, int64_t q, int64
     if (e != cudaSuccess) return e;
     const DevInfo di = dev_info();
     const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(cdiv(q, 4), kT), (int64_t)di.sms * 8));
-    k_mark_endpoints<<<(unsigned)ctas, kT, 0, s>>>(l, r, q, n, reinterpret_cast<uint32_t *>(BP), err);
+    launch_pdl(k_mark_endpoints, (unsigned)ctas, kT, 0, s, l, r, q, n, reinterpret_cast<uint32_t *>(BP), err);
     note_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (st) st->mark(s);
@@ -850,9 +854,9 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     SrcU64 src{AQ};
     const int64_t qctas = query_ctas(q, di.sms);                                                        // step 4
     if (vecq)
-        k_query_two<SrcU64, true, true, true><<<(unsigned)qctas, kT, 0, s>>>(src, lenq, logk_con, T, nullptr, l, r, BP, CP, CB, n, out, q, nullptr);
+        launch_pdl(k_query_two<SrcU64, true, true, true>, (unsigned)qctas, kT, 0, s, src, lenq, logk_con, T, nullptr, l, r, BP, CP, CB, n, out, q, nullptr);
     else
-        k_query_two<SrcU64, true, false, true><<<(unsigned)qctas, kT, 0, s>>>(src, lenq, logk_con, T, nullptr, l, r, BP, CP, CB, n, out, q, nullptr);
+        launch_pdl(k_query_two<SrcU64, true, false, true>, (unsigned)qctas, kT, 0, s, src, lenq, logk_con, T, nullptr, l, r, BP, CP, CB, n, out, q, nullptr);
     note_launches(1);
     e = cudaGetLastError();
     st->mark(s);

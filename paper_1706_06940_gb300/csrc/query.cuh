@@ -313,6 +313,7 @@ __global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk
                                                     const uint16_t *__restrict__ CB,
                                                     int64_t n_a, int32_t *__restrict__ out, int64_t q,
                                                     unsigned *err) {
+    pdl_wait();
     // Phase A answers the queries the coarse table settles.  Each warp queues
     // the others (their indices) in its own shared-memory queue, and as soon
     // as 32 are queued it resolves them (phase B: fine table and edge scans),

@@ -24,7 +24,7 @@ cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint
     const Len len{n, nullptr};
     const int64_t ctas = query_ctas(q, di.sms);
 #define RMQ_LQ2(VQ, V) \
-    k_query_two<SrcI32, false, VQ, V><<<(unsigned)ctas, kThreads, 0, s>>>(src, len, logk, T, Cs, l, r, nullptr, nullptr, nullptr, n, out, q, err)
+    launch_pdl(k_query_two<SrcI32, false, VQ, V>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T, Cs, l, r, nullptr, nullptr, nullptr, n, out, q, err)
     if (vecq && vec) RMQ_LQ2(true, true);
     else if (vecq) RMQ_LQ2(true, false);
     else if (vec) RMQ_LQ2(false, true);

@@ -67,6 +67,30 @@ __host__ __device__ __forceinline__ Coarse coarse_geom(int64_t nb) {
     }
 }
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may be
+// scheduled while the previous kernel of the stream drains (its launch and
+// set-up overlap that kernel's tail); it calls pdl_wait() before it reads or
+// writes anything, which waits for the previous kernel to complete and its
+// memory to be visible.  For a kernel launched without the attribute the wait
+// is a no-op.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <class... KArgs, class... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Streaming 128-bit load that does not allocate in L1 (data read once).
 __device__ __forceinline__ int4 ld_stream_v4(const int4 *p) {
     int4 v;

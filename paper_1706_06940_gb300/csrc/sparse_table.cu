@@ -23,6 +23,7 @@ constexpr int kThreads = 256;
 template <int R, int LV>
 __global__ void __launch_bounds__(kThreads) k_st_round(uint64_t *__restrict__ T, Len len, int logk, int b, int S,
                                                       bool two_level) {
+    pdl_wait();
     const int64_t n = len.get();
     const int64_t nb = (n + (1ll << logk) - 1) >> logk;
     if (nb < 2) return;
@@ -70,6 +71,7 @@ __global__ void __launch_bounds__(kThreads) k_st_round(uint64_t *__restrict__ T,
 // CTA's shared memory, since the coarse table has at most kCoarseCap entries.
 __global__ void __launch_bounds__(1024) k_coarse_table(const uint64_t *__restrict__ T, Len len, int logk,
                                                        uint64_t *__restrict__ Cs) {
+    pdl_wait();
     __shared__ uint64_t c[kCoarseCap];
     const int64_t n = len.get();
     const int64_t nb = (n + (1ll << logk) - 1) >> logk;
@@ -118,7 +120,7 @@ cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, 
     {
         const int64_t ctas = cdiv(nb_max, kS0);
         if (top > 0) {
-            k_st_round<1, kLV0><<<(unsigned)ctas, kThreads, smem0, s>>>(T, len, logk, 0, kS0, two);
+            launch_pdl(k_st_round<1, kLV0>, (unsigned)ctas, kThreads, smem0, s, T, len, logk, 0, kS0, two);
             note_launches(1);
         }
         cudaError_t e = cudaGetLastError();
@@ -129,13 +131,13 @@ cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, 
         const int64_t ngroups = stride / 32;
         const int64_t nstr = cdiv(nb_max, stride);
         const int64_t ctas = ngroups * cdiv(nstr, kS1);
-        k_st_round<32, kLV1><<<(unsigned)ctas, kThreads, smem1, s>>>(T, len, logk, b, kS1, two);
+        launch_pdl(k_st_round<32, kLV1>, (unsigned)ctas, kThreads, smem1, s, T, len, logk, b, kS1, two);
         note_launches(1);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     if (two && Cs) {
-        k_coarse_table<<<1, 1024, 0, s>>>(T, len, logk, Cs);
+        launch_pdl(k_coarse_table, 1, 1024, 0, s, T, len, logk, Cs);
         note_launches(1);
         return cudaGetLastError();
     }
