@@ -540,13 +540,11 @@ __global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const ui
     const int64_t nfull = n / kATile;        // tiles wholly inside [0, n)
     const int64_t nv = n / 4;                // vectors wholly inside [0, n)
     const int64_t nw = (n + 31) >> 5;        // bitmap words; BP[nw] is the end entry
-    for (int64_t t = warp; t < ntA; t += nwarps) {
-        // the tile's cells are requested together with its bitmap words (one
-        // round trip); tiles outside [P_0, P_{m-1}] are skipped after the fact
+    // a tile's cells and its bitmap words, requested together
+    auto load_tile = [&](int64_t t, int4 (&v)[8], uint2 &e) {
         const int64_t wi = t * 32 + lane;
-        const uint2 e = __ldg(BP + (wi < nw ? wi : nw));
+        e = __ldg(BP + (wi < nw ? wi : nw));
         const int64_t ts = t * kATile;
-        int4 v[8];
         if (VEC && t < nfull) {
             const int4 *tp = reinterpret_cast<const int4 *>(src.a) + ts / 4 + lane;
 #pragma unroll
@@ -567,6 +565,12 @@ __global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const ui
                 }
             }
         }
+    };
+    for (int64_t t = warp; t < ntA; t += nwarps) {
+        const int64_t ts = t * kATile;
+        int4 v[8];
+        uint2 e;
+        load_tile(t, v, e);
         const uint32_t word = e.x;
         const int32_t s_t = (int32_t)__shfl_sync(0xffffffffu, e.y, 0) - 1;      // open before the tile
         const uint32_t nbits = __popc(word);
@@ -750,14 +754,19 @@ cudaError_t contract_bitmap(const int32_t *A, int64_t n, const uint2 *BP, const 
                             cudaStream_t s) {
     const int64_t ntA = cdiv(n, kATile);
     const DevInfo di = dev_info();
-    const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(ntA, kT / 32), (int64_t)di.sms * 3));
     SrcI32 src{A};
     static bool attr[64] = {false};
+    static int occ[64] = {0};
     if (di.device >= 0 && di.device < 64 && !attr[di.device]) {
         cudaFuncSetAttribute(k_contract<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kContractSmem);
         cudaFuncSetAttribute(k_contract<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kContractSmem);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_contract<true>, kT, kContractSmem);
+        occ[di.device] = std::max(1, per_sm);
         attr[di.device] = true;
     }
+    const int per_sm = (di.device >= 0 && di.device < 64) ? occ[di.device] : 1;   // one resident wave
+    const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(ntA, kT / 32), (int64_t)di.sms * per_sm));
     if ((reinterpret_cast<uintptr_t>(A) & 15) == 0)
         launch_pdl(k_contract<true>, (unsigned)ctas, kT, kContractSmem, s, src, n, BP, m_dev, ntA, AQ);
     else
