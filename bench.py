@@ -51,8 +51,8 @@ def parse_args():
     p.add_argument("--duration", type=float, default=2.0, help="served: seconds of arrivals")
     p.add_argument("--rate", type=float, default=1e4, help="served: requests per second")
     p.add_argument("--arrays", type=int, default=512)
-    p.add_argument("--n", type=float, default=1e8)
-    p.add_argument("--q", type=float, default=1e7)
+    p.add_argument("--n", "--array-size", dest="n", type=float, default=1e8)
+    p.add_argument("--q", "--num-queries", dest="q", type=float, default=1e7)
     p.add_argument("--seed", type=int, default=1002)
     p.add_argument("--variant", choices=["both", "plain", "contracted"], default="both")
     p.add_argument("--k", type=int, default=0, help="plain-form block size (0 = tuned)")

@@ -126,8 +126,9 @@ rmq_status rmq_batch_timed(const int32_t *A, int64_t n, const int32_t *l, const 
 /* rmq_batch_ex on HOST buffers: copies A, l, r to the device, answers, copies
  * out back, and returns after out_host is written (synchronous).  Host
  * buffers may be pageable or pinned; pinned ones copy faster.  Device
- * buffers come from the stream-ordered pool.  Invalid queries are reported
- * in the return value (RMQ_ERR_QUERY_RANGE) as well as by -1 entries. */
+ * buffers come from the stream-ordered pool.  Invalid queries answer -1; the
+ * call returns what rmq_stream_status returns after the batch (the device
+ * error word, so RMQ_ERR_QUERY_RANGE for invalid queries), and clears it. */
 rmq_status rmq_batch_host(const int32_t *A_host, int64_t n, const int32_t *l_host,
                           const int32_t *r_host, int64_t q, int32_t *out_host,
                           const rmq_opts *opts, void *stream);

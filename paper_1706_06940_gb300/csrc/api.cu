@@ -259,10 +259,9 @@ rmq_status rmq_batch_host(const int32_t *A_host, int64_t n, const int32_t *l_hos
         if ((st = rmq_batch_ex(dA, n, dl, dr, q, dout, opts, stream)) != RMQ_OK) return st;
         if ((e = cudaMemcpyAsync(out_host, dout, bq, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_status(e);
     }
-    if (cudaStreamSynchronize(s) != cudaSuccess) return RMQ_ERR_CUDA;
-    for (int64_t i = 0; i < q; ++i)
-        if (out_host[i] < 0) return RMQ_ERR_QUERY_RANGE;
-    return RMQ_OK;
+    // invalid queries were counted in the device error word: report (and
+    // clear) it, as rmq_stream_status does, without scanning out_host
+    return rmq_stream_status(stream);
 }
 
 rmq_status rmq_batch_multi(const rmq_array *arrays, int32_t H, const int32_t *l, const int32_t *r, int32_t *out,
