@@ -140,20 +140,90 @@ __device__ __forceinline__ uint64_t warp_scan_min(const Src &src, int64_t n, int
     return warp_min(best);
 }
 
-// Run every queued scan of the warp, one at a time, each with all 32 lanes.
+// Run every queued scan of the warp.  Long scans, or a single one, run one at
+// a time on the whole warp (warp_scan_min).  When several are queued and all
+// are short enough for one round of a smaller team, the warp splits into 2 or
+// 4 teams of 16 or 8 lanes that run as many scans at once (consecutive-lane
+// 16-byte vectors, two per lane), so that their latencies overlap.
 template <class Src, bool VEC>
 __device__ __forceinline__ void warp_drain_scans(const Src &src, int64_t n, bool has, const Pending &p,
                                                  uint64_t &best) {
+    constexpr int EPV = Src::EPV;
     const int lane = threadIdx.x & 31;
     unsigned pend = __ballot_sync(0xffffffffu, has);
+    const int64_t nvfull = n / EPV;
+    if (!pend) return;
+    // the longest queued scan, in 16-byte vectors, decides whether teams pay
+    int fit = 1;
+    if (pend & (pend - 1)) {
+        const uint32_t len = has ? (uint32_t)(p.hi / EPV - p.lo / EPV + 1) : 0u;
+        const uint32_t maxlen = __reduce_max_sync(0xffffffffu, len);
+        fit = maxlen <= 16u ? 4 : (maxlen <= 32u ? 2 : 1);   // teams whose one round covers it
+    }
     while (pend) {
-        const int s = __ffs(pend) - 1;
-        pend &= pend - 1;
-        const int64_t lo = __shfl_sync(0xffffffffu, p.lo, s);
-        const int64_t hi = __shfl_sync(0xffffffffu, p.hi, s);
-        const uint32_t lb = __shfl_sync(0xffffffffu, p.lb, s);
-        const uint64_t v = warp_scan_min<Src, VEC>(src, n, lo, hi, lb);
-        if (lane == s) best = kmin(best, v);
+        const int cnt = __popc(pend);
+        if (cnt == 1 || fit == 1) {
+            const int s = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const int64_t lo = __shfl_sync(0xffffffffu, p.lo, s);
+            const int64_t hi = __shfl_sync(0xffffffffu, p.hi, s);
+            const uint32_t lb = __shfl_sync(0xffffffffu, p.lb, s);
+            const uint64_t v = warp_scan_min<Src, VEC>(src, n, lo, hi, lb);
+            if (lane == s) best = kmin(best, v);
+            continue;
+        }
+        const int nteams = cnt >= 4 ? fit : 2;
+        const int ts = 32 / nteams;                  // lanes per team
+        const int team = lane / ts, tl = lane % ts;
+        // the scans taken now: the nteams lowest pending lanes
+        unsigned taken = 0, x = pend;
+        for (int t = 0; t < nteams && x; ++t) {
+            taken |= x & (~x + 1u);
+            x &= x - 1;
+        }
+        pend &= ~taken;
+        unsigned y = taken;
+        for (int t = 0; t < team && y; ++t) y &= y - 1;
+        const int s = y ? __ffs(y) - 1 : -1;         // the lane whose scan this team runs
+        const int src_lane = s < 0 ? 0 : s;
+        const int64_t lo = __shfl_sync(0xffffffffu, p.lo, src_lane);
+        const int64_t hi = s < 0 ? lo - 1 : __shfl_sync(0xffffffffu, p.hi, src_lane);
+        const uint32_t lb = __shfl_sync(0xffffffffu, p.lb, src_lane);
+        const int64_t vlo = lo / EPV, vhi = hi / EPV;
+        const unsigned tmask = (ts == 32 ? 0xffffffffu : ((1u << ts) - 1u)) << (team * ts);
+        uint64_t tb = KEY_MAX;
+        bool live = s >= 0 && hi >= lo;
+        for (int64_t v0 = vlo; __any_sync(0xffffffffu, live); v0 += 2 * ts) {
+            if (live) {
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int64_t vi = v0 + u * ts + tl;
+                    if (vi <= vhi) {
+                        uint64_t kk[EPV];
+                        if (vi < nvfull) {
+                            src.template vec<VEC>(vi, kk);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < EPV; ++e) kk[e] = vi * EPV + e < n ? src.one(vi * EPV + e) : KEY_MAX;
+                        }
+#pragma unroll
+                        for (int e = 0; e < EPV; ++e) {
+                            const int64_t i = vi * EPV + e;
+                            if (i >= lo && i <= hi) tb = kmin(tb, kk[e]);
+                        }
+                    }
+                }
+            }
+            // a team stops when its range is done or it met its block minimum
+            const unsigned met = __ballot_sync(0xffffffffu, live && key_hi(tb) == lb) & tmask;
+            if (v0 + 2 * ts > vhi || met) live = false;
+        }
+        for (int off = ts / 2; off > 0; off >>= 1) tb = kmin(tb, __shfl_xor_sync(0xffffffffu, tb, off));
+        // the lane of each taken scan collects its team's result
+        const bool mine = (taken >> lane) & 1u;
+        const int my_team = __popc(taken & ((1u << lane) - 1u));
+        const uint64_t v = __shfl_sync(0xffffffffu, tb, (mine ? my_team : 0) * ts);
+        if (mine) best = kmin(best, v);
     }
 }
 
