@@ -157,16 +157,19 @@ rmq_status batch_plain(const int32_t *A, int64_t n, const int32_t *l, const int3
     const int64_t nb = cdiv(n, 1ll << logk);
     Workspace ws;
     const int64_t te = two_level_entries(nb);
-    rmq_status st = ws.alloc((size_t)te * 8, s);
+    // the 128-cell minima of the two-level layout (Sec. 3.3) when k >= 128
+    const int64_t m1 = logk >= 7 ? cdiv(n, 128) : 0;
+    rmq_status st = ws.alloc((size_t)(te + m1) * 8, s);
     if (st != RMQ_OK) return st;
     uint64_t *T = static_cast<uint64_t *>(ws.p);
+    uint64_t *M1 = m1 ? T + te : nullptr;
     cudaError_t e;
     sg->mark(s);
-    if ((e = launch_block_minima_i32(A, n, logk, T, s)) != cudaSuccess) return cuda_status(e);
+    if ((e = launch_block_minima_i32(A, n, logk, T, s, M1)) != cudaSuccess) return cuda_status(e);
     sg->mark(s);
     if ((e = launch_sparse_table(T, Len{n, nullptr}, logk, nb, s, true)) != cudaSuccess) return cuda_status(e);
     sg->mark(s);
-    e = launch_query_plain(A, n, logk, T, nullptr, l, r, q, out, s);
+    e = launch_query_plain(A, n, logk, T, nullptr, l, r, q, out, s, M1);
     sg->mark(s);
     return cuda_status(e);
 }

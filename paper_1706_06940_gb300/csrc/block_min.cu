@@ -18,8 +18,14 @@ constexpr int kThreads = 256;
 // are loaded before any is used to keep enough bytes in flight.  With REV
 // the blocks are visited from the end (a sequence just written is then read
 // while its most recent part is still in L2).
-template <class Src, int UNR, bool VEC, bool REV>
-__global__ void __launch_bounds__(kThreads) k_block_min_warp(Src src, Len len, int logk, uint64_t *__restrict__ T0) {
+// With M1 (int32 source, k >= 128) the kernel also stores the minimum of
+// every 128 consecutive cells (one vector per lane), the small blocks of the
+// paper's two-level layout (Sec. 3.3, k1 = 128 dividing k2 = k): a 32-bit
+// warp reduction of the values, then the leftmost lane holding the minimum.
+// M1 has ceil(n / 128) entries.
+template <class Src, int UNR, bool VEC, bool REV, bool WM1>
+__global__ void __launch_bounds__(kThreads) k_block_min_warp(Src src, Len len, int logk, uint64_t *__restrict__ T0,
+                                                             uint64_t *__restrict__ M1) {
     pdl_wait();
     constexpr int EPV = Src::EPV;
     const int64_t n = len.get();
@@ -40,9 +46,19 @@ __global__ void __launch_bounds__(kThreads) k_block_min_warp(Src src, Len len, i
 #pragma unroll
             for (int x = 0; x < UNR; ++x) src.template vec<VEC>(v0 + (int64_t)(u + x) * 32, kk[x]);
 #pragma unroll
-            for (int x = 0; x < UNR; ++x)
+            for (int x = 0; x < UNR; ++x) {
+                uint64_t rk = KEY_MAX;
 #pragma unroll
-                for (int e = 0; e < EPV; ++e) best = kmin(best, kk[x][e]);
+                for (int e = 0; e < EPV; ++e) rk = kmin(rk, kk[x][e]);
+                best = kmin(best, rk);
+                if (WM1) {   // the row of 128 cells this vector belongs to
+                    const uint32_t hv = (uint32_t)(rk >> 32);
+                    const uint32_t mh = __reduce_min_sync(0xffffffffu, hv);
+                    const int f = __ffs(__ballot_sync(0xffffffffu, hv == mh)) - 1;
+                    const uint64_t rowkey = __shfl_sync(0xffffffffu, rk, f);
+                    if (lane == 0) M1[b * (K >> 7) + u + x] = rowkey;
+                }
+            }
         }
         best = warp_min(best);
         if (lane == 0) T0[b] = best;
@@ -52,6 +68,14 @@ __global__ void __launch_bounds__(kThreads) k_block_min_warp(Src src, Len len, i
         for (int64_t i = nfull * K + lane; i < n; i += 32) best = kmin(best, src.one(i));
         best = warp_min(best);
         if (lane == 0) T0[nfull] = best;
+        if (WM1) {
+            for (int64_t row = (nfull * K) >> 7; (row << 7) < n; ++row) {
+                uint64_t rk = KEY_MAX;
+                for (int64_t i = (row << 7) + lane; i < n && i < ((row + 1) << 7); i += 32) rk = kmin(rk, src.one(i));
+                rk = warp_min(rk);
+                if (lane == 0) M1[row] = rk;
+            }
+        }
     }
 }
 
@@ -101,7 +125,8 @@ __global__ void __launch_bounds__(kThreads) k_block_min_group(Src src, Len len, 
 }
 
 template <class Src, bool VEC, bool REV>
-cudaError_t block_min_dispatch(Src src, Len len, int64_t n_max, int logk, uint64_t *T0, cudaStream_t s) {
+cudaError_t block_min_dispatch(Src src, Len len, int64_t n_max, int logk, uint64_t *T0, cudaStream_t s,
+                               uint64_t *M1 = nullptr) {
     constexpr int EPV = Src::EPV;
     const DevInfo di = dev_info();
     const int64_t K = 1ll << logk;
@@ -111,10 +136,14 @@ cudaError_t block_min_dispatch(Src src, Len len, int64_t n_max, int logk, uint64
     if (vpb >= 32) {
         const int64_t ctas = std::min<int64_t>(cdiv(nb, kThreads / 32), (int64_t)di.sms * 8);
         const int vpl = vpb / 32;
-        if (vpl >= 8) launch_pdl(k_block_min_warp<Src, 8, VEC, REV>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0);
-        else if (vpl >= 4) launch_pdl(k_block_min_warp<Src, 4, VEC, REV>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0);
-        else if (vpl >= 2) launch_pdl(k_block_min_warp<Src, 2, VEC, REV>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0);
-        else launch_pdl(k_block_min_warp<Src, 1, VEC, REV>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0);
+        if (vpl >= 8) (M1 ? launch_pdl(k_block_min_warp<Src, 8, VEC, REV, Src::EPV == 4>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0, M1)
+                              : launch_pdl(k_block_min_warp<Src, 8, VEC, REV, false>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0, M1));
+        else if (vpl >= 4) (M1 ? launch_pdl(k_block_min_warp<Src, 4, VEC, REV, Src::EPV == 4>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0, M1)
+                              : launch_pdl(k_block_min_warp<Src, 4, VEC, REV, false>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0, M1));
+        else if (vpl >= 2) (M1 ? launch_pdl(k_block_min_warp<Src, 2, VEC, REV, Src::EPV == 4>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0, M1)
+                              : launch_pdl(k_block_min_warp<Src, 2, VEC, REV, false>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0, M1));
+        else (M1 ? launch_pdl(k_block_min_warp<Src, 1, VEC, REV, Src::EPV == 4>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0, M1)
+                              : launch_pdl(k_block_min_warp<Src, 1, VEC, REV, false>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0, M1));
     } else {
         const int64_t nvec = nb * vpb;
         const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(nvec, 128 * (kThreads / 32)), (int64_t)di.sms * 8));
@@ -126,11 +155,12 @@ cudaError_t block_min_dispatch(Src src, Len len, int64_t n_max, int logk, uint64
 
 }  // namespace
 
-cudaError_t launch_block_minima_i32(const int32_t *A, int64_t n, int logk, uint64_t *T0, cudaStream_t s) {
+cudaError_t launch_block_minima_i32(const int32_t *A, int64_t n, int logk, uint64_t *T0, cudaStream_t s,
+                                    uint64_t *M1) {
     SrcI32 src{A};
     Len len{n, nullptr};
-    if ((reinterpret_cast<uintptr_t>(A) & 15) == 0) return block_min_dispatch<SrcI32, true, false>(src, len, n, logk, T0, s);
-    return block_min_dispatch<SrcI32, false, false>(src, len, n, logk, T0, s);
+    if ((reinterpret_cast<uintptr_t>(A) & 15) == 0) return block_min_dispatch<SrcI32, true, false>(src, len, n, logk, T0, s, logk >= 7 ? M1 : nullptr);
+    return block_min_dispatch<SrcI32, false, false>(src, len, n, logk, T0, s, logk >= 7 ? M1 : nullptr);
 }
 
 cudaError_t launch_block_minima_u64(const uint64_t *AQ, Len len, int64_t n_max, int logk, uint64_t *T0,

@@ -863,9 +863,9 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     SrcU64 src{AQ};
     const int64_t qctas = query_ctas(q, di.sms);                                                        // step 4
     if (vecq)
-        launch_pdl(k_query_two<SrcU64, true, true, true>, (unsigned)qctas, kT, 0, s, src, lenq, logk_con, T, nullptr, l, r, BP, CP, CB, n, out, q, nullptr);
+        launch_pdl(k_query_two<SrcU64, true, true, true>, (unsigned)qctas, kT, 0, s, src, lenq, logk_con, T, nullptr, l, r, BP, CP, CB, nullptr, n, out, q, nullptr);
     else
-        launch_pdl(k_query_two<SrcU64, true, false, true>, (unsigned)qctas, kT, 0, s, src, lenq, logk_con, T, nullptr, l, r, BP, CP, CB, n, out, q, nullptr);
+        launch_pdl(k_query_two<SrcU64, true, false, true>, (unsigned)qctas, kT, 0, s, src, lenq, logk_con, T, nullptr, l, r, BP, CP, CB, nullptr, n, out, q, nullptr);
     note_launches(1);
     e = cudaGetLastError();
     st->mark(s);

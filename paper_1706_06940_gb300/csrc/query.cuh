@@ -140,14 +140,83 @@ __device__ __forceinline__ uint64_t warp_scan_min(const Src &src, int64_t n, int
     return warp_min(best);
 }
 
+// Minimum key of A[lo .. hi] (clipped to [0, n)) over the lanes' vectors
+// vlo + lane, vlo + lane + 32, ...: a part of at most 128 cells costs one
+// load per lane (two for the lane at an unaligned end).
+template <bool VEC>
+__device__ __forceinline__ uint64_t lane_part_min(const SrcI32 &src, int64_t n, int64_t lo, int64_t hi) {
+    const int lane = threadIdx.x & 31;
+    uint64_t m = KEY_MAX;
+    const int64_t nvfull = n / 4;
+    for (int64_t vi = lo / 4 + lane; vi <= hi / 4; vi += 32) {
+        uint64_t kk[4];
+        if (vi < nvfull) {
+            src.template vec<VEC>(vi, kk);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) kk[e] = vi * 4 + e < n ? src.one(vi * 4 + e) : KEY_MAX;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int64_t i = vi * 4 + e;
+            if (i >= lo && i <= hi) m = kmin(m, kk[e]);
+        }
+    }
+    return m;
+}
+
+// Minimum key over A[lo .. hi], a part of one block of k >= 128 cells, with
+// the 128-cell minima M1 of the two-level layout (Sec. 3.3, k1 = 128): the
+// small blocks strictly inside come from M1; an end small block's minimum is
+// taken when it lies in the range, else (and only when it could matter) its
+// part of at most 128 cells is scanned.  Two rounds of loads at most: M1,
+// then the end parts.  The whole warp calls it with the same arguments.
+template <bool VEC>
+__device__ __forceinline__ uint64_t warp_range_min_m1(const SrcI32 &src, const uint64_t *__restrict__ M1,
+                                                      int64_t n, int64_t lo, int64_t hi) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long *Mu = reinterpret_cast<const unsigned long long *>(M1);
+    const int64_t ml = lo >> 7, mh = hi >> 7;
+    uint64_t best = KEY_MAX;
+    bool scan_l = false, scan_r = false;
+    int64_t l_end = hi, r_beg = lo;
+    if (ml == mh) {
+        const uint64_t e0 = __ldg(Mu + ml);
+        const uint32_t p = key_pos(e0);
+        if (p >= lo && p <= hi) return e0;
+        scan_l = true;                              // the whole range, at most 128 cells
+    } else {
+        uint64_t inner = KEY_MAX;
+        for (int64_t j = ml + 1 + lane; j < mh; j += 32) inner = kmin(inner, __ldg(Mu + j));
+        const uint64_t el = __ldg(Mu + ml), er = __ldg(Mu + mh);
+        best = warp_min(inner);
+        if (el < best) {
+            if (key_pos(el) >= lo) best = el;
+            else scan_l = true;
+        }
+        if (er < best) {
+            if (key_pos(er) <= hi) best = er;
+            else scan_r = true;
+        }
+        l_end = ((ml + 1) << 7) - 1;
+        r_beg = mh << 7;
+    }
+    uint64_t sc = KEY_MAX;
+    if (scan_l) sc = lane_part_min<VEC>(src, n, lo, l_end);
+    if (scan_r) sc = kmin(sc, lane_part_min<VEC>(src, n, r_beg, hi));
+    return kmin(best, warp_min(sc));
+}
+
 // Run every queued scan of the warp.  Long scans, or a single one, run one at
 // a time on the whole warp (warp_scan_min).  When several are queued and all
 // are short enough for one round of a smaller team, the warp splits into 2 or
 // 4 teams of 16 or 8 lanes that run as many scans at once (consecutive-lane
 // 16-byte vectors, two per lane), so that their latencies overlap.
+// With M1 (the int32 source only), a scan of a part of a block goes through
+// warp_range_min_m1 instead.
 template <class Src, bool VEC>
 __device__ __forceinline__ void warp_drain_scans(const Src &src, int64_t n, bool has, const Pending &p,
-                                                 uint64_t &best) {
+                                                 uint64_t &best, const uint64_t *M1 = nullptr) {
     constexpr int EPV = Src::EPV;
     const int lane = threadIdx.x & 31;
     unsigned pend = __ballot_sync(0xffffffffu, has);
@@ -168,7 +237,12 @@ __device__ __forceinline__ void warp_drain_scans(const Src &src, int64_t n, bool
             const int64_t lo = __shfl_sync(0xffffffffu, p.lo, s);
             const int64_t hi = __shfl_sync(0xffffffffu, p.hi, s);
             const uint32_t lb = __shfl_sync(0xffffffffu, p.lb, s);
-            const uint64_t v = warp_scan_min<Src, VEC>(src, n, lo, hi, lb);
+            uint64_t v;
+            if constexpr (EPV == 4) {
+                v = M1 ? warp_range_min_m1<VEC>(src, M1, n, lo, hi) : warp_scan_min<Src, VEC>(src, n, lo, hi, lb);
+            } else {
+                v = warp_scan_min<Src, VEC>(src, n, lo, hi, lb);
+            }
             if (lane == s) best = kmin(best, v);
             continue;
         }
@@ -326,7 +400,7 @@ __device__ __forceinline__ void resolve_queued(const Src src, int64_t n, int log
                                             int64_t nb, const uint64_t *cs, const Coarse g,
                                             const int32_t *__restrict__ L, const int32_t *__restrict__ R,
                                             const uint2 *__restrict__ BP, int32_t *__restrict__ out,
-                                            const uint32_t *q_ids, int take) {
+                                            const uint32_t *q_ids, int take, const uint64_t *M1) {
     const int lane = threadIdx.x & 31;
     const int sh = logk + g.lc;
     const bool has = lane < take;
@@ -362,8 +436,8 @@ __device__ __forceinline__ void resolve_queued(const Src src, int64_t n, int log
             }
         }
     }
-    warp_drain_scans<Src, VEC>(src, n, hl, pl, best);
-    warp_drain_scans<Src, VEC>(src, n, hr, pr, best);
+    warp_drain_scans<Src, VEC>(src, n, hl, pl, best, M1);
+    warp_drain_scans<Src, VEC>(src, n, hr, pr, best, M1);
     if (has) out[qid] = (int32_t)key_pos(best);
     __syncwarp();
 }
@@ -380,7 +454,7 @@ __global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk
                                                     const uint64_t *__restrict__ Cs,
                                                     const int32_t *__restrict__ L, const int32_t *__restrict__ R,
                                                     const uint2 *__restrict__ BP, const uint32_t *__restrict__ CP,
-                                                    const uint16_t *__restrict__ CB,
+                                                    const uint16_t *__restrict__ CB, const uint64_t *__restrict__ M1,
                                                     int64_t n_a, int32_t *__restrict__ out, int64_t q,
                                                     unsigned *err) {
     pdl_wait();
@@ -411,7 +485,7 @@ __global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk
     int nq = 0;   // queued (warp-uniform)
     const int sh = logk + g.lc;
     auto resolve = [&](int take) {
-        resolve_queued<Src, CON, VEC>(src, n, logk, T, nb, cs, g, L, R, BP, out, my + nq - take, take);
+        resolve_queued<Src, CON, VEC>(src, n, logk, T, nb, cs, g, L, R, BP, out, my + nq - take, take, M1);
         nq -= take;
     };
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;

@@ -13,7 +13,8 @@ constexpr int kThreads = 256;
 
 // The kernel is the generic k_query_two of query.cuh over the int32 source.
 cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint64_t *T, const uint64_t *Cs,
-                               const int32_t *l, const int32_t *r, int64_t q, int32_t *out, cudaStream_t s) {
+                               const int32_t *l, const int32_t *r, int64_t q, int32_t *out, cudaStream_t s,
+                               const uint64_t *M1) {
     if (q <= 0) return cudaSuccess;
     const DevInfo di = dev_info();
     const bool vecq = ((reinterpret_cast<uintptr_t>(l) | reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
@@ -24,7 +25,7 @@ cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint
     const Len len{n, nullptr};
     const int64_t ctas = query_ctas(q, di.sms);
 #define RMQ_LQ2(VQ, V) \
-    launch_pdl(k_query_two<SrcI32, false, VQ, V>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T, Cs, l, r, nullptr, nullptr, nullptr, n, out, q, err)
+    launch_pdl(k_query_two<SrcI32, false, VQ, V>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T, Cs, l, r, nullptr, nullptr, nullptr, M1, n, out, q, err)
     if (vecq && vec) RMQ_LQ2(true, true);
     else if (vecq) RMQ_LQ2(true, false);
     else if (vec) RMQ_LQ2(false, true);

@@ -183,7 +183,9 @@ inline int ilog2_host(uint64_t x) { int t = -1; while (x) { x >>= 1; ++t; } retu
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // Launchers (plain.cu).  All enqueue on `s` and return the launch status.
-cudaError_t launch_block_minima_i32(const int32_t *A, int64_t n, int logk, uint64_t *T0, cudaStream_t s);
+// M1 (optional, k >= 128): minima of every 128 cells, ceil(n / 128) entries.
+cudaError_t launch_block_minima_i32(const int32_t *A, int64_t n, int logk, uint64_t *T0, cudaStream_t s,
+                                    uint64_t *M1 = nullptr);
 cudaError_t launch_block_minima_u64(const uint64_t *AQ, Len len, int64_t n_max, int logk, uint64_t *T0,
                                     cudaStream_t s);
 // The table's block count is nb = ceil(len / 2^logk), read on the device from
@@ -222,8 +224,10 @@ __host__ __device__ inline int bucket_shift(int64_t n) {
 __host__ __device__ inline int64_t bucket_count(int64_t n) { return ((n - 1) >> bucket_shift(n)) + 1; }
 // Plain-form query over a two-level table; Cs == nullptr: the coarse table is
 // built by every query CTA from level lc of T.
+// M1 (optional): the 128-cell minima of A, used for the partial-block parts.
 cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint64_t *T, const uint64_t *Cs,
-                               const int32_t *l, const int32_t *r, int64_t q, int32_t *out, cudaStream_t s);
+                               const int32_t *l, const int32_t *r, int64_t q, int32_t *out, cudaStream_t s,
+                               const uint64_t *M1 = nullptr);
 
 // Many arrays in one persistent launch (multi.cu).
 constexpr int kMultiMax = 1024;   // arrays per launch (their descriptors travel as a kernel parameter)
