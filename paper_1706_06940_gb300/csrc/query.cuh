@@ -113,9 +113,10 @@ __device__ __forceinline__ uint64_t warp_scan_min(const Src &src, int64_t n, int
     uint64_t best = KEY_MAX;
     const int64_t vlo = lo / EPV, vhi = hi / EPV;
     const int64_t nvfull = n / EPV;  // vectors that lie wholly inside [0, n)
-    for (int64_t v0 = vlo; v0 <= vhi; v0 += 64) {
+    constexpr int U = EPV == 2 ? 4 : 2;   // vectors per lane and round (8-byte keys: 256 per round)
+    for (int64_t v0 = vlo; v0 <= vhi; v0 += 32 * U) {
 #pragma unroll
-        for (int x = 0; x < 2; ++x) {
+        for (int x = 0; x < U; ++x) {
             const int64_t vi = v0 + x * 32 + lane;
             if (vi <= vhi) {
                 uint64_t kk[EPV];
