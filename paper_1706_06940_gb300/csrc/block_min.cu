@@ -40,6 +40,11 @@ __global__ void __launch_bounds__(kThreads) k_block_min_warp(Src src, Len len, i
     for (int64_t bi = warp; bi < nfull; bi += nwarps) {
         const int64_t b = REV ? nfull - 1 - bi : bi;
         const int64_t v0 = b * vpb + lane;
+        // the warp's next block is fetched into L2 while this one is reduced
+        if (VEC && lane == 0 && bi + nwarps < nfull) {
+            const int64_t bn = REV ? nfull - 1 - (bi + nwarps) : bi + nwarps;
+            prefetch_l2_bulk(src.a + bn * K, (uint32_t)(K * sizeof(*src.a)));
+        }
         uint64_t best = KEY_MAX;
         for (int u = 0; u < vpl; u += UNR) {
             uint64_t kk[UNR][EPV];

@@ -415,6 +415,15 @@ __global__ void __launch_bounds__(kT) k_bits_partial(const uint2 *__restrict__ B
     if (threadIdx.x == 0) partial[blockIdx.x] = total;
 }
 
+// Position of word i (0 <= i < 32 kIPT) in a warp's staging buffer, which
+// is written by rows of 32 words and read back as kIPT consecutive words per
+// lane: the 16-byte chunk index is XORed with its bits 3..5, so that neither
+// pattern has bank conflicts.
+__device__ __forceinline__ int stage_pos(int i) {
+    const int ch = i >> 2;
+    return ((ch ^ ((ch >> 3) & 7)) << 2) | (i & 3);
+}
+
 // Also sets to KEY_MAX every A_Q entry that the contraction combines with
 // atomics: the segment open just before each tile of kATile cells (the
 // segment whose left end P_j lies below the tile, when j <= m - 2).
@@ -424,22 +433,22 @@ __global__ void __launch_bounds__(kT) k_bits_partial(const uint2 *__restrict__ B
 // The tile's offset and the total m come from the tile counts of
 // k_bits_partial (every CTA adds up the counts of the tiles before it);
 // block 0 stores m.
-__global__ void __launch_bounds__(kT) k_bits_final(uint2 *__restrict__ BP, int64_t nbp,
-                                                   const uint32_t *__restrict__ partial, int64_t *m_dev,
-                                                   int64_t ntA, uint64_t *__restrict__ AQ, int64_t n, int logk_q,
-                                                   uint32_t *__restrict__ CP, uint16_t *__restrict__ CB) {
+__global__ void __launch_bounds__(kT, 6) k_bits_final(uint2 *__restrict__ BP, int64_t nbp,
+                                                      const uint32_t *__restrict__ partial, int64_t *m_dev,
+                                                      int64_t ntA, uint64_t *__restrict__ AQ, int64_t n, int logk_q,
+                                                      uint32_t *__restrict__ CP, uint16_t *__restrict__ CB) {
     pdl_wait();
-    __shared__ uint32_t wsum[kT / 32];
+    __shared__ uint32_t wsum[kT / 32], wbefore[kT / 32], wall[kT / 32];
+    __shared__ __align__(16) uint32_t stage[2][kT / 32][32 * kIPT];   // words, exclusive counts
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t *st = stage[0][w], *sx = stage[1][w];
+    // a warp's 32 kIPT words: loaded by rows of 32, counted kIPT per lane
     const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)w * (32 * kIPT);
-    uint32_t c[kIPT], words[kIPT];
-    uint32_t s = 0;
+    uint32_t words[kIPT];
 #pragma unroll
     for (int i = 0; i < kIPT; ++i) {
         const int64_t e = base + i * 32 + lane;
         words[i] = e < nbp ? BP[e].x : 0u;
-        c[i] = __popc(words[i]);
-        s += c[i];
     }
     uint32_t before = 0, all = 0;
     for (int64_t i = threadIdx.x; i < gridDim.x; i += kT) {
@@ -447,15 +456,51 @@ __global__ void __launch_bounds__(kT) k_bits_final(uint2 *__restrict__ BP, int64
         all += v;
         before += i < blockIdx.x ? v : 0u;
     }
-    uint32_t tile_off, m32;
-    block_excl_scan(before, wsum, tile_off);
-    block_excl_scan(all, wsum, m32);
-    s = __reduce_add_sync(0xffffffffu, s);
-    uint32_t total;
-    uint32_t run = block_excl_scan(lane == 0 ? s : 0u, wsum, total);
-    run = __shfl_sync(0xffffffffu, run, 0) + tile_off;
+#pragma unroll
+    for (int i = 0; i < kIPT; ++i) st[stage_pos(i * 32 + lane)] = words[i];
+    __syncwarp();
+    uint32_t cnt[kIPT];
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < kIPT; j += 4) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(st + stage_pos(kIPT * lane + j));
+        cnt[j] = __popc(v.x); cnt[j + 1] = __popc(v.y); cnt[j + 2] = __popc(v.z); cnt[j + 3] = __popc(v.w);
+        s += cnt[j] + cnt[j + 1] + cnt[j + 2] + cnt[j + 3];
+    }
+    // thread order is word order: one scan of the per-thread counts, plus
+    // the offset of this tile and the total m from the tile counts
+    uint32_t x = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    before = __reduce_add_sync(0xffffffffu, before);
+    all = __reduce_add_sync(0xffffffffu, all);
+    if (lane == 31) wsum[w] = x;
+    if (lane == 0) { wbefore[w] = before; wall[w] = all; }
+    __syncthreads();
+    uint32_t run = x - s, tile_off = 0, m32 = 0;
+#pragma unroll
+    for (int v = 0; v < kT / 32; ++v) {
+        run += v < w ? wsum[v] : 0u;
+        tile_off += wbefore[v];
+        m32 += wall[v];
+    }
+    run += tile_off;
     const int64_t m = m32;
     if (blockIdx.x == 0 && threadIdx.x == 0) *m_dev = m;
+    // exclusive counts of the lane's words, back in row order
+#pragma unroll
+    for (int j = 0; j < kIPT; j += 4) {
+        uint4 v;
+        v.x = run; run += cnt[j];
+        v.y = run; run += cnt[j + 1];
+        v.z = run; run += cnt[j + 2];
+        v.w = run; run += cnt[j + 3];
+        *reinterpret_cast<uint4 *>(sx + stage_pos(kIPT * lane + j)) = v;
+    }
+    __syncwarp();
     // coarse geometry of the table over A_Q (m - 1 entries)
     const int64_t nbq = m >= 2 ? (m - 2 + (1ll << logk_q)) >> logk_q : 0;
     const bool index = CP != nullptr && nbq > 0;
@@ -466,29 +511,22 @@ __global__ void __launch_bounds__(kT) k_bits_final(uint2 *__restrict__ BP, int64
     if (index && blockIdx.x == 0 && threadIdx.x == 0) CB[nbk] = (uint16_t)(g.nbc - 1);
 #pragma unroll
     for (int i = 0; i < kIPT; ++i) {
-        uint32_t x = c[i];
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-            if (lane >= d) x += y;
-        }
-        const uint32_t ex = run + x - c[i];
+        const uint32_t ex = sx[stage_pos(i * 32 + lane)], word = st[stage_pos(i * 32 + lane)];
         const int64_t e = base + i * 32 + lane;
         if (e < nbp) {
-            BP[e].y = ex;
+            BP[e] = make_uint2(word, ex);
             if ((e & (kATile / 32 - 1)) == 0 && (e / (kATile / 32)) < ntA) {
                 const int64_t sg = (int64_t)ex - 1;
                 if (sg >= 0 && sg <= m - 2) AQ[sg] = KEY_MAX;
             }
             if (index && e < nbp - 1) {
-                const uint32_t word = words[i];
                 // a coarse block of A_Q begins at the (j 2^sh)-th mark
                 const int64_t j = ((int64_t)ex + (1ll << sh) - 1) >> sh;
                 const int64_t t = (j << sh) - (int64_t)ex;
-                if (j < g.nbc && t < (int64_t)c[i]) {
-                    uint32_t w = word;
-                    for (int64_t d = 0; d < t; ++d) w &= w - 1u;   // drop the t lower marks
-                    CP[j] = (uint32_t)(e * 32 + __ffs(w) - 1);
+                if (j < g.nbc && t < (int64_t)__popc(word)) {
+                    uint32_t wd = word;
+                    for (int64_t d = 0; d < t; ++d) wd &= wd - 1u;   // drop the t lower marks
+                    CP[j] = (uint32_t)(e * 32 + __ffs(wd) - 1);
                 }
                 // bucket start: the last coarse block that begins at or before it
                 if (((e << 5) & ((1ll << bs) - 1)) == 0) {
@@ -498,7 +536,6 @@ __global__ void __launch_bounds__(kT) k_bits_final(uint2 *__restrict__ BP, int64
                 }
             }
         }
-        run += __shfl_sync(0xffffffffu, x, 31);
     }
 }
 

@@ -104,6 +104,13 @@ __device__ __forceinline__ ulonglong2 ld_stream_v2u64(const ulonglong2 *p) {
     return v;
 }
 
+// Asks L2 to fetch [p, p + bytes) ahead of its use; p and bytes must be
+// multiples of 16 and the range must lie inside one allocation.  Nothing is
+// waited for and nothing lands in shared memory.
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // ---------------------------------------------------------------- sources
 // A "source" yields packed keys of a sequence: the int32 input A (key built
 // from value and index) or an array of ready keys (the contracted A_Q).
