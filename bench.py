@@ -364,10 +364,13 @@ def run_ours(args, dist):
     # the block table keeps levels 0 .. lc (the coarse level above lives in
     # shared memory); with k >= 128 the block-minima pass also writes the
     # minima of every 128 cells (Sec. 3.3's small blocks)
+    # (the coarse summary: at most 4096 entries, level t holding its
+    # nbc - 2^t + 1 defined entries)
     lc = 0
     while True:
         nbc = -(-nb // (1 << lc))
-        if nbc * (int(np.floor(np.log2(nbc))) + 1) <= 4096:
+        lvc = nbc.bit_length()
+        if lvc * (nbc + 1) - ((1 << lvc) - 1) <= 4096:
             break
         lc += 1
     m1 = -(-n // 128) if k >= 128 else 0

@@ -504,7 +504,8 @@ __global__ void __launch_bounds__(kT, 6) k_bits_final(uint2 *__restrict__ BP, in
     // coarse geometry of the table over A_Q (m - 1 entries)
     const int64_t nbq = m >= 2 ? (m - 2 + (1ll << logk_q)) >> logk_q : 0;
     const bool index = CP != nullptr && nbq > 0;
-    const Coarse g = coarse_geom(nbq > 0 ? nbq : 1);
+    // the coarse index serves the batch query, whose geometry is kCoarseCapCon's
+    const Coarse g = coarse_geom(nbq > 0 ? nbq : 1, kCoarseCapCon);
     const int sh = logk_q + g.lc;
     const int bs = bucket_shift(n);
     const int64_t nbk = bucket_count(n);
@@ -857,7 +858,7 @@ cudaError_t contract(const int32_t *A, int64_t n, const uint32_t *P, const int64
 size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con) {
     const int64_t mq_max = std::max<int64_t>(std::min<int64_t>(2 * q, n) - 1, 1);
     const int64_t nbq = cdiv(mq_max, 1ll << logk_con);
-    const int64_t lv = coarse_geom(nbq).lc + 1;
+    const int64_t lv = coarse_geom(nbq, kCoarseCapCon).lc + 1;
     size_t b = 0;
     b += align256(bitmap_entries(n) * sizeof(uint2));  // endpoint bitmap with rank counts
     b += align256(8);                                 // m
@@ -872,7 +873,7 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
                            int32_t *out, int logk_con, void *ws, cudaStream_t s, Stages *st) {
     const int64_t mq_max = std::max<int64_t>(std::min<int64_t>(2 * q, n) - 1, 1);
     const int64_t nbq = cdiv(mq_max, 1ll << logk_con);
-    const int64_t lv = coarse_geom(nbq).lc + 1;
+    const int64_t lv = coarse_geom(nbq, kCoarseCapCon).lc + 1;
     Carver c{static_cast<char *>(ws)};
     uint2 *BP = c.take<uint2>(bitmap_entries(n));
     int64_t *m_dev = c.take<int64_t>(1);
@@ -893,16 +894,24 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     st->mark(s);
     const Len lenq{0, m_dev};
     if ((e = launch_block_minima_u64(AQ, lenq, mq_max, logk_con, T, s)) != cudaSuccess) return e;         // step 3
-    if ((e = launch_sparse_table(T, lenq, logk_con, nbq, s, true)) != cudaSuccess) return e;              // step 3
+    if ((e = launch_sparse_table(T, lenq, logk_con, nbq, s, true, nullptr, kCoarseCapCon)) != cudaSuccess)
+        return e;                                                                                         // step 3
     st->mark(s);
     const bool vecq = ((reinterpret_cast<uintptr_t>(l) | reinterpret_cast<uintptr_t>(r) |
                         reinterpret_cast<uintptr_t>(out)) & 15) == 0;
     SrcU64 src{AQ};
     const int64_t qctas = query_ctas(q, di.sms);                                                        // step 4
+    // m is known on the device only: room for the largest coarse table
+    const size_t smem = (size_t)kCoarseCapCon * sizeof(uint64_t);
     if (vecq)
-        launch_pdl(k_query_two<SrcU64, true, true, true>, (unsigned)qctas, kT, 0, s, src, lenq, logk_con, T, nullptr, l, r, BP, CP, CB, nullptr, n, out, q, nullptr);
+        e = launch_query_two<SrcU64, true, true, true>(di.device, (unsigned)qctas, smem, s, src, lenq, logk_con,
+                                                       kCoarseCapCon, T, nullptr, l, r, BP, CP, CB, nullptr, n,
+                                                       out, q, nullptr);
     else
-        launch_pdl(k_query_two<SrcU64, true, false, true>, (unsigned)qctas, kT, 0, s, src, lenq, logk_con, T, nullptr, l, r, BP, CP, CB, nullptr, n, out, q, nullptr);
+        e = launch_query_two<SrcU64, true, false, true>(di.device, (unsigned)qctas, smem, s, src, lenq, logk_con,
+                                                        kCoarseCapCon, T, nullptr, l, r, BP, CP, CB, nullptr, n,
+                                                        out, q, nullptr);
+    if (e != cudaSuccess) return e;
     note_launches(1);
     e = cudaGetLastError();
     st->mark(s);

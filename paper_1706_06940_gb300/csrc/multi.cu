@@ -292,11 +292,12 @@ __global__ void __launch_bounds__(kMT, 3) k_multi(const __grid_constant__ MultiP
                 __syncthreads();
                 for (int t = 1; t < g.lvc; ++t) {
                     const int64_t half = 1ll << (t - 1), cnt = g.nbc - (1ll << t) + 1;
-                    for (int64_t J = threadIdx.x; J < cnt; J += kMT)
-                        cs[t * g.nbc + J] = kmin(cs[(t - 1) * g.nbc + J], cs[(t - 1) * g.nbc + J + half]);
+                    uint64_t *cur = cs + g.row(t);
+                    const uint64_t *prev = cs + g.row(t - 1);
+                    for (int64_t J = threadIdx.x; J < cnt; J += kMT) cur[J] = kmin(prev[J], prev[J + half]);
                     __syncthreads();
                 }
-                for (int64_t i = g.nbc + threadIdx.x; i < g.nbc * g.lvc; i += kMT) C[i] = cs[i];
+                for (int64_t i = g.nbc + threadIdx.x; i < g.size(); i += kMT) C[i] = cs[i];
                 __threadfence();
                 __syncthreads();
                 const bool withhold = (p.flags & RMQ_FLAG_TEST_WITHHOLD_READY) && h == 0;
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(kMT, 3) k_multi(const __grid_constant__ MultiP
             }
             __threadfence();
             const uint64_t *C = p.Cs + (int64_t)h * kCoarseCap;
-            for (int64_t i = threadIdx.x; i < g.nbc * g.lvc; i += kMT) cs[i] = __ldcg(reinterpret_cast<const unsigned long long *>(C) + i);
+            for (int64_t i = threadIdx.x; i < g.size(); i += kMT) cs[i] = __ldcg(reinterpret_cast<const unsigned long long *>(C) + i);
             __syncthreads();
             const uint64_t *T0 = p.T0 + t0off[h];
             const int sh = d.logk + g.lc;
@@ -510,7 +511,7 @@ __global__ void __launch_bounds__(kMT, 3) k_query_handles(const __grid_constant_
         const int64_t qn = min((int64_t)kQueriesPerItem, (int64_t)d.q - c0);
         const int64_t qbase = qoff[h] + c0;
         if (threadIdx.x == 0) n_open = 0;
-        load_coarse(cs, d.Cs, (int)(g.nbc * g.lvc));
+        load_coarse(cs, d.Cs, (int)g.size());
         __syncthreads();
         bool bad = false;
 #pragma unroll

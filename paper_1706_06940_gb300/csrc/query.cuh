@@ -87,7 +87,7 @@ __device__ __forceinline__ uint64_t resolve_coarse(const uint64_t *cs, const Coa
     uint64_t best = KEY_MAX;
     if (BR - BL >= 2) {
         const int t = 31 - __clz((int)(BR - BL - 1));
-        const uint64_t *row = cs + (uint32_t)t * (uint32_t)g.nbc;
+        const uint64_t *row = cs + g.row32(t);
         best = kmin(row[BL + 1], row[BR - (1u << t)]);
     }
     const uint64_t cl = cs[BL], cr = cs[BR];
@@ -322,27 +322,29 @@ __device__ __forceinline__ void build_coarse(uint64_t *cs, const uint64_t *__res
     __syncthreads();
     for (int t = 1; t < g.lvc; ++t) {
         const int half = 1 << (t - 1), cnt = (int)g.nbc - (1 << t) + 1;
-        uint64_t *cur = cs + t * (int)g.nbc;
-        const uint64_t *prev = cur - g.nbc;
+        uint64_t *cur = cs + g.row(t);
+        const uint64_t *prev = cs + g.row(t - 1);
         for (int J = threadIdx.x; J < cnt; J += blockDim.x) cur[J] = kmin(prev[J], prev[J + half]);
         __syncthreads();
     }
 }
 
-// Copy the coarse table into shared memory: every thread issues all its loads
-// before any store, so the copy costs one round trip to L2.
+// Copy the coarse table into shared memory: each thread has 8 loads in
+// flight before it stores them.
 __device__ __forceinline__ void load_coarse(uint64_t *cs, const uint64_t *__restrict__ Cs, int total) {
-    constexpr int PER = kCoarseCap / 256;
-    uint64_t tmp[PER];
+    constexpr int PER = 8;
+    for (int b = 0; b < total; b += PER * (int)blockDim.x) {
+        uint64_t tmp[PER];
 #pragma unroll
-    for (int x = 0; x < PER; ++x) {
-        const int i = threadIdx.x + x * 256;
-        tmp[x] = i < total ? __ldg(reinterpret_cast<const unsigned long long *>(Cs) + i) : 0ull;
-    }
+        for (int x = 0; x < PER; ++x) {
+            const int i = b + threadIdx.x + x * (int)blockDim.x;
+            tmp[x] = i < total ? __ldg(reinterpret_cast<const unsigned long long *>(Cs) + i) : 0ull;
+        }
 #pragma unroll
-    for (int x = 0; x < PER; ++x) {
-        const int i = threadIdx.x + x * 256;
-        if (i < total) cs[i] = tmp[x];
+        for (int x = 0; x < PER; ++x) {
+            const int i = b + threadIdx.x + x * (int)blockDim.x;
+            if (i < total) cs[i] = tmp[x];
+        }
     }
 }
 
@@ -356,7 +358,7 @@ __device__ __forceinline__ void load_coarse(uint64_t *cs, const uint64_t *__rest
 __device__ __forceinline__ bool coarse_blocks_min(const uint64_t *cs, const Coarse &g, uint32_t BL, uint32_t BR,
                                                   uint32_t la, uint32_t ra, uint64_t &m) {
     const int t = 31 - __clz((int)(BR - BL + 1));
-    const uint64_t *row = cs + (uint32_t)t * (uint32_t)g.nbc;
+    const uint64_t *row = cs + g.row32(t);
     m = kmin(row[BL], row[BR + 1 - (1u << t)]);
     const uint32_t p = key_pos(m);
     return p >= la && p <= ra;
@@ -450,8 +452,12 @@ __device__ __forceinline__ void resolve_queued(const Src src, int64_t n, int log
 //     Phase A needs only the coarse blocks of a_i and b_i - 1, which the
 //     coarse index (CP, CB) gives from l_i and r_i - 1; the ranks themselves
 //     are looked up in BP for the queries left to phase B.
+//   cap: the coarse geometry of the table (coarse_geom(nb, cap)); the
+//     dynamic shared memory holds its coarse table (coarse_geom(...).size()
+//     entries at most).
 template <class Src, bool CON, bool VECQ, bool VEC>
-__global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk, const uint64_t *__restrict__ T,
+__global__ void __launch_bounds__(kQueryThreads, kQueryCtasPerSm)
+k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
                                                     const uint64_t *__restrict__ Cs,
                                                     const int32_t *__restrict__ L, const int32_t *__restrict__ R,
                                                     const uint2 *__restrict__ BP, const uint32_t *__restrict__ CP,
@@ -464,15 +470,16 @@ __global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk
     // as 32 are queued it resolves them (phase B: fine table and edge scans),
     // so the latency of that work overlaps the streaming of other warps.
     constexpr int kQueue = 160;   // a step adds at most 128
-    __shared__ uint64_t cs[kCoarseCap];
+    extern __shared__ __align__(16) uint64_t query_coarse_smem[];
+    uint64_t *cs = query_coarse_smem;
     __shared__ uint32_t cp[CON ? kCoarseBlocksMax : 1];
     __shared__ uint16_t cb[CON ? kBucketsMax : 1];
-    __shared__ uint32_t queue[8][kQueue];
+    __shared__ uint32_t queue[kQueryThreads / 32][kQueue];
     const int64_t n = len.get();
     const int64_t nb = (n + (1ll << logk) - 1) >> logk;
-    const Coarse g = coarse_geom(nb);
+    const Coarse g = coarse_geom(nb, cap);
     // the coarse table: copied when the caller keeps one, else built here
-    if (Cs) load_coarse(cs, Cs, (int)(g.nbc * g.lvc));
+    if (Cs) load_coarse(cs, Cs, (int)g.size());
     else if (nb > 0) build_coarse(cs, T, nb, g);
     const int bs = CON ? bucket_shift(n_a) : 0;
     if (CON && nb > 0) {
@@ -568,6 +575,22 @@ __global__ void __launch_bounds__(256, 4) k_query_two(Src src, Len len, int logk
         if (!CON && bad && err) atomicOr(err, ERR_QUERY_RANGE);
     }
     if (nq > 0) resolve(nq);
+}
+
+// Launches k_query_two with `smem` bytes of coarse table (at most
+// kCoarseCapMax entries); the first launch of each instantiation on a device
+// raises the kernel's dynamic shared memory limit to that maximum.
+template <class Src, bool CON, bool VECQ, bool VEC, class... Args>
+inline cudaError_t launch_query_two(int device, unsigned ctas, size_t smem, cudaStream_t s, Args... args) {
+    static bool raised[64] = {false};
+    auto kern = k_query_two<Src, CON, VECQ, VEC>;
+    if (device < 0 || device >= 64 || !raised[device]) {
+        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)(kCoarseCapMax * sizeof(uint64_t)));
+        if (e != cudaSuccess) return e;
+        if (device >= 0 && device < 64) raised[device] = true;
+    }
+    return launch_pdl(kern, ctas, kQueryThreads, smem, s, args...);
 }
 
 }  // namespace rmq

@@ -7,15 +7,12 @@
 
 namespace rmq {
 
-namespace {
-constexpr int kThreads = 256;
-}  // namespace
-
 // The kernel is the generic k_query_two of query.cuh over the int32 source.
 cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint64_t *T, const uint64_t *Cs,
                                const int32_t *l, const int32_t *r, int64_t q, int32_t *out, cudaStream_t s,
-                               const uint64_t *M1) {
+                               const uint64_t *M1, int cap) {
     if (q <= 0) return cudaSuccess;
+    if (cap < 1 || cap > kCoarseCapMax || (Cs && cap != kCoarseCap)) return cudaErrorInvalidValue;
     const DevInfo di = dev_info();
     const bool vecq = ((reinterpret_cast<uintptr_t>(l) | reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
     const bool vec = (reinterpret_cast<uintptr_t>(A) & 15) == 0;
@@ -24,13 +21,18 @@ cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint
     SrcI32 src{A};
     const Len len{n, nullptr};
     const int64_t ctas = query_ctas(q, di.sms);
-#define RMQ_LQ2(VQ, V) \
-    launch_pdl(k_query_two<SrcI32, false, VQ, V>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T, Cs, l, r, nullptr, nullptr, nullptr, M1, n, out, q, err)
+    const int64_t nb = n > 0 ? ((n - 1) >> logk) + 1 : 0;
+    const size_t smem = (size_t)coarse_geom(nb, cap).size() * sizeof(uint64_t);
+    cudaError_t e;
+#define RMQ_LQ2(VQ, V)                                                                                             \
+    e = launch_query_two<SrcI32, false, VQ, V>(di.device, (unsigned)ctas, smem, s, src, len, logk, cap, T, Cs, l, r, \
+                                               nullptr, nullptr, nullptr, M1, n, out, q, err)
     if (vecq && vec) RMQ_LQ2(true, true);
     else if (vecq) RMQ_LQ2(true, false);
     else if (vec) RMQ_LQ2(false, true);
     else RMQ_LQ2(false, false);
 #undef RMQ_LQ2
+    if (e != cudaSuccess) return e;
     note_launches(1);
     return cudaGetLastError();
 }

@@ -45,23 +45,38 @@ __host__ __device__ __forceinline__ int ilog2_hd(uint64_t x) {
 // applied to the memory hierarchy): coarse blocks are 2^lc consecutive
 // blocks, and the summary holds levels lc .. lc + lvc - 1 of the table at the
 // coarse block starts, i.e. a sparse table over nbc coarse blocks, small
-// enough (<= kCoarseCap entries) to live in shared memory while queries run.
-// lc is the smallest shift for which it fits.
+// enough (<= cap entries) to live in shared memory while queries run.  Level
+// t keeps only its nbc - 2^t + 1 defined entries, stored one level after the
+// other.  lc is the smallest shift for which the summary fits.
+//   kCoarseCap: every plain-form table (the summary of a table that outlives
+//     a call is kept in memory; a batch call's query CTAs build it in shared
+//     memory);
+//   kCoarseCapCon: the table over A_Q of a contracted batch call.  A query
+//     the summary leaves open costs more there (two rank lookups, 8-byte
+//     scans), so its summary is finer.
 constexpr int kCoarseCap = 4096;
+constexpr int kCoarseCapCon = 6656;
+constexpr int kCoarseCapMax = kCoarseCapCon;
 struct Coarse {
     int lc;            // log2 of blocks per coarse block
     int lvc;           // levels of the coarse table
     int64_t nbc;       // coarse blocks (the last may be partial)
     int64_t nbc_full;  // coarse blocks made of 2^lc whole blocks
+    // first entry of level t; row(lvc) is the size of the summary
+    __host__ __device__ __forceinline__ int64_t row(int t) const { return (int64_t)t * (nbc + 1) - ((1ll << t) - 1); }
+    __host__ __device__ __forceinline__ int64_t size() const { return nbc > 0 ? row(lvc) : 0; }
+    __device__ __forceinline__ uint32_t row32(int t) const {
+        return (uint32_t)t * ((uint32_t)nbc + 1u) - ((1u << t) - 1u);
+    }
 };
-__host__ __device__ __forceinline__ Coarse coarse_geom(int64_t nb) {
+__host__ __device__ __forceinline__ Coarse coarse_geom(int64_t nb, int cap = kCoarseCap) {
     Coarse g{0, 1, nb, nb};
     if (nb < 1) { g.nbc = g.nbc_full = 0; return g; }
     for (int lc = 0;; ++lc) {
-        const int64_t nbc = (nb + (1ll << lc) - 1) >> lc;
-        const int lvc = ilog2_hd((uint64_t)nbc) + 1;
-        if (nbc * lvc <= kCoarseCap) {
-            g.lc = lc; g.lvc = lvc; g.nbc = nbc; g.nbc_full = nb >> lc;
+        g.nbc = (nb + (1ll << lc) - 1) >> lc;
+        g.lvc = ilog2_hd((uint64_t)g.nbc) + 1;
+        if (g.size() <= cap) {
+            g.lc = lc; g.nbc_full = nb >> lc;
             return g;
         }
     }
@@ -199,18 +214,22 @@ cudaError_t launch_block_minima_u64(const uint64_t *AQ, Len len, int64_t n_max, 
 // `len`; nb_max bounds it on the host and sizes the launches.
 // two_level == false: every level 1 .. floor(log2 nb) of the block table.
 // two_level == true: the two-level layout -- levels 1 .. lc of the block
-//   table; with Cs, also the coarse table (kCoarseCap entries) in Cs (else
-//   each query CTA builds it in shared memory from level lc).
+//   table for the coarse geometry of cap; with Cs (cap == kCoarseCap only),
+//   also the coarse table in Cs (else each query CTA builds it in shared
+//   memory from level lc).
 cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, cudaStream_t s,
-                                bool two_level = false, uint64_t *Cs = nullptr);
+                                bool two_level = false, uint64_t *Cs = nullptr, int cap = kCoarseCap);
 // Entries of the two-level block table (levels 0 .. lc) for nb blocks.
-inline int64_t two_level_entries(int64_t nb) { return nb < 1 ? 0 : nb * (coarse_geom(nb).lc + 1); }
-// Query kernel: kQueryCtasPerSm CTAs per SM (<= 43 KB shared memory, <= 64
-// registers), one wave, 8 warps of 128 queries per step.
-constexpr int kQueryCtasPerSm = 4;
+inline int64_t two_level_entries(int64_t nb, int cap = kCoarseCap) {
+    return nb < 1 ? 0 : nb * (coarse_geom(nb, cap).lc + 1);
+}
+// Query kernel: kQueryCtasPerSm CTAs of kQueryThreads per SM (<= 80 KB
+// shared memory, <= 64 registers), one wave, 16 warps of 128 queries per step.
+constexpr int kQueryThreads = 512;
+constexpr int kQueryCtasPerSm = 2;
 inline int64_t query_ctas(int64_t q, int sms) {
     const int64_t steps = (q + 127) / 128;
-    int64_t ctas = (steps + 7) / 8;
+    int64_t ctas = (steps + kQueryThreads / 32 - 1) / (kQueryThreads / 32);
     const int64_t cap = (int64_t)sms * kQueryCtasPerSm;
     if (ctas > cap) ctas = cap;
     return ctas < 1 ? 1 : ctas;
@@ -220,8 +239,19 @@ inline int64_t query_ctas(int64_t q, int sms) {
 // 2^s positions, CB[i] = the last coarse block that begins at or before
 // position i 2^s (0 if none); CB[nbk] = nbc - 1.  A query's coarse blocks
 // follow from l and r through these two small arrays, without its ranks.
-// nbc * lvc <= kCoarseCap implies nbc <= 455.
-constexpr int kCoarseBlocksMax = 512;
+// A summary of at most kCoarseCapCon entries has nbc <= 766.
+constexpr int kCoarseBlocksMax = 768;
+constexpr int64_t coarse_size_of(int64_t nbc) {
+    int lvc = 0;
+    while ((nbc >> lvc) > 0) ++lvc;
+    return lvc * (nbc + 1) - ((1ll << lvc) - 1);
+}
+constexpr int64_t coarse_blocks_fitting(int64_t cap) {
+    int64_t nbc = 1;
+    while (coarse_size_of(nbc + 1) <= cap) ++nbc;
+    return nbc;
+}
+static_assert(coarse_blocks_fitting(kCoarseCapCon) <= kCoarseBlocksMax, "coarse index too small");
 constexpr int kBucketsMax = 2048;
 __host__ __device__ inline int bucket_shift(int64_t n) {
     int s = 5;
@@ -232,9 +262,10 @@ __host__ __device__ inline int64_t bucket_count(int64_t n) { return ((n - 1) >> 
 // Plain-form query over a two-level table; Cs == nullptr: the coarse table is
 // built by every query CTA from level lc of T.
 // M1 (optional): the 128-cell minima of A, used for the partial-block parts.
+// cap: the coarse geometry the table was built for (kCoarseCap when Cs is given).
 cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint64_t *T, const uint64_t *Cs,
                                const int32_t *l, const int32_t *r, int64_t q, int32_t *out, cudaStream_t s,
-                               const uint64_t *M1 = nullptr);
+                               const uint64_t *M1 = nullptr, int cap = kCoarseCap);
 
 // Many arrays in one persistent launch (multi.cu).
 constexpr int kMultiMax = 1024;   // arrays per launch (their descriptors travel as a kernel parameter)

@@ -20,14 +20,16 @@ constexpr int kThreads = 256;
 // needs once (coalesced along rho for R = 32, along s for R = 1), doubles in
 // ping-pong buffers and writes every level's rows < S.  Round 0 uses R = 1
 // (contiguous tiles); later rounds start at b >= 5, so R = 32 divides 2^b.
+// cap > 0: levels up to lc of the two-level layout for that coarse geometry;
+// cap == 0: every level.
 template <int R, int LV>
 __global__ void __launch_bounds__(kThreads) k_st_round(uint64_t *__restrict__ T, Len len, int logk, int b, int S,
-                                                      bool two_level) {
+                                                      int cap) {
     pdl_wait();
     const int64_t n = len.get();
     const int64_t nb = (n + (1ll << logk) - 1) >> logk;
     if (nb < 2) return;
-    const int top = two_level ? coarse_geom(nb).lc : ilog2_dev((uint64_t)nb);
+    const int top = cap > 0 ? coarse_geom(nb, cap).lc : ilog2_dev((uint64_t)nb);
     if (b >= top) return;
     const int nlev = min(LV, top - b);
     const int rows = S + (1 << nlev);
@@ -91,12 +93,12 @@ __global__ void __launch_bounds__(1024) k_coarse_table(const uint64_t *__restric
     __syncthreads();
     for (int t = 1; t < g.lvc; ++t) {
         const int64_t half = 1ll << (t - 1), cnt = g.nbc - (1ll << t) + 1;
-        uint64_t *cur = c + (int64_t)t * g.nbc;
-        const uint64_t *prev = c + (int64_t)(t - 1) * g.nbc;
+        uint64_t *cur = c + g.row(t);
+        const uint64_t *prev = c + g.row(t - 1);
         for (int64_t J = threadIdx.x; J < cnt; J += blockDim.x) cur[J] = kmin(prev[J], prev[J + half]);
         __syncthreads();
     }
-    for (int64_t i = threadIdx.x; i < g.nbc * g.lvc; i += blockDim.x) Cs[i] = c[i];
+    for (int64_t i = threadIdx.x; i < g.size(); i += blockDim.x) Cs[i] = c[i];
 }
 
 constexpr int kLV0 = 12, kS0 = 256;   // round 0: levels 1..12, 256 outputs per CTA
@@ -105,9 +107,11 @@ constexpr int kLV1 = 6, kS1 = 64;     // later rounds: 6 levels, 32 residues x 6
 }  // namespace
 
 cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, cudaStream_t s, bool two,
-                                uint64_t *Cs) {
+                                uint64_t *Cs, int cap) {
     if (nb_max < 1) return cudaSuccess;
-    const int top = two ? coarse_geom(nb_max).lc : (nb_max >= 2 ? ilog2_host((uint64_t)nb_max) : 0);
+    if (cap < 1 || cap > kCoarseCapMax || (Cs && cap != kCoarseCap)) return cudaErrorInvalidValue;
+    const int top = two ? coarse_geom(nb_max, cap).lc : (nb_max >= 2 ? ilog2_host((uint64_t)nb_max) : 0);
+    const int kcap = two ? cap : 0;
     static bool attr_done[64] = {false};
     const DevInfo di = dev_info();
     const size_t smem0 = 2ull * (kS0 + (1 << kLV0)) * 1 * sizeof(uint64_t);
@@ -120,7 +124,7 @@ cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, 
     {
         const int64_t ctas = cdiv(nb_max, kS0);
         if (top > 0) {
-            launch_pdl(k_st_round<1, kLV0>, (unsigned)ctas, kThreads, smem0, s, T, len, logk, 0, kS0, two);
+            launch_pdl(k_st_round<1, kLV0>, (unsigned)ctas, kThreads, smem0, s, T, len, logk, 0, kS0, kcap);
             note_launches(1);
         }
         cudaError_t e = cudaGetLastError();
@@ -131,7 +135,7 @@ cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, 
         const int64_t ngroups = stride / 32;
         const int64_t nstr = cdiv(nb_max, stride);
         const int64_t ctas = ngroups * cdiv(nstr, kS1);
-        launch_pdl(k_st_round<32, kLV1>, (unsigned)ctas, kThreads, smem1, s, T, len, logk, b, kS1, two);
+        launch_pdl(k_st_round<32, kLV1>, (unsigned)ctas, kThreads, smem1, s, T, len, logk, b, kS1, kcap);
         note_launches(1);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -168,6 +168,21 @@ def test_small_n_and_few_blocks(R, n):
     check(R, A, l, r, ks=(32,), kcons=(32,))
 
 
+# Block counts (k = 32) around the largest coarse summaries that keep one
+# block per coarse block (510 coarse blocks for the plain form's 4096-entry
+# summary, 766 for the contracted form's 6656-entry one), around the level
+# boundaries 512, 1024 and 2048, and around the next doubling (1020/1021,
+# 1532/1533); the contracted form sees comparable counts over A_Q.
+@pytest.mark.parametrize("nb", [510, 511, 512, 766, 767, 1021, 1024, 1025, 1532, 1533, 2047])
+def test_coarse_summary_capacity_boundaries(R, nb):
+    n = nb * 32 - 5
+    A = W.uniform_array(n, nb + 60, 0, 1000)
+    l, r = W.uniform_queries(n, 20_000, nb + 61)
+    ls, rs = W.log_width_queries(n, 3000, nb + 62, 1, 3000)
+    l, r = np.concatenate([l, ls, [0, n - 1, 0]]), np.concatenate([r, rs, [n - 1, n - 1, 0]])
+    check(R, A, l.astype(np.int32), r.astype(np.int32), ks=(32, 64), kcons=(32,))
+
+
 def oracle_all_ranges(n):
     i, j = np.triu_indices(n)
     return i.astype(np.int32), j.astype(np.int32)
