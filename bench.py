@@ -54,6 +54,8 @@ def parse_args():
     p.add_argument("--n", "--array-size", dest="n", type=float, default=1e8)
     p.add_argument("--q", "--num-queries", dest="q", type=float, default=1e7)
     p.add_argument("--seed", type=int, default=1002)
+    p.add_argument("--array", choices=["uniform", "permutation"], default="uniform",
+                   help="single: A uniform int32 (default) or the paper's permutation with n/2 swaps")
     p.add_argument("--variant", choices=["both", "plain", "contracted"], default="both")
     p.add_argument("--k", type=int, default=0, help="plain-form block size (0 = tuned)")
     p.add_argument("--k-con", type=int, default=0, help="contracted-form block size (0 = tuned)")
@@ -99,16 +101,22 @@ class Dist:
             self.pg.destroy_process_group()
 
 
-def workload(n, q, seed, rank):
+def workload(n, q, seed, rank, array="uniform"):
     from paper_1706_06940_gb300 import workloads as W
-    A = W.uniform_array(n, seed + 7919 * rank)
+    if array == "permutation":
+        A = W.paper_permutation(n, seed + 7919 * rank)
+    else:
+        A = W.uniform_array(n, seed + 7919 * rank)
     l, r = W.uniform_queries(n, q, seed + 7919 * rank + 1)
     return A, l, r
 
 
-def workload_name(n, q):
-    return ("paper-shaped single array: A int32 n=%g uniform in [0,2^31), q=%g queries with l,r uniform "
-            "over [0,n) swapped so l<=r; one step = the batch answered by plain BbST and by BbST_CON" % (n, q))
+def workload_name(n, q, array="uniform"):
+    what = ("the paper's array (1..n after n/2 random pair swaps)" if array == "permutation"
+            else "uniform in [0,2^31)")
+    return ("paper-shaped single array: A int32 n=%g %s, q=%g queries with l,r uniform "
+            "over [0,n) swapped so l<=r; one step = the batch answered by plain BbST and by BbST_CON"
+            % (n, what, q))
 
 
 class ClockSampler:
@@ -177,9 +185,10 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def profiled_traffic(kernel_src_rel, summary_rel):
+def profiled_traffic(kernel_src_rel, summary_rel, n, k):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current source of the kernel (its sha256 is recorded there)."""
+    the current source of the kernel (its sha256 is recorded there) and on
+    this workload's n and k (recorded as workload_n, workload_k)."""
     try:
         text = open(os.path.join(ROOT, summary_rel)).read()
         src = open(os.path.join(ROOT, kernel_src_rel), "rb").read()
@@ -187,7 +196,11 @@ def profiled_traffic(kernel_src_rel, summary_rel):
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", text)
     h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    wn = re.search(r"workload_n:\s*([0-9]+)", text)
+    wk = re.search(r"workload_k:\s*([0-9]+)", text)
     if not m or not h or h.group(1) != hashlib.sha256(src).hexdigest():
+        return None
+    if not wn or not wk or int(wn.group(1)) != n or int(wk.group(1)) != k:
         return None
     return int(m.group(1))
 
@@ -224,7 +237,7 @@ def run_reference(args, dist):
     import oracle
     oracle.build()
     n, q = int(args.n), int(args.q)
-    A, l, r = workload(n, q, args.seed, 0)
+    A, l, r = workload(n, q, args.seed, 0, args.array)
     threads = oracle.max_threads()
     per_step = max(0.2, min(2.0, 90.0 / max(args.steps + args.warmup, 1)))
     s = max(threads, 8)
@@ -250,7 +263,7 @@ def run_reference(args, dist):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / max(len(times), 1), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": workload_name(n, q), "n": n, "q": q, "seed": args.seed,
+        "config": {"workload": workload_name(n, q, args.array), "n": n, "q": q, "seed": args.seed,
                    "sample_queries_per_step": per},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": "naive oracle, %d queries of the batch per step, %d timed steps"
@@ -276,7 +289,7 @@ def run_ours(args, dist):
     torch.cuda.set_device(dist.local)
     dev = torch.device("cuda", dist.local)
     n, q = int(args.n), int(args.q)
-    A, l, r = workload(n, q, args.seed, dist.rank)
+    A, l, r = workload(n, q, args.seed, dist.rank, args.array)
     dA = torch.from_numpy(A).to(dev)
     dl, dr = torch.from_numpy(l).to(dev), torch.from_numpy(r).to(dev)
     outs = {"plain": torch.empty(q, dtype=torch.int32, device=dev),
@@ -385,7 +398,9 @@ def run_ours(args, dist):
                 else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_launch": bytes_a1,
                 "traffic": profiled_traffic("paper_1706_06940_gb300/csrc/block_min.cu",
-                                            "profiles/block_minima_n1e8.md")}
+                                            "profiles/block_minima_n1e8.md", n, k)}
+    # device workspace of each form (the extra memory of Table 2)
+    ws_bytes = {f: rmq.rmq_batch_workspace_bytes(n, q, vcode[f], k=k, k_con=k_con) for f in forms}
     # whole-form HBM accounting (algorithmic bytes of the plain form)
     hbm_plain = None
     if "plain" in form_ms:
@@ -423,7 +438,7 @@ def run_ours(args, dist):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": workload_name(n, q), "n": n, "q": q, "seed": args.seed,
+            "config": {"workload": workload_name(n, q, args.array), "n": n, "q": q, "seed": args.seed,
                        "forms": forms, "k": k, "k_con": k_con, "k_autotuned": {"range": [32, 4096],
                                                                            "best_ms": tune_ms},
                        "l2": "flushed before each form (outside the timed events) by a 256 MiB write, then a 256 MiB "
@@ -433,6 +448,8 @@ def run_ours(args, dist):
             "forms": {f: {"ms": form_ms[f], "queries_per_s": q / (form_ms[f] * 1e-3),
                           "stages_ms": stages[f]} for f in forms},
             "hbm_plain": hbm_plain,
+            "memory": {f: {"workspace_bytes": ws_bytes[f], "pct_of_4n": 100.0 * ws_bytes[f] / (4 * n)}
+                       for f in forms},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,

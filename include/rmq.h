@@ -275,6 +275,15 @@ const char *rmq_strerror(rmq_status s);
  * with nb = ceil(n / k) (the memory model of Table 2).  -1 on bad arguments. */
 int64_t rmq_table_bytes(int64_t n, int32_t k);
 
+/* Device workspace, in bytes, that one rmq_batch_ex call with these
+ * arguments takes from the stream-ordered pool: the extra memory beside the
+ * 4n bytes of A, as Table 2 reports it.  Plain form: levels 0..lc of the
+ * block table and, for k >= 128, the minima of every 128 cells.  Contracted
+ * form: the endpoint bitmap with rank counts, A_Q (up to min(2q, n) - 1
+ * keys), the table over A_Q and the coarse index.  Host only; -1 on bad
+ * arguments (those rmq_batch_ex rejects). */
+int64_t rmq_batch_workspace_bytes(int64_t n, int64_t q, const rmq_opts *opts);
+
 /* The tuner's choice of form and block sizes for (n, q); host only. */
 rmq_status rmq_tune(int64_t n, int64_t q, rmq_opts *out);
 

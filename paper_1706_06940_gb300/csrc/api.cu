@@ -152,13 +152,17 @@ rmq_opts resolve_opts(int64_t n, int64_t q, const rmq_opts *opts) {
     return t;
 }
 
+// Keys of a plain batch call's workspace: levels 0..lc of the block table,
+// then, when k >= 128, the 128-cell minima of the two-level layout (Sec. 3.3).
+int64_t plain_table_keys(int64_t n, int logk) { return two_level_entries(cdiv(n, 1ll << logk)); }
+int64_t plain_m1_keys(int64_t n, int logk) { return logk >= 7 ? cdiv(n, 128) : 0; }
+
 rmq_status batch_plain(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
                        int logk, cudaStream_t s, Stages *sg) {
     const int64_t nb = cdiv(n, 1ll << logk);
     Workspace ws;
-    const int64_t te = two_level_entries(nb);
-    // the 128-cell minima of the two-level layout (Sec. 3.3) when k >= 128
-    const int64_t m1 = logk >= 7 ? cdiv(n, 128) : 0;
+    const int64_t te = plain_table_keys(n, logk);
+    const int64_t m1 = plain_m1_keys(n, logk);
     rmq_status st = ws.alloc((size_t)(te + m1) * 8, s);
     if (st != RMQ_OK) return st;
     uint64_t *T = static_cast<uint64_t *>(ws.p);
@@ -435,6 +439,16 @@ const char *rmq_strerror(rmq_status s) {
 int64_t rmq_table_bytes(int64_t n, int32_t k) {
     if (n <= 0 || n > kMaxN || !pow2_in_range(k)) return -1;
     return table_entries(n, ilog2_host((uint64_t)k)) * 8;
+}
+
+int64_t rmq_batch_workspace_bytes(int64_t n, int64_t q, const rmq_opts *opts) {
+    int32_t dummy = 0;
+    if (check_batch_args(&dummy, n, &dummy, &dummy, q, &dummy, opts) != RMQ_OK) return -1;
+    if (q == 0) return 0;
+    const rmq_opts o = resolve_opts(n, q, opts);
+    if (o.variant == RMQ_VARIANT_CONTRACTED) return (int64_t)con_workspace_bytes(n, q, ilog2_host((uint64_t)o.k_con));
+    const int logk = ilog2_host((uint64_t)o.k);
+    return (plain_table_keys(n, logk) + plain_m1_keys(n, logk)) * 8;
 }
 
 // The tuner: a choice measured by rmq_autotune for this (n, q) shape when

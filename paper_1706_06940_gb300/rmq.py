@@ -99,6 +99,7 @@ _SIGS = {
     "rmq_stream_status": (_i32, [_vp]),
     "rmq_strerror": (ctypes.c_char_p, [_i32]),
     "rmq_table_bytes": (_i64, [_i64, _i32]),
+    "rmq_batch_workspace_bytes": (_i64, [_i64, _i64, ctypes.POINTER(rmq_opts)]),
     "rmq_tune": (_i32, [_i64, _i64, ctypes.POINTER(rmq_opts)]),
     "rmq_block_minima": (_i32, [_vp, _i64, _i32, _vp, _vp]),
     "rmq_sparse_table_build": (_i32, [_vp, _i64, _vp]),
@@ -367,6 +368,12 @@ def rmq_strerror(status) -> str:
 
 def rmq_table_bytes(n: int, k: int) -> int:
     return int(load().rmq_table_bytes(int(n), int(k)))
+
+
+def rmq_batch_workspace_bytes(n: int, q: int, variant=0, k=0, k_con=0) -> int:
+    """Device workspace of one rmq_batch_ex call (-1 on bad arguments)."""
+    o = _opts(variant, k, k_con)
+    return int(load().rmq_batch_workspace_bytes(int(n), int(q), ctypes.byref(o)))
 
 
 def rmq_tune(n: int, q: int) -> dict:

@@ -57,6 +57,35 @@ def test_table_bytes_rejects_bad_arguments(lib):
     assert rmq.rmq_table_bytes(1, 32) == 8
 
 
+@pytest.mark.parametrize("n,k", [(10**8, 1024), (10**9, 512), (10**9, 4096), (1000, 32), (5, 64)])
+def test_plain_workspace_between_level_zero_and_the_full_table(lib, n, k):
+    """The plain form keeps levels 0..lc of the block table (at least level 0,
+    at most the full table of Table 2) plus, for k >= 128, one key per 128 cells."""
+    ws = rmq.rmq_batch_workspace_bytes(n, 1000, rmq.Variant.PLAIN, k=k)
+    nb = -(-n // k)
+    m1 = 8 * (-(-n // 128)) if k >= 128 else 0
+    assert 8 * nb + m1 <= ws <= rmq.rmq_table_bytes(n, k) + m1
+
+
+def test_contracted_workspace_holds_the_bitmap_and_a_q(lib):
+    n = 10**9
+    prev = 0
+    for q in (10, 10**4, 10**6, 10**7, 10**8, 10**9):
+        ws = rmq.rmq_batch_workspace_bytes(n, q, rmq.Variant.CONTRACTED, k_con=256)
+        a_q = 8 * (min(2 * q, n) - 1)
+        assert ws >= 8 * (n // 32) + a_q, q
+        assert ws >= prev
+        prev = ws
+
+
+def test_workspace_bytes_rejects_bad_arguments(lib):
+    assert rmq.rmq_batch_workspace_bytes(0, 10) == -1
+    assert rmq.rmq_batch_workspace_bytes(100, -1) == -1
+    assert rmq.rmq_batch_workspace_bytes(100, 10, k=48) == -1
+    assert rmq.rmq_batch_workspace_bytes(100, 10, variant=7) == -1
+    assert rmq.rmq_batch_workspace_bytes(100, 0) == 0
+
+
 @pytest.mark.parametrize("n,q", [(1, 1), (1000, 10), (10**6, 1000), (10**8, 10**7), (2**31 - 1, 2**30)])
 def test_tune_returns_valid_options(lib, n, q):
     t = rmq.rmq_tune(n, q)
