@@ -49,8 +49,23 @@ rmq_status rmq_autotune(const int32_t *A, int64_t n, const int32_t *l, const int
         return RMQ_ERR_INVALID_ARG;
     if (!A || n <= 0 || q <= 0 || !l || !r || !out) return RMQ_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // every timed run starts from an L2 holding none of the batch, as a call
+    // on fresh data does: a write of twice the L2 size evicts it (skipped if
+    // that buffer cannot be had)
+    int dev = 0, l2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    const size_t flush_bytes = 2 * (size_t)std::max(l2, 0);
+    void *flush = nullptr;
+    if (flush_bytes && cudaMallocAsync(&flush, flush_bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        flush = nullptr;
+    }
     cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return RMQ_ERR_CUDA;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (flush) cudaFreeAsync(flush, s);
+        return RMQ_ERR_CUDA;
+    }
     rmq_opts win{RMQ_VARIANT_PLAIN, k_min, 512, 0};
     float win_ms = 1e30f;
     rmq_status st = RMQ_OK;
@@ -59,7 +74,8 @@ rmq_status rmq_autotune(const int32_t *A, int64_t n, const int32_t *l, const int
         for (int32_t k = k_min; k <= k_max && st == RMQ_OK; k *= 2) {
             rmq_opts o{form, form == RMQ_VARIANT_PLAIN ? k : 0, form == RMQ_VARIANT_CONTRACTED ? k : 0, 0};
             float ms = 1e30f;
-            for (int rep = 0; rep < 3 && st == RMQ_OK; ++rep) {   // the first run warms caches and the pool
+            for (int rep = 0; rep < 4 && st == RMQ_OK; ++rep) {   // the first run warms the pool
+                if (flush) cudaMemsetAsync(flush, rep, flush_bytes, s);
                 cudaEventRecord(e0, s);
                 st = rmq_batch_ex(A, n, l, r, q, out, &o, stream);
                 cudaEventRecord(e1, s);
@@ -77,6 +93,7 @@ rmq_status rmq_autotune(const int32_t *A, int64_t n, const int32_t *l, const int
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (flush) cudaFreeAsync(flush, s);
     if (st != RMQ_OK) return st;
     // remember the winner; both block sizes are filled in for later calls
     rmq_opts fill;
