@@ -292,7 +292,7 @@ rmq_status rmq_tune(int64_t n, int64_t q, rmq_opts *out);
  * [k_min, k_max] (0, 0 = [32, 4096]) and for the form(s) allowed by
  * `variant` (AUTO = both), and returns the fastest options in *best (and its
  * time in ms in *best_ms, may be NULL).  Each candidate runs once untimed,
- * then three times, each after a write of twice the L2 size has evicted the
+ * then three times, each after a read of twice the L2 size has evicted the
  * batch from L2; its time is the best of the three.  `out` receives answers while it
  * measures.  Waits for the device.  With variant == AUTO the choice is
  * remembered for the (n, q) shape (log2 rounded) and used by rmq_tune,

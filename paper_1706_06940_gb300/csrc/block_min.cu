@@ -15,17 +15,20 @@ constexpr int kThreads = 256;
 // Warp per block (k / EPV >= 32 vectors): every lane reads k/(32*EPV)
 // consecutive-lane 16-byte vectors (coalesced, streaming), keeps the minimum
 // packed key, and a shuffle reduction gives the block minimum.  UNR vectors
-// are loaded before any is used to keep enough bytes in flight.  With REV
-// the blocks are visited from the end (a sequence just written is then read
-// while its most recent part is still in L2).
+// are loaded before any is used to keep enough bytes in flight; when a block
+// gives each lane fewer than 8 vectors, a warp takes G = 8 / UNR consecutive
+// blocks at once, so that it still reads 4 KB of contiguous memory per round.
+// With REV the blocks are visited from the end (a sequence just written is
+// then read while its most recent part is still in L2).
 // With M1 (int32 source, k >= 128) the kernel also stores the minimum of
 // every 128 consecutive cells (one vector per lane), the small blocks of the
 // paper's two-level layout (Sec. 3.3, k1 = 128 dividing k2 = k): a 32-bit
 // warp reduction of the values, then the leftmost lane holding the minimum.
 // M1 has ceil(n / 128) entries.
-template <class Src, int UNR, bool VEC, bool REV, bool WM1>
+template <class Src, int UNR, bool VEC, bool REV, bool WM1, int G>
 __global__ void __launch_bounds__(kThreads) k_block_min_warp(Src src, Len len, int logk, uint64_t *__restrict__ T0,
                                                              uint64_t *__restrict__ M1) {
+    static_assert(G == 1 || UNR * G == 8, "a group of blocks is 8 vectors per lane");
     pdl_wait();
     constexpr int EPV = Src::EPV;
     const int64_t n = len.get();
@@ -36,38 +39,62 @@ __global__ void __launch_bounds__(kThreads) k_block_min_warp(Src src, Len len, i
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int vpb = (int)(K / EPV);
-    const int vpl = vpb >> 5;
-    for (int64_t bi = warp; bi < nfull; bi += nwarps) {
-        const int64_t b = REV ? nfull - 1 - bi : bi;
-        const int64_t v0 = b * vpb + lane;
-        // the warp's next block is fetched into L2 while this one is reduced
-        if (VEC && lane == 0 && bi + nwarps < nfull) {
-            const int64_t bn = REV ? nfull - 1 - (bi + nwarps) : bi + nwarps;
-            prefetch_l2_bulk(src.a + bn * K, (uint32_t)(K * sizeof(*src.a)));
+    const int vpl = vpb >> 5;   // == UNR when G > 1
+    // reduce the UNR vectors of row group u of block b already loaded in kk
+    auto fold = [&](int64_t b, int u, uint64_t (&kk)[UNR][EPV], uint64_t &best) {
+#pragma unroll
+        for (int x = 0; x < UNR; ++x) {
+            uint64_t rk = KEY_MAX;
+#pragma unroll
+            for (int e = 0; e < EPV; ++e) rk = kmin(rk, kk[x][e]);
+            best = kmin(best, rk);
+            if (WM1) {   // the row of 128 cells this vector belongs to
+                const uint32_t hv = (uint32_t)(rk >> 32);
+                const uint32_t mh = __reduce_min_sync(0xffffffffu, hv);
+                const int f = __ffs(__ballot_sync(0xffffffffu, hv == mh)) - 1;
+                const uint64_t rowkey = __shfl_sync(0xffffffffu, rk, f);
+                if (lane == 0) M1[b * (K >> 7) + u + x] = rowkey;
+            }
         }
+    };
+    auto one_block = [&](int64_t b) {
+        const int64_t v0 = b * vpb + lane;
         uint64_t best = KEY_MAX;
         for (int u = 0; u < vpl; u += UNR) {
             uint64_t kk[UNR][EPV];
 #pragma unroll
             for (int x = 0; x < UNR; ++x) src.template vec<VEC>(v0 + (int64_t)(u + x) * 32, kk[x]);
-#pragma unroll
-            for (int x = 0; x < UNR; ++x) {
-                uint64_t rk = KEY_MAX;
-#pragma unroll
-                for (int e = 0; e < EPV; ++e) rk = kmin(rk, kk[x][e]);
-                best = kmin(best, rk);
-                if (WM1) {   // the row of 128 cells this vector belongs to
-                    const uint32_t hv = (uint32_t)(rk >> 32);
-                    const uint32_t mh = __reduce_min_sync(0xffffffffu, hv);
-                    const int f = __ffs(__ballot_sync(0xffffffffu, hv == mh)) - 1;
-                    const uint64_t rowkey = __shfl_sync(0xffffffffu, rk, f);
-                    if (lane == 0) M1[b * (K >> 7) + u + x] = rowkey;
-                }
-            }
+            fold(b, u, kk, best);
         }
         best = warp_min(best);
         if (lane == 0) T0[b] = best;
+    };
+    const int64_t ngrp = nfull / G;   // whole groups of G blocks
+    for (int64_t gi = warp; gi < ngrp; gi += nwarps) {
+        const int64_t b0 = (REV ? ngrp - 1 - gi : gi) * G;
+        // the warp's next group is fetched into L2 while this one is reduced
+        if (VEC && lane == 0 && gi + nwarps < ngrp) {
+            const int64_t bn = (REV ? ngrp - 1 - (gi + nwarps) : gi + nwarps) * G;
+            prefetch_l2_bulk(src.a + bn * K, (uint32_t)(G * K * sizeof(*src.a)));
+        }
+        if (G == 1) {
+            one_block(b0);
+        } else {
+            uint64_t kk[G][UNR][EPV];
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int x = 0; x < UNR; ++x) src.template vec<VEC>((b0 + g) * vpb + lane + x * 32, kk[g][x]);
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                uint64_t best = KEY_MAX;
+                fold(b0 + g, 0, kk[g], best);
+                best = warp_min(best);
+                if (lane == 0) T0[b0 + g] = best;
+            }
+        }
     }
+    for (int64_t b = ngrp * G + warp; b < nfull; b += nwarps) one_block(b);   // fewer than G left
     if (nfull < nb && warp == nfull % nwarps) {  // the short last block
         uint64_t best = KEY_MAX;
         for (int64_t i = nfull * K + lane; i < n; i += 32) best = kmin(best, src.one(i));
@@ -141,14 +168,16 @@ cudaError_t block_min_dispatch(Src src, Len len, int64_t n_max, int logk, uint64
     if (vpb >= 32) {
         const int64_t ctas = std::min<int64_t>(cdiv(nb, kThreads / 32), (int64_t)di.sms * 8);
         const int vpl = vpb / 32;
-        if (vpl >= 8) (M1 ? launch_pdl(k_block_min_warp<Src, 8, VEC, REV, Src::EPV == 4>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0, M1)
-                              : launch_pdl(k_block_min_warp<Src, 8, VEC, REV, false>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0, M1));
-        else if (vpl >= 4) (M1 ? launch_pdl(k_block_min_warp<Src, 4, VEC, REV, Src::EPV == 4>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0, M1)
-                              : launch_pdl(k_block_min_warp<Src, 4, VEC, REV, false>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0, M1));
-        else if (vpl >= 2) (M1 ? launch_pdl(k_block_min_warp<Src, 2, VEC, REV, Src::EPV == 4>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0, M1)
-                              : launch_pdl(k_block_min_warp<Src, 2, VEC, REV, false>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0, M1));
-        else (M1 ? launch_pdl(k_block_min_warp<Src, 1, VEC, REV, Src::EPV == 4>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0, M1)
-                              : launch_pdl(k_block_min_warp<Src, 1, VEC, REV, false>, (unsigned)ctas, kThreads, 0, s, src, len, logk, T0, M1));
+#define RMQ_BMW(U, G)                                                                                          \
+    (M1 ? launch_pdl(k_block_min_warp<Src, U, VEC, REV, Src::EPV == 4, G>, (unsigned)ctas, kThreads, 0, s, src, len, \
+                     logk, T0, M1)                                                                              \
+        : launch_pdl(k_block_min_warp<Src, U, VEC, REV, false, G>, (unsigned)ctas, kThreads, 0, s, src, len, logk,   \
+                     T0, M1))
+        if (vpl >= 8) RMQ_BMW(8, 1);
+        else if (vpl >= 4) RMQ_BMW(4, 2);
+        else if (vpl >= 2) RMQ_BMW(2, 4);
+        else RMQ_BMW(1, 8);
+#undef RMQ_BMW
     } else {
         const int64_t nvec = nb * vpb;
         const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(nvec, 128 * (kThreads / 32)), (int64_t)di.sms * 8));

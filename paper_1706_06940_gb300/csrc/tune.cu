@@ -17,6 +17,20 @@ namespace {
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, rmq_opts> g_tuned;   // (round(log2 n), round(log2 q)) -> choice
 
+// Reads `vecs` 16-byte vectors (their values do not matter) so that L2 holds
+// this buffer's clean lines and none of a batch's; the xor of what it read
+// is stored only in the impossible case that it equals the buffer's address.
+__global__ void k_l2_evict(const int4 *__restrict__ p, int64_t vecs, int4 *sink) {
+    unsigned acc = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < vecs; i += (int64_t)gridDim.x * blockDim.x) {
+        int4 v;
+        asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p + i));
+        acc ^= (unsigned)(v.x ^ v.y ^ v.z ^ v.w);
+    }
+    if (acc == (unsigned)reinterpret_cast<uintptr_t>(p) && threadIdx.x == 0) sink->x = (int)acc;
+}
+
 std::pair<int, int> shape_key(int64_t n, int64_t q) {
     auto lg = [](int64_t x) { return (int)std::lround(std::log2((double)x)); };   // nearest log2
     return {lg(std::max<int64_t>(n, 1)), lg(std::max<int64_t>(q, 1))};
@@ -50,8 +64,8 @@ rmq_status rmq_autotune(const int32_t *A, int64_t n, const int32_t *l, const int
     if (!A || n <= 0 || q <= 0 || !l || !r || !out) return RMQ_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // every timed run starts from an L2 holding none of the batch, as a call
-    // on fresh data does: a write of twice the L2 size evicts it (skipped if
-    // that buffer cannot be had)
+    // on fresh data does: a read of twice the L2 size evicts it and leaves
+    // only clean lines (skipped if that buffer cannot be had)
     int dev = 0, l2 = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
@@ -75,7 +89,11 @@ rmq_status rmq_autotune(const int32_t *A, int64_t n, const int32_t *l, const int
             rmq_opts o{form, form == RMQ_VARIANT_PLAIN ? k : 0, form == RMQ_VARIANT_CONTRACTED ? k : 0, 0};
             float ms = 1e30f;
             for (int rep = 0; rep < 4 && st == RMQ_OK; ++rep) {   // the first run warms the pool
-                if (flush) cudaMemsetAsync(flush, rep, flush_bytes, s);
+                if (flush) {
+                    k_l2_evict<<<(unsigned)(dev_info().sms * 8), 256, 0, s>>>(static_cast<const int4 *>(flush),
+                                                                             (int64_t)(flush_bytes / 16),
+                                                                             static_cast<int4 *>(flush));
+                }
                 cudaEventRecord(e0, s);
                 st = rmq_batch_ex(A, n, l, r, q, out, &o, stream);
                 cudaEventRecord(e1, s);
