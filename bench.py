@@ -60,7 +60,7 @@ def parse_args():
     p.add_argument("--k", type=int, default=0, help="plain-form block size (0 = tuned)")
     p.add_argument("--k-con", type=int, default=0, help="contracted-form block size (0 = tuned)")
     p.add_argument("--e2e-steps", type=int, default=3)
-    p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline")
+    p.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -212,14 +212,16 @@ def cpu_baseline(A, l, r, budget_s):
 
     import oracle
     threads = oracle.max_threads()
-    s = min(len(l), max(threads, 8))
-    t0 = time.perf_counter()
-    oracle.rmq_naive(A, l[:s], r[:s])
-    dt = max(time.perf_counter() - t0, 1e-6)
-    s2 = int(min(len(l), max(s, budget_s * s / dt)))
-    t0 = time.perf_counter()
-    oracle.rmq_naive(A, l[:s2], r[:s2])
-    dt2 = time.perf_counter() - t0
+    # grow the sample until one run takes at least half the budget (a small
+    # sample is dominated by its longest query on one thread)
+    s2 = min(len(l), max(threads, 8))
+    while True:
+        t0 = time.perf_counter()
+        oracle.rmq_naive(A, l[:s2], r[:s2])
+        dt2 = time.perf_counter() - t0
+        if dt2 >= 0.5 * budget_s or s2 == len(l):
+            break
+        s2 = int(min(len(l), max(2 * s2, 0.8 * budget_s * s2 / max(dt2, 1e-6))))
     width = float(np.sum(r[:s2].astype(np.int64) - l[:s2] + 1))
     return {"value": s2 / dt2, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "naive oracle on the first %d of the %d queries (%.3g cells scanned), %.1f s"
