@@ -433,10 +433,13 @@ __device__ __forceinline__ int stage_pos(int i) {
 // The tile's offset and the total m come from the tile counts of
 // k_bits_partial (every CTA adds up the counts of the tiles before it);
 // block 0 stores m.
+// bs, nbk: bucket_shift(n), bucket_count(n) (word indices are below 2^26, so
+// the per-word arithmetic is 32-bit).
 __global__ void __launch_bounds__(kT, 6) k_bits_final(uint2 *__restrict__ BP, int64_t nbp,
                                                       const uint32_t *__restrict__ partial, int64_t *m_dev,
-                                                      int64_t ntA, uint64_t *__restrict__ AQ, int64_t n, int logk_q,
-                                                      uint32_t *__restrict__ CP, uint16_t *__restrict__ CB) {
+                                                      int64_t ntA, uint64_t *__restrict__ AQ, int logk_q,
+                                                      uint32_t *__restrict__ CP, uint16_t *__restrict__ CB, int bs,
+                                                      int64_t nbk) {
     pdl_wait();
     __shared__ uint32_t wsum[kT / 32], wbefore[kT / 32], wall[kT / 32];
     __shared__ __align__(16) uint32_t stage[2][kT / 32][32 * kIPT];   // words, exclusive counts
@@ -507,34 +510,40 @@ __global__ void __launch_bounds__(kT, 6) k_bits_final(uint2 *__restrict__ BP, in
     // the coarse index serves the batch query, whose geometry is kCoarseCapCon's
     const Coarse g = coarse_geom(nbq > 0 ? nbq : 1, kCoarseCapCon);
     const int sh = logk_q + g.lc;
-    const int bs = bucket_shift(n);
-    const int64_t nbk = bucket_count(n);
-    if (index && blockIdx.x == 0 && threadIdx.x == 0) CB[nbk] = (uint16_t)(g.nbc - 1);
+    const uint32_t nbc = (uint32_t)g.nbc;
+    const uint32_t bmask = (1u << (bs - 5)) - 1u;   // word e starts a bucket iff (e & bmask) == 0
+    if (index && blockIdx.x == 0 && threadIdx.x == 0) CB[nbk] = (uint16_t)(nbc - 1);
+    const uint32_t ebase = (uint32_t)base;
+    const bool all_in = base + 32 * kIPT <= nbp - 1;   // no end entry and nothing past it
 #pragma unroll
     for (int i = 0; i < kIPT; ++i) {
         const uint32_t ex = sx[stage_pos(i * 32 + lane)], word = st[stage_pos(i * 32 + lane)];
-        const int64_t e = base + i * 32 + lane;
-        if (e < nbp) {
-            BP[e] = make_uint2(word, ex);
-            if ((e & (kATile / 32 - 1)) == 0 && (e / (kATile / 32)) < ntA) {
-                const int64_t sg = (int64_t)ex - 1;
-                if (sg >= 0 && sg <= m - 2) AQ[sg] = KEY_MAX;
-            }
-            if (index && e < nbp - 1) {
-                // a coarse block of A_Q begins at the (j 2^sh)-th mark
-                const int64_t j = ((int64_t)ex + (1ll << sh) - 1) >> sh;
-                const int64_t t = (j << sh) - (int64_t)ex;
-                if (j < g.nbc && t < (int64_t)__popc(word)) {
+        const uint32_t e = ebase + (uint32_t)(i * 32 + lane);
+        if (!all_in && (int64_t)e >= nbp) continue;
+        BP[e] = make_uint2(word, ex);
+        if (lane == 0 && (int64_t)(e >> 5) < ntA) {   // the first word of a contraction tile
+            const int64_t sg = (int64_t)ex - 1;
+            if (sg >= 0 && sg <= m - 2) AQ[sg] = KEY_MAX;
+        }
+        if (index && (all_in || (int64_t)e < nbp - 1)) {
+            // a coarse block of A_Q begins at the (j 2^sh)-th mark: is one of
+            // this word's marks ex .. ex + c - 1 a multiple of 2^sh?  (2^sh >= 32,
+            // so at most one is; for ex = 0, ex - 1 wraps and mark 0 counts)
+            const uint32_t c = __popc(word);
+            if (c && ((ex + c - 1u) >> sh) != ((ex - 1u) >> sh)) {
+                const uint32_t jb = (ex + (1u << sh) - 1u) >> sh;
+                const uint32_t t = (jb << sh) - ex;
+                if (jb < nbc) {
                     uint32_t wd = word;
-                    for (int64_t d = 0; d < t; ++d) wd &= wd - 1u;   // drop the t lower marks
-                    CP[j] = (uint32_t)(e * 32 + __ffs(wd) - 1);
+                    for (uint32_t d = 0; d < t; ++d) wd &= wd - 1u;   // drop the t lower marks
+                    CP[jb] = e * 32u + (uint32_t)(__ffs(wd) - 1);
                 }
-                // bucket start: the last coarse block that begins at or before it
-                if (((e << 5) & ((1ll << bs) - 1)) == 0) {
-                    const int64_t upto = (int64_t)ex + (word & 1u);   // marks <= 32e
-                    const int64_t cb = upto >= 1 ? (upto - 1) >> sh : 0;
-                    CB[(e << 5) >> bs] = (uint16_t)(cb < g.nbc - 1 ? cb : g.nbc - 1);
-                }
+            }
+            // bucket start: the last coarse block that begins at or before it
+            if ((e & bmask) == 0) {
+                const uint32_t upto = ex + (word & 1u);   // marks <= 32e
+                const uint32_t cb = upto >= 1u ? (upto - 1u) >> sh : 0u;
+                CB[e >> (bs - 5)] = (uint16_t)(cb < nbc - 1u ? cb : nbc - 1u);
             }
         }
     }
@@ -781,7 +790,8 @@ cudaError_t bitmap_ranks(uint2 *BP, int64_t n, int64_t *m_dev, uint64_t *AQ, uin
     const int64_t nbp = bitmap_entries(n);
     const int64_t tiles = cdiv(nbp, kTile);
     launch_pdl(k_bits_partial, (unsigned)tiles, kT, 0, s, BP, nbp, aux);
-    launch_pdl(k_bits_final, (unsigned)tiles, kT, 0, s, BP, nbp, aux, m_dev, AQ ? cdiv(n, kATile) : 0, AQ, n, logk_q, CP, CB);
+    launch_pdl(k_bits_final, (unsigned)tiles, kT, 0, s, BP, nbp, aux, m_dev, AQ ? cdiv(n, kATile) : 0, AQ, logk_q, CP, CB,
+               bucket_shift(n), bucket_count(n));
     note_launches(2);
     return cudaGetLastError();
 }
@@ -904,7 +914,8 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     // m is known on the device only: room for the largest coarse table
     const size_t smem = (size_t)kCoarseCapCon * sizeof(uint64_t);
     if (vecq)
-        e = launch_query_two<SrcU64, true, true, true>(di.device, (unsigned)qctas, smem, s, src, lenq, logk_con,
+        e = launch_query_two<SrcU64, true, true, true>(di.device, (unsigned)qctas,
+                                                       smem + query_ring_bytes<true, true>(), s, src, lenq, logk_con,
                                                        kCoarseCapCon, T, nullptr, l, r, BP, CP, CB, nullptr, n,
                                                        out, q, nullptr);
     else

@@ -452,9 +452,20 @@ __device__ __forceinline__ void resolve_queued(const Src src, int64_t n, int log
 //     Phase A needs only the coarse blocks of a_i and b_i - 1, which the
 //     coarse index (CP, CB) gives from l_i and r_i - 1; the ranks themselves
 //     are looked up in BP for the queries left to phase B.
-//   cap: the coarse geometry of the table (coarse_geom(nb, cap)); the
-//     dynamic shared memory holds its coarse table (coarse_geom(...).size()
-//     entries at most).
+//   cap: the coarse geometry of the table (coarse_geom(nb, cap)).
+// Dynamic shared memory: for the plain form with VECQ, each warp's ring of
+// the l, r of its next kQueryRing steps (query_ring_bytes in all), then the
+// coarse table (coarse_geom(...).size() keys at most).  The contracted form
+// loads the next step's l, r into registers instead: the ring's 64 KB per SM
+// cost its phase B more than the deeper prefetch saved.
+constexpr int kQueryRing = 4;
+template <bool CON, bool VECQ>
+__host__ __device__ constexpr bool query_uses_ring() { return VECQ && !CON; }
+template <bool CON, bool VECQ>
+__host__ __device__ constexpr size_t query_ring_bytes() {
+    return query_uses_ring<CON, VECQ>() ? (size_t)(kQueryThreads / 32) * kQueryRing * 2 * 32 * 16 : 0;
+}
+
 template <class Src, bool CON, bool VECQ, bool VEC>
 __global__ void __launch_bounds__(kQueryThreads, kQueryCtasPerSm)
 k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
@@ -470,8 +481,11 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
     // as 32 are queued it resolves them (phase B: fine table and edge scans),
     // so the latency of that work overlaps the streaming of other warps.
     constexpr int kQueue = 160;   // a step adds at most 128
-    extern __shared__ __align__(16) uint64_t query_coarse_smem[];
-    uint64_t *cs = query_coarse_smem;
+    constexpr bool RING = query_uses_ring<CON, VECQ>();
+    constexpr int kRing = kQueryRing;
+    extern __shared__ __align__(16) uint64_t query_dyn_smem[];
+    int4 *ring = reinterpret_cast<int4 *>(query_dyn_smem);
+    uint64_t *cs = query_dyn_smem + query_ring_bytes<CON, VECQ>() / sizeof(uint64_t);
     __shared__ uint32_t cp[CON ? kCoarseBlocksMax : 1];
     __shared__ uint16_t cb[CON ? kBucketsMax : 1];
     __shared__ uint32_t queue[kQueryThreads / 32][kQueue];
@@ -498,9 +512,21 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
     };
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    // the next step's l, r are loaded before the current step is processed, so
-    // every warp keeps a batch of loads in flight
+    // RING: the l, r of the warp's next kRing steps are in flight at any
+    // time: each lane copies its 16 bytes of l and of r into its slots of the
+    // warp's ring (one commit group per step, empty past the end of the
+    // batch).  Otherwise the next step's l, r are loaded into registers
+    // before the current step is processed.
     const int64_t stride = nwarps * 128;
+    int4 *wring = ring + (threadIdx.x >> 5) * (kRing * 64);
+    const uint32_t ring_sh = RING ? (uint32_t)__cvta_generic_to_shared(wring) : 0u;
+    auto issue = [&](int64_t b, int slot) {
+        if (b + 3 < q) {
+            cp_async16(ring_sh + (uint32_t)(slot * 64 + lane) * 16u, L + b);
+            cp_async16(ring_sh + (uint32_t)(slot * 64 + 32 + lane) * 16u, R + b);
+        }
+        cp_async_commit();
+    };
     int4 p0 = make_int4(0, 0, 0, 0), p1 = p0;
     auto fetch = [&](int64_t b) {
         if (VECQ && b + 3 < q) {
@@ -508,17 +534,30 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
             p1 = __ldcs(reinterpret_cast<const int4 *>(R + b));
         }
     };
-    fetch(warp * 128 + lane * 4);
+    if (RING) {
+#pragma unroll
+        for (int j = 0; j < kRing; ++j) issue(warp * 128 + j * stride + lane * 4, j);
+    } else {
+        fetch(warp * 128 + lane * 4);
+    }
+    int slot = 0;
     const int32_t na = (int32_t)n_a;
     for (int64_t wb = warp * 128; wb < q; wb += stride) {
         const int64_t base = wb + lane * 4;
         const bool full = VECQ && base + 3 < q;
         int32_t lq[4], rq[4];
+        if (RING) {
+            cp_async_wait<kRing - 1>();   // this step's copies have landed
+            if (full) {
+                p0 = wring[slot * 64 + lane];
+                p1 = wring[slot * 64 + 32 + lane];
+            }
+        }
         if (full) {
             lq[0] = p0.x; lq[1] = p0.y; lq[2] = p0.z; lq[3] = p0.w;
             rq[0] = p1.x; rq[1] = p1.y; rq[2] = p1.z; rq[3] = p1.w;
         }
-        fetch(base + stride);
+        if (!RING) fetch(base + stride);
         if (!full) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -551,6 +590,10 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
             o[i] = !ok ? -1 : (single ? lq[i] : (inside ? (int32_t)key_pos(m) : -1));
             need |= (use && !inside ? 1u : 0u) << i;
         }
+        if (RING) {   // the slot's values are used: it takes the step kRing on
+            issue(base + kRing * stride, slot);
+            slot = slot + 1 == kRing ? 0 : slot + 1;
+        }
         if (full) {
             __stcs(reinterpret_cast<int4 *>(out + base), make_int4(o[0], o[1], o[2], o[3]));
         } else {
@@ -575,18 +618,20 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
         if (!CON && bad && err) atomicOr(err, ERR_QUERY_RANGE);
     }
     if (nq > 0) resolve(nq);
+    if (RING) cp_async_wait<0>();   // no copy is left in flight (all were empty)
 }
 
-// Launches k_query_two with `smem` bytes of coarse table (at most
-// kCoarseCapMax entries); the first launch of each instantiation on a device
-// raises the kernel's dynamic shared memory limit to that maximum.
+// Launches k_query_two with `smem` bytes of dynamic shared memory (the ring
+// plus at most kCoarseCapMax keys of coarse table); the first launch of each
+// instantiation on a device raises the kernel's limit to that maximum.
 template <class Src, bool CON, bool VECQ, bool VEC, class... Args>
 inline cudaError_t launch_query_two(int device, unsigned ctas, size_t smem, cudaStream_t s, Args... args) {
     static bool raised[64] = {false};
     auto kern = k_query_two<Src, CON, VECQ, VEC>;
     if (device < 0 || device >= 64 || !raised[device]) {
-        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)(kCoarseCapMax * sizeof(uint64_t)));
+        const cudaError_t e = cudaFuncSetAttribute(
+            kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            (int)(query_ring_bytes<CON, VECQ>() + kCoarseCapMax * sizeof(uint64_t)));
         if (e != cudaSuccess) return e;
         if (device >= 0 && device < 64) raised[device] = true;
     }

@@ -22,11 +22,12 @@ cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint
     const Len len{n, nullptr};
     const int64_t ctas = query_ctas(q, di.sms);
     const int64_t nb = n > 0 ? ((n - 1) >> logk) + 1 : 0;
-    const size_t smem = (size_t)coarse_geom(nb, cap).size() * sizeof(uint64_t);
+    const size_t cs_bytes = (size_t)coarse_geom(nb, cap).size() * sizeof(uint64_t);
     cudaError_t e;
-#define RMQ_LQ2(VQ, V)                                                                                             \
-    e = launch_query_two<SrcI32, false, VQ, V>(di.device, (unsigned)ctas, smem, s, src, len, logk, cap, T, Cs, l, r, \
-                                               nullptr, nullptr, nullptr, M1, n, out, q, err)
+#define RMQ_LQ2(VQ, V)                                                                                    \
+    e = launch_query_two<SrcI32, false, VQ, V>(di.device, (unsigned)ctas,                                \
+                                               query_ring_bytes<false, VQ>() + cs_bytes, s, src, len, logk, \
+                                               cap, T, Cs, l, r, nullptr, nullptr, nullptr, M1, n, out, q, err)
     if (vecq && vec) RMQ_LQ2(true, true);
     else if (vecq) RMQ_LQ2(true, false);
     else if (vec) RMQ_LQ2(false, true);
