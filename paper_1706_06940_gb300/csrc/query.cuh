@@ -14,6 +14,22 @@ struct Pending {
     uint32_t lb = 0;
 };
 
+// Edge parts a CTA's warps defer to the end of the kernel, when all its
+// warps drain them together: the number of parts per warp varies a lot
+// (about 1.6 on average for a uniform batch, up to 8 on some warps), and a
+// warp that drained its own parts at once would hold the whole kernel back.
+// A part's result is combined into its query's entry with a shared-memory
+// atomicMin; the entries' answers are written after the drain.
+constexpr int kPoolParts = 256;
+constexpr int kPoolQueries = 256;
+struct PartPool {
+    uint32_t lo[kPoolParts], hi[kPoolParts], lb[kPoolParts];
+    uint16_t q[kPoolParts];
+    unsigned long long best[kPoolQueries];
+    uint32_t qid[kPoolQueries];
+    int nparts, nq;   // reserved so far (may exceed the capacities)
+};
+
 // Step 4 on the block table for one valid (sub)query, before any scan.
 // [lo, hi] is the range in the source's index space; [la, ra] bound its ends
 // in A's positions (equal to [lo, hi] for the plain form; for A_Q, entry j
@@ -403,7 +419,8 @@ __device__ __forceinline__ void resolve_queued(const Src src, int64_t n, int log
                                             int64_t nb, const uint64_t *cs, const Coarse g,
                                             const int32_t *__restrict__ L, const int32_t *__restrict__ R,
                                             const uint2 *__restrict__ BP, int32_t *__restrict__ out,
-                                            const uint32_t *q_ids, int take, const uint64_t *M1) {
+                                            const uint32_t *q_ids, int take, const uint64_t *M1,
+                                            PartPool *pool) {
     const int lane = threadIdx.x & 31;
     const int sh = logk + g.lc;
     const bool has = lane < take;
@@ -439,10 +456,65 @@ __device__ __forceinline__ void resolve_queued(const Src src, int64_t n, int log
             }
         }
     }
-    warp_drain_scans<Src, VEC>(src, n, hl, pl, best, M1);
-    warp_drain_scans<Src, VEC>(src, n, hr, pr, best, M1);
-    if (has) out[qid] = (int32_t)key_pos(best);
+    // a query with edge parts goes to the CTA's pool when both fit; its
+    // answer is then written after the pool's drain
+    bool defer = false;
+    const int np = (hl ? 1 : 0) + (hr ? 1 : 0);
+    if (np) {
+        const int pi = atomicAdd(&pool->nparts, np);
+        const int qi = atomicAdd(&pool->nq, 1);
+        defer = pi + np <= kPoolParts && qi < kPoolQueries;
+        if (defer) {
+            pool->qid[qi] = qid;
+            pool->best[qi] = best;
+        } else if (qi < kPoolQueries) {
+            pool->qid[qi] = 0xffffffffu;   // reserved, unused
+        }
+        int w = pi;
+        for (int side = 0; side < 2; ++side) {
+            if (!(side == 0 ? hl : hr)) continue;
+            if (w < kPoolParts) {
+                const Pending &pp = side == 0 ? pl : pr;
+                pool->lo[w] = defer ? (uint32_t)pp.lo : 1u;   // 1 > 0: an empty part
+                pool->hi[w] = defer ? (uint32_t)pp.hi : 0u;
+                pool->lb[w] = pp.lb;
+                pool->q[w] = (uint16_t)(defer ? qi : 0);
+            }
+            ++w;
+        }
+    }
+    warp_drain_scans<Src, VEC>(src, n, hl && !defer, pl, best, M1);
+    warp_drain_scans<Src, VEC>(src, n, hr && !defer, pr, best, M1);
+    if (has && !defer) out[qid] = (int32_t)key_pos(best);
     __syncwarp();
+}
+
+// The CTA's warps drain the pooled edge parts (warp w takes parts w, w + W,
+// ...), then write the pooled queries' answers.  Called by all threads of
+// the CTA, after every warp has finished its queries.
+template <class Src, bool VEC>
+__device__ __forceinline__ void drain_pool(const Src src, int64_t n, const uint64_t *M1, PartPool *pool,
+                                           int32_t *__restrict__ out) {
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int parts = min(pool->nparts, kPoolParts);
+    for (int p = w; p < parts; p += nw) {
+        const uint32_t lo = pool->lo[p], hi = pool->hi[p];
+        if (lo > hi) continue;   // reserved, unused
+        uint64_t v;
+        if constexpr (Src::EPV == 4) {
+            v = M1 ? warp_range_min_m1<VEC>(src, M1, n, lo, hi) : warp_scan_min<Src, VEC>(src, n, lo, hi, pool->lb[p]);
+        } else {
+            v = warp_scan_min<Src, VEC>(src, n, lo, hi, pool->lb[p]);
+        }
+        if (lane == 0) atomicMin(&pool->best[pool->q[p]], (unsigned long long)v);
+    }
+    __syncthreads();
+    const int nq = min(pool->nq, kPoolQueries);
+    for (int e = threadIdx.x; e < nq; e += blockDim.x) {
+        const uint32_t qid = pool->qid[e];
+        if (qid != 0xffffffffu) out[qid] = (int32_t)key_pos(pool->best[e]);
+    }
 }
 
 //   plain (CON = false): the source is A; query i covers [l_i, r_i].
@@ -489,6 +561,8 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
     __shared__ uint32_t cp[CON ? kCoarseBlocksMax : 1];
     __shared__ uint16_t cb[CON ? kBucketsMax : 1];
     __shared__ uint32_t queue[kQueryThreads / 32][kQueue];
+    __shared__ PartPool pool;
+    if (threadIdx.x == 0) pool.nparts = pool.nq = 0;   // visible after the barrier below
     const int64_t n = len.get();
     const int64_t nb = (n + (1ll << logk) - 1) >> logk;
     const Coarse g = coarse_geom(nb, cap);
@@ -507,7 +581,7 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
     int nq = 0;   // queued (warp-uniform)
     const int sh = logk + g.lc;
     auto resolve = [&](int take) {
-        resolve_queued<Src, CON, VEC>(src, n, logk, T, nb, cs, g, L, R, BP, out, my + nq - take, take, M1);
+        resolve_queued<Src, CON, VEC>(src, n, logk, T, nb, cs, g, L, R, BP, out, my + nq - take, take, M1, &pool);
         nq -= take;
     };
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -619,6 +693,7 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
     }
     if (nq > 0) resolve(nq);
     if (RING) cp_async_wait<0>();   // no copy is left in flight (all were empty)
+    drain_pool<Src, VEC>(src, n, M1, &pool, out);
 }
 
 // Launches k_query_two with `smem` bytes of dynamic shared memory (the ring
