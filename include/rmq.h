@@ -339,14 +339,15 @@ rmq_status rmq_rank_endpoints(const uint32_t *pos_sorted, const uint32_t *tag_so
                               int32_t *rank_l, int32_t *rank_r, void *stream);
 
 /* Sec. 3.1 step 1 as the batch path computes it: a bitmap over the
- * positions of A in place of the sort.  BP is uint32[2 * (ceil(n/32) + 1)]:
- * BP[2w] = bit word w (bit b set: position 32w + b is an endpoint of some
- * query), BP[2w + 1] = number of set bits in words 0 .. w-1; the final pair
- * is (0, m).  The set bits in increasing order are P of rmq_rank_endpoints,
- * and the rank of an endpoint p is BP[2(p/32) + 1] + popcount of the bits of
- * word p/32 below p % 32.  *m_dev (device int64) = m.  An invalid query marks
- * position 0 (as the sort's pair (0, 0)) and raises the device error word.
- * BP must be 8-byte aligned; it is cleared by the call. */
+ * positions of A in place of the sort.  With W = ceil(n/32) + 1, BP is
+ * uint32[2W]: BP[w] (w < W) = bit word w (bit b set: position 32w + b is an
+ * endpoint of some query; word W-1 is 0), BP[W + w] = number of set bits in
+ * words 0 .. w-1 (so BP[2W - 1] = m).  The set bits in increasing order are P
+ * of rmq_rank_endpoints, and the rank of an endpoint p is BP[W + p/32] +
+ * popcount of the bits of word p/32 below p % 32.  *m_dev (device int64) = m.
+ * An invalid query marks position 0 (as the sort's pair (0, 0)) and raises
+ * the device error word.  BP must be 4-byte aligned; the call writes all of
+ * it. */
 rmq_status rmq_endpoint_bitmap(const int32_t *l, const int32_t *r, int64_t q, int64_t n,
                                uint32_t *BP, int64_t *m_dev, void *stream);
 

@@ -506,12 +506,12 @@ rmq_status rmq_endpoint_bitmap(const int32_t *l, const int32_t *r, int64_t q, in
                                int64_t *m_dev, void *stream) {
     if (!BP || !m_dev || n <= 0 || n > kMaxN || q < 0 || q > kMaxQ) return RMQ_ERR_INVALID_ARG;
     if (q > 0 && (!l || !r)) return RMQ_ERR_INVALID_ARG;
-    if (reinterpret_cast<uintptr_t>(BP) & 7) return RMQ_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(BP) & 3) return RMQ_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
     Workspace ws;
     rmq_status st = ws.alloc(endpoint_bitmap_workspace_bytes(n), s);
     if (st != RMQ_OK) return st;
-    return cuda_status(endpoint_bitmap(l, r, q, n, reinterpret_cast<uint2 *>(BP), m_dev, nullptr, ws.p, s));
+    return cuda_status(endpoint_bitmap(l, r, q, n, BP, BP + bitmap_entries(n), m_dev, nullptr, ws.p, s));
 }
 
 rmq_status rmq_contract(const int32_t *A, int64_t n, const uint32_t *P, const int64_t *m_dev, int64_t m_max,

@@ -331,12 +331,12 @@ __global__ void __launch_bounds__(kT) k_rank_scatter(const uint32_t *__restrict_
 // positions of A (a counting sort of keys drawn from [0, n)): bit p of the
 // bitmap is set when p is an endpoint.  The set bits, in increasing order,
 // are exactly the distinct sorted positions P of step 1, and the rank of an
-// endpoint is the number of set bits below it.  BP holds one uint2 per 32
-// positions (x = bit word, y = set bits in all earlier words), plus a final
-// entry (x = 0, y = m) so that every rank lookup stays in bounds.
+// endpoint is the number of set bits below it.  BW holds one bit word per 32
+// positions and BC, for each word, the set bits in all earlier words; a final
+// entry (word 0, count m) keeps every rank lookup in bounds.
 __device__ __forceinline__ void mark_bit(uint32_t *bw, uint32_t p) {
-    // fire-and-forget OR into word p / 32 (the .x field of its uint2)
-    asm volatile("red.global.or.b32 [%0], %1;" ::"l"(bw + 2 * (p >> 5)), "r"(1u << (p & 31)) : "memory");
+    // fire-and-forget OR into word p / 32
+    asm volatile("red.global.or.b32 [%0], %1;" ::"l"(bw + (p >> 5)), "r"(1u << (p & 31)) : "memory");
 }
 
 // Marks both ends of every query.  An invalid query marks position 0 (the
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(kT) k_mark_endpoints(const int32_t *__restrict
         const bool crowded = __any_sync(0xffffffffu, __shfl_xor_sync(0xffffffffu, w, 1) == w);
         if (!has) return;
         const uint32_t bit = 1u << (p & 31);
-        if (crowded && (__ldcg(bw + 2 * (size_t)w) & bit)) return;
+        if (crowded && (__ldcg(bw + w) & bit)) return;
         mark_bit(bw, p);
     };
     auto mark = [&](bool has, int32_t l, int32_t r) {
@@ -396,10 +396,10 @@ __global__ void __launch_bounds__(kT) k_mark_positions(const uint32_t *__restric
         mark_bit(bw, P[j]);
 }
 
-// Rank counts: the exclusive scan of popc(BP[w].x) into BP[w].y, over the
+// Rank counts: the exclusive scan of popc(BW[w]) into BC[w], over the
 // nbp = ceil(n / 32) + 1 entries, in tiles of kTile entries (warp w of a CTA
 // owns 512 consecutive entries, lane-interleaved rows of 32).
-__global__ void __launch_bounds__(kT) k_bits_partial(const uint2 *__restrict__ BP, int64_t nbp,
+__global__ void __launch_bounds__(kT) k_bits_partial(const uint32_t *__restrict__ BW, int64_t nbp,
                                                      uint32_t *__restrict__ partial) {
     pdl_wait();
     __shared__ uint32_t wsum[kT / 32];
@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(kT) k_bits_partial(const uint2 *__restrict__ B
 #pragma unroll
     for (int i = 0; i < kIPT; ++i) {
         const int64_t e = base + i * kT + threadIdx.x;
-        if (e < nbp) c += __popc(BP[e].x);
+        if (e < nbp) c += __popc(BW[e]);
     }
     uint32_t total;
     block_excl_scan(c, wsum, total);
@@ -435,7 +435,8 @@ __device__ __forceinline__ int stage_pos(int i) {
 // block 0 stores m.
 // bs, nbk: bucket_shift(n), bucket_count(n) (word indices are below 2^26, so
 // the per-word arithmetic is 32-bit).
-__global__ void __launch_bounds__(kT, 6) k_bits_final(uint2 *__restrict__ BP, int64_t nbp,
+__global__ void __launch_bounds__(kT, 6) k_bits_final(const uint32_t *__restrict__ BW, uint32_t *__restrict__ BC,
+                                                      int64_t nbp,
                                                       const uint32_t *__restrict__ partial, int64_t *m_dev,
                                                       int64_t ntA, uint64_t *__restrict__ AQ, int logk_q,
                                                       uint32_t *__restrict__ CP, uint16_t *__restrict__ CB, int bs,
@@ -451,7 +452,7 @@ __global__ void __launch_bounds__(kT, 6) k_bits_final(uint2 *__restrict__ BP, in
 #pragma unroll
     for (int i = 0; i < kIPT; ++i) {
         const int64_t e = base + i * 32 + lane;
-        words[i] = e < nbp ? BP[e].x : 0u;
+        words[i] = e < nbp ? BW[e] : 0u;
     }
     uint32_t before = 0, all = 0;
     for (int64_t i = threadIdx.x; i < gridDim.x; i += kT) {
@@ -520,7 +521,7 @@ __global__ void __launch_bounds__(kT, 6) k_bits_final(uint2 *__restrict__ BP, in
         const uint32_t ex = sx[stage_pos(i * 32 + lane)], word = st[stage_pos(i * 32 + lane)];
         const uint32_t e = ebase + (uint32_t)(i * 32 + lane);
         if (!all_in && (int64_t)e >= nbp) continue;
-        BP[e] = make_uint2(word, ex);
+        BC[e] = ex;
         if (lane == 0 && (int64_t)(e >> 5) < ntA) {   // the first word of a contraction tile
             const int64_t sg = (int64_t)ex - 1;
             if (sg >= 0 && sg <= m - 2) AQ[sg] = KEY_MAX;
@@ -557,7 +558,7 @@ __device__ __forceinline__ void emit_atomic(uint64_t *H, int64_t s, uint64_t v) 
 
 // One warp per tile of kATile = 1024 cells; lane L owns the 32 consecutive
 // cells [32L, 32L + 32) of the tile, whose endpoint marks are exactly the
-// bitmap word BP[32t + L].x, and BP[32t + L].y - 1 is the segment open at the
+// bitmap word BW[32t + L], and BC[32t + L] - 1 is the segment open at the
 // lane's first cell.  Segment j covers A[P_j .. P_{j+1}]; a marked cell P_j
 // closes segment j-1 (it is its last cell) and opens segment j.  The tile is
 // read with coalesced 16-byte loads and handed to the lanes through shared
@@ -574,7 +575,8 @@ __device__ __forceinline__ int swz(int x) { return (x & ~7) | ((x & 7) ^ ((x >> 
 constexpr int kContractSmem = (kT / 32) * kATile * 8;   // per warp: the tile, then its slots
 
 template <bool VEC>
-__global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const uint2 *__restrict__ BP,
+__global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const uint32_t *__restrict__ BW,
+                                                 const uint32_t *__restrict__ BC,
                                                  const int64_t *m_dev, int64_t ntA, uint64_t *__restrict__ H) {
     pdl_wait();
     extern __shared__ uint64_t csmem[];
@@ -586,11 +588,12 @@ __global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const ui
     const int32_t m = (int32_t)*m_dev;       // m <= n < 2^31: segment numbers fit in 32 bits
     const int64_t nfull = n / kATile;        // tiles wholly inside [0, n)
     const int64_t nv = n / 4;                // vectors wholly inside [0, n)
-    const int64_t nw = (n + 31) >> 5;        // bitmap words; BP[nw] is the end entry
+    const int64_t nw = (n + 31) >> 5;        // bitmap words; entry nw is the end entry
     // a tile's cells and its bitmap words, requested together
     auto load_tile = [&](int64_t t, int4 (&v)[8], uint2 &e) {
         const int64_t wi = t * 32 + lane;
-        e = __ldg(BP + (wi < nw ? wi : nw));
+        const int64_t ei = wi < nw ? wi : nw;
+        e = make_uint2(__ldg(BW + ei), __ldg(BC + ei));
         const int64_t ts = t * kATile;
         if (VEC && t < nfull) {
             const int4 *tp = reinterpret_cast<const int4 *>(src.a) + ts / 4 + lane;
@@ -782,15 +785,16 @@ int64_t bitmap_entries(int64_t n) { return cdiv(n, 32) + 1; }
 
 namespace {
 
-// BP[w].y = set bits in words before w, *m_dev = all set bits; A_Q entries
+// BC[w] = set bits in words before w, *m_dev = all set bits; A_Q entries
 // that the contraction combines with atomics are set to KEY_MAX (AQ may be
 // null when no contraction follows).  aux: scan_aux_words(tiles) words.
-cudaError_t bitmap_ranks(uint2 *BP, int64_t n, int64_t *m_dev, uint64_t *AQ, uint32_t *aux, cudaStream_t s,
+cudaError_t bitmap_ranks(const uint32_t *BW, uint32_t *BC, int64_t n, int64_t *m_dev, uint64_t *AQ, uint32_t *aux,
+                         cudaStream_t s,
                          int logk_q = 0, uint32_t *CP = nullptr, uint16_t *CB = nullptr) {
     const int64_t nbp = bitmap_entries(n);
     const int64_t tiles = cdiv(nbp, kTile);
-    launch_pdl(k_bits_partial, (unsigned)tiles, kT, 0, s, BP, nbp, aux);
-    launch_pdl(k_bits_final, (unsigned)tiles, kT, 0, s, BP, nbp, aux, m_dev, AQ ? cdiv(n, kATile) : 0, AQ, logk_q, CP, CB,
+    launch_pdl(k_bits_partial, (unsigned)tiles, kT, 0, s, BW, nbp, aux);
+    launch_pdl(k_bits_final, (unsigned)tiles, kT, 0, s, BW, BC, nbp, aux, m_dev, AQ ? cdiv(n, kATile) : 0, AQ, logk_q, CP, CB,
                bucket_shift(n), bucket_count(n));
     note_launches(2);
     return cudaGetLastError();
@@ -798,7 +802,8 @@ cudaError_t bitmap_ranks(uint2 *BP, int64_t n, int64_t *m_dev, uint64_t *AQ, uin
 
 size_t bitmap_aux_bytes(int64_t n) { return align256(cdiv(bitmap_entries(n), kTile) * 4); }
 
-cudaError_t contract_bitmap(const int32_t *A, int64_t n, const uint2 *BP, const int64_t *m_dev, uint64_t *AQ,
+cudaError_t contract_bitmap(const int32_t *A, int64_t n, const uint32_t *BW, const uint32_t *BC,
+                            const int64_t *m_dev, uint64_t *AQ,
                             cudaStream_t s) {
     const int64_t ntA = cdiv(n, kATile);
     const DevInfo di = dev_info();
@@ -816,9 +821,9 @@ cudaError_t contract_bitmap(const int32_t *A, int64_t n, const uint2 *BP, const 
     const int per_sm = (di.device >= 0 && di.device < 64) ? occ[di.device] : 1;   // one resident wave
     const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(ntA, kT / 32), (int64_t)di.sms * per_sm));
     if ((reinterpret_cast<uintptr_t>(A) & 15) == 0)
-        launch_pdl(k_contract<true>, (unsigned)ctas, kT, kContractSmem, s, src, n, BP, m_dev, ntA, AQ);
+        launch_pdl(k_contract<true>, (unsigned)ctas, kT, kContractSmem, s, src, n, BW, BC, m_dev, ntA, AQ);
     else
-        launch_pdl(k_contract<false>, (unsigned)ctas, kT, kContractSmem, s, src, n, BP, m_dev, ntA, AQ);
+        launch_pdl(k_contract<false>, (unsigned)ctas, kT, kContractSmem, s, src, n, BW, BC, m_dev, ntA, AQ);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -827,42 +832,44 @@ cudaError_t contract_bitmap(const int32_t *A, int64_t n, const uint2 *BP, const 
 
 size_t endpoint_bitmap_workspace_bytes(int64_t n) { return bitmap_aux_bytes(n); }
 
-cudaError_t endpoint_bitmap(const int32_t *l, const int32_t *r, int64_t q, int64_t n, uint2 *BP, int64_t *m_dev,
-                            uint64_t *AQ, void *ws, cudaStream_t s, Stages *st, int logk_q, uint32_t *CP,
-                            uint16_t *CB) {
+cudaError_t endpoint_bitmap(const int32_t *l, const int32_t *r, int64_t q, int64_t n, uint32_t *BW, uint32_t *BC,
+                            int64_t *m_dev, uint64_t *AQ, void *ws, cudaStream_t s, Stages *st, int logk_q,
+                            uint32_t *CP, uint16_t *CB) {
     unsigned *err = err_word_ptr();
     if (!err) return cudaErrorUnknown;
-    cudaError_t e = cudaMemsetAsync(BP, 0, (size_t)bitmap_entries(n) * sizeof(uint2), s);
+    // only the bit words need clearing: k_bits_final writes every count
+    cudaError_t e = cudaMemsetAsync(BW, 0, (size_t)bitmap_entries(n) * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     const DevInfo di = dev_info();
     const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(cdiv(q, 4), kT), (int64_t)di.sms * 8));
-    launch_pdl(k_mark_endpoints, (unsigned)ctas, kT, 0, s, l, r, q, n, reinterpret_cast<uint32_t *>(BP), err);
+    launch_pdl(k_mark_endpoints, (unsigned)ctas, kT, 0, s, l, r, q, n, BW, err);
     note_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (st) st->mark(s);
-    return bitmap_ranks(BP, n, m_dev, AQ, static_cast<uint32_t *>(ws), s, logk_q, CP, CB);
+    return bitmap_ranks(BW, BC, n, m_dev, AQ, static_cast<uint32_t *>(ws), s, logk_q, CP, CB);
 }
 
 size_t contract_workspace_bytes(int64_t n) {
-    return align256(bitmap_entries(n) * sizeof(uint2)) + align256(8) + bitmap_aux_bytes(n);
+    return 2 * align256(bitmap_entries(n) * sizeof(uint32_t)) + align256(8) + bitmap_aux_bytes(n);
 }
 
 cudaError_t contract(const int32_t *A, int64_t n, const uint32_t *P, const int64_t *m_dev, int64_t m_max,
                      uint64_t *AQ, void *ws, cudaStream_t s) {
     // P -> bitmap -> ranks, then the same contraction as the batch path
     Carver c{static_cast<char *>(ws)};
-    uint2 *BP = c.take<uint2>(bitmap_entries(n));
+    uint32_t *BW = c.take<uint32_t>(bitmap_entries(n));
+    uint32_t *BC = c.take<uint32_t>(bitmap_entries(n));
     int64_t *m2 = c.take<int64_t>(1);
     uint32_t *aux = reinterpret_cast<uint32_t *>(c.p + c.used);
-    cudaError_t e = cudaMemsetAsync(BP, 0, (size_t)bitmap_entries(n) * sizeof(uint2), s);
+    cudaError_t e = cudaMemsetAsync(BW, 0, (size_t)bitmap_entries(n) * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     const DevInfo di = dev_info();
     const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(std::max<int64_t>(m_max, 1), kT), (int64_t)di.sms * 8));
-    k_mark_positions<<<(unsigned)ctas, kT, 0, s>>>(P, m_dev, reinterpret_cast<uint32_t *>(BP));
+    k_mark_positions<<<(unsigned)ctas, kT, 0, s>>>(P, m_dev, BW);
     note_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = bitmap_ranks(BP, n, m2, AQ, aux, s)) != cudaSuccess) return e;
-    return contract_bitmap(A, n, BP, m2, AQ, s);
+    if ((e = bitmap_ranks(BW, BC, n, m2, AQ, aux, s)) != cudaSuccess) return e;
+    return contract_bitmap(A, n, BW, BC, m2, AQ, s);
 }
 
 size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con) {
@@ -870,7 +877,7 @@ size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con) {
     const int64_t nbq = cdiv(mq_max, 1ll << logk_con);
     const int64_t lv = coarse_geom(nbq, kCoarseCapCon).lc + 1;
     size_t b = 0;
-    b += align256(bitmap_entries(n) * sizeof(uint2));  // endpoint bitmap with rank counts
+    b += 2 * align256(bitmap_entries(n) * sizeof(uint32_t));  // endpoint bitmap words, rank counts
     b += align256(8);                                 // m
     b += align256(mq_max * 8);                        // A_Q
     b += align256(nbq * lv * 8);                      // table over A_Q
@@ -885,7 +892,8 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     const int64_t nbq = cdiv(mq_max, 1ll << logk_con);
     const int64_t lv = coarse_geom(nbq, kCoarseCapCon).lc + 1;
     Carver c{static_cast<char *>(ws)};
-    uint2 *BP = c.take<uint2>(bitmap_entries(n));
+    uint32_t *BW = c.take<uint32_t>(bitmap_entries(n));
+    uint32_t *BC = c.take<uint32_t>(bitmap_entries(n));
     int64_t *m_dev = c.take<int64_t>(1);
     uint64_t *AQ = c.take<uint64_t>(mq_max);
     uint64_t *T = c.take<uint64_t>(nbq * lv);
@@ -898,9 +906,9 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     const DevInfo di = dev_info();
     st->mark(s);
     // step 1: the endpoint bitmap (marks), then the rank counts
-    if ((e = endpoint_bitmap(l, r, q, n, BP, m_dev, AQ, aux, s, st, logk_con, CP, CB)) != cudaSuccess) return e;
+    if ((e = endpoint_bitmap(l, r, q, n, BW, BC, m_dev, AQ, aux, s, st, logk_con, CP, CB)) != cudaSuccess) return e;
     st->mark(s);
-    if ((e = contract_bitmap(A, n, BP, m_dev, AQ, s)) != cudaSuccess) return e;             // step 2
+    if ((e = contract_bitmap(A, n, BW, BC, m_dev, AQ, s)) != cudaSuccess) return e;         // step 2
     st->mark(s);
     const Len lenq{0, m_dev};
     if ((e = launch_block_minima_u64(AQ, lenq, mq_max, logk_con, T, s)) != cudaSuccess) return e;         // step 3
@@ -916,11 +924,11 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     if (vecq)
         e = launch_query_two<SrcU64, true, true, true>(di.device, (unsigned)qctas,
                                                        smem + query_ring_bytes<true, true>(), s, src, lenq, logk_con,
-                                                       kCoarseCapCon, T, nullptr, l, r, BP, CP, CB, nullptr, n,
+                                                       kCoarseCapCon, T, nullptr, l, r, BW, BC, CP, CB, nullptr, n,
                                                        out, q, nullptr);
     else
         e = launch_query_two<SrcU64, true, false, true>(di.device, (unsigned)qctas, smem, s, src, lenq, logk_con,
-                                                        kCoarseCapCon, T, nullptr, l, r, BP, CP, CB, nullptr, n,
+                                                        kCoarseCapCon, T, nullptr, l, r, BW, BC, CP, CB, nullptr, n,
                                                         out, q, nullptr);
     if (e != cudaSuccess) return e;
     note_launches(1);

@@ -390,11 +390,11 @@ __device__ __forceinline__ bool coarse_span_min(const uint64_t *cs, const Coarse
 
 // Rank of a marked position p in the endpoint bitmap: the number of distinct
 // endpoint positions below p, i.e. the index of p in the sorted list P.
-// BP[w].x is bit word w (bit b set: position 32w + b is an endpoint) and
-// BP[w].y the number of set bits in the words before w.
-__device__ __forceinline__ uint32_t bitmap_rank(const uint2 *__restrict__ BP, uint32_t p) {
-    const uint2 e = __ldg(BP + (p >> 5));
-    return e.y + __popc(e.x & ((1u << (p & 31)) - 1u));
+// BW[w] is bit word w (bit b set: position 32w + b is an endpoint) and BC[w]
+// the number of set bits in the words before w.
+__device__ __forceinline__ uint32_t bitmap_rank(const uint32_t *__restrict__ BW, const uint32_t *__restrict__ BC,
+                                                uint32_t p) {
+    return __ldg(BC + (p >> 5)) + __popc(__ldg(BW + (p >> 5)) & ((1u << (p & 31)) - 1u));
 }
 
 // Coarse block of A_Q holding the A_Q entry that begins at the last mark
@@ -418,7 +418,8 @@ template <class Src, bool CON, bool VEC>
 __device__ __forceinline__ void resolve_queued(const Src src, int64_t n, int logk, const uint64_t *__restrict__ T,
                                             int64_t nb, const uint64_t *cs, const Coarse g,
                                             const int32_t *__restrict__ L, const int32_t *__restrict__ R,
-                                            const uint2 *__restrict__ BP, int32_t *__restrict__ out,
+                                            const uint32_t *__restrict__ BW, const uint32_t *__restrict__ BC,
+                                            int32_t *__restrict__ out,
                                             const uint32_t *q_ids, int take, const uint64_t *M1,
                                             PartPool *pool) {
     const int lane = threadIdx.x & 31;
@@ -431,8 +432,8 @@ __device__ __forceinline__ void resolve_queued(const Src src, int64_t n, int log
     if (has) {
         qid = q_ids[lane];
         const int32_t l = L[qid], r = R[qid];
-        const int64_t lo = CON ? (int64_t)bitmap_rank(BP, (uint32_t)l) : l;
-        const int64_t hi = CON ? (int64_t)bitmap_rank(BP, (uint32_t)r) - 1 : r;
+        const int64_t lo = CON ? (int64_t)bitmap_rank(BW, BC, (uint32_t)l) : l;
+        const int64_t hi = CON ? (int64_t)bitmap_rank(BW, BC, (uint32_t)r) - 1 : r;
         int sub;
         best = resolve_coarse(cs, g, logk, (uint32_t)lo, (uint32_t)hi, (uint32_t)l, (uint32_t)r, sub);
         if (sub == SUB_WHOLE) {
@@ -520,10 +521,10 @@ __device__ __forceinline__ void drain_pool(const Src src, int64_t n, const uint6
 //   plain (CON = false): the source is A; query i covers [l_i, r_i].
 //   contracted (CON = true): the source is A_Q; query i covers
 //     A_Q[a_i .. b_i - 1] with a_i, b_i the ranks of l_i, r_i in the
-//     endpoint bitmap BP; a_i == b_i means l_i == r_i and the answer is l_i.
+//     endpoint bitmap (BW, BC); a_i == b_i means l_i == r_i and the answer is l_i.
 //     Phase A needs only the coarse blocks of a_i and b_i - 1, which the
 //     coarse index (CP, CB) gives from l_i and r_i - 1; the ranks themselves
-//     are looked up in BP for the queries left to phase B.
+//     are looked up in the bitmap for the queries left to phase B.
 //   cap: the coarse geometry of the table (coarse_geom(nb, cap)).
 // Dynamic shared memory: for the plain form with VECQ, each warp's ring of
 // the l, r of its next kQueryRing steps (query_ring_bytes in all), then the
@@ -543,7 +544,8 @@ __global__ void __launch_bounds__(kQueryThreads, kQueryCtasPerSm)
 k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
                                                     const uint64_t *__restrict__ Cs,
                                                     const int32_t *__restrict__ L, const int32_t *__restrict__ R,
-                                                    const uint2 *__restrict__ BP, const uint32_t *__restrict__ CP,
+                                                    const uint32_t *__restrict__ BW, const uint32_t *__restrict__ BC,
+                                                    const uint32_t *__restrict__ CP,
                                                     const uint16_t *__restrict__ CB, const uint64_t *__restrict__ M1,
                                                     int64_t n_a, int32_t *__restrict__ out, int64_t q,
                                                     unsigned *err) {
@@ -581,7 +583,8 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
     int nq = 0;   // queued (warp-uniform)
     const int sh = logk + g.lc;
     auto resolve = [&](int take) {
-        resolve_queued<Src, CON, VEC>(src, n, logk, T, nb, cs, g, L, R, BP, out, my + nq - take, take, M1, &pool);
+        resolve_queued<Src, CON, VEC>(src, n, logk, T, nb, cs, g, L, R, BW, BC, out, my + nq - take, take, M1,
+                                      &pool);
         nq -= take;
     };
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;

@@ -27,7 +27,8 @@ cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint
 #define RMQ_LQ2(VQ, V)                                                                                    \
     e = launch_query_two<SrcI32, false, VQ, V>(di.device, (unsigned)ctas,                                \
                                                query_ring_bytes<false, VQ>() + cs_bytes, s, src, len, logk, \
-                                               cap, T, Cs, l, r, nullptr, nullptr, nullptr, M1, n, out, q, err)
+                                               cap, T, Cs, l, r, nullptr, nullptr, nullptr, nullptr, M1, n, out, q, \
+                                               err)
     if (vecq && vec) RMQ_LQ2(true, true);
     else if (vecq) RMQ_LQ2(true, false);
     else if (vec) RMQ_LQ2(false, true);

@@ -320,14 +320,15 @@ cudaError_t rank_endpoints(const uint32_t *pos, const uint32_t *tag, int64_t q, 
 size_t rank_workspace_bytes(int64_t q);
 cudaError_t contract(const int32_t *A, int64_t n, const uint32_t *P, const int64_t *m_dev, int64_t m_max,
                      uint64_t *AQ, void *ws, cudaStream_t s);
-// Endpoint bitmap of the batch path: BP (bitmap_entries(n) uint2), *m_dev =
-// number of distinct endpoint positions; AQ entries combined by the
-// contraction are reset when AQ is given.
+// Endpoint bitmap of the batch path: BW, the bitmap_entries(n) bit words
+// (the last one 0), and BC, the set bits before each word (BC[last] = m);
+// *m_dev = m, the number of distinct endpoint positions; AQ entries combined
+// by the contraction are reset when AQ is given.
 int64_t bitmap_entries(int64_t n);
 size_t endpoint_bitmap_workspace_bytes(int64_t n);
-cudaError_t endpoint_bitmap(const int32_t *l, const int32_t *r, int64_t q, int64_t n, uint2 *BP, int64_t *m_dev,
-                            uint64_t *AQ, void *ws, cudaStream_t s, Stages *st = nullptr, int logk_q = 0,
-                            uint32_t *CP = nullptr, uint16_t *CB = nullptr);
+cudaError_t endpoint_bitmap(const int32_t *l, const int32_t *r, int64_t q, int64_t n, uint32_t *BW, uint32_t *BC,
+                            int64_t *m_dev, uint64_t *AQ, void *ws, cudaStream_t s, Stages *st = nullptr,
+                            int logk_q = 0, uint32_t *CP = nullptr, uint16_t *CB = nullptr);
 size_t contract_workspace_bytes(int64_t n);
 
 }  // namespace rmq

@@ -427,8 +427,9 @@ def rmq_rank_endpoints(pos_sorted, tag_sorted, q, P_out, m_dev, rank_l, rank_r, 
 
 
 def rmq_endpoint_bitmap(l, r, n, BP, m_dev, stream=None):
-    """BP: int32/uint32 tensor of 2 * (ceil(n / 32) + 1) words (pairs: bit word,
-    set bits before it); m_dev: one int64 on the device."""
+    """BP: int32/uint32 tensor of 2W words, W = ceil(n / 32) + 1 (the W bit
+    words, then the W counts of set bits before each word); m_dev: one int64
+    on the device."""
     _check(load().rmq_endpoint_bitmap(_dptr(l, _i32t(), "l"), _dptr(r, _i32t(), "r"), l.numel(), int(n),
                                       _dptr(BP, None, "BP"), _dptr(m_dev, None, "m_dev"), _stream(stream, l)))
 

@@ -253,10 +253,12 @@ def test_a5_rank_endpoints(R, n, q):
 
 
 def bitmap_ranks_host(BP, pos):
-    """Rank of each position from the (word, count) pairs: count + popcount
-    of the word's bits below the position."""
-    w = BP[0::2].view(np.uint32)
-    c = BP[1::2].view(np.uint32).astype(np.int64)
+    """Rank of each position from the bit words (first half of BP) and the
+    counts (second half): count + popcount of the word's bits below the
+    position."""
+    half = len(BP) // 2
+    w = BP[:half].view(np.uint32)
+    c = BP[half:].view(np.uint32).astype(np.int64)
     idx = pos >> 5
     below = w[idx] & ((np.uint32(1) << (pos & 31).astype(np.uint32)) - np.uint32(1))
     pc = np.array([bin(int(x)).count("1") for x in below], dtype=np.int64)
@@ -280,9 +282,9 @@ def test_a4_a5_endpoint_bitmap(R, n, q):
     bp = BP.cpu().numpy()
     wp, wt = oracle.sort_endpoints(l, r)
     P_want, ra_want, rb_want = oracle.rank_endpoints(wp, wt, q)
-    bits = np.unpackbits(np.ascontiguousarray(bp[0::2]).view(np.uint8), bitorder="little")
+    bits = np.unpackbits(np.ascontiguousarray(bp[:nbp]).view(np.uint8), bitorder="little")
     assert np.array_equal(np.nonzero(bits)[0].astype(np.uint32), P_want)
-    assert int(m.item()) == len(P_want) and bp[-1] == len(P_want) and bp[-2] == 0
+    assert int(m.item()) == len(P_want) and bp[-1] == len(P_want) and bp[nbp - 1] == 0
     assert np.array_equal(bitmap_ranks_host(bp, l.astype(np.int64)), ra_want)
     assert np.array_equal(bitmap_ranks_host(bp, r.astype(np.int64)), rb_want)
 
@@ -305,7 +307,7 @@ def test_a4_endpoint_bitmap_clustered_endpoints(R):
     bp = BP.cpu().numpy()
     wp, wt = oracle.sort_endpoints(l, r)
     P_want, ra_want, rb_want = oracle.rank_endpoints(wp, wt, q)
-    bits = np.unpackbits(np.ascontiguousarray(bp[0::2]).view(np.uint8), bitorder="little")
+    bits = np.unpackbits(np.ascontiguousarray(bp[:nbp]).view(np.uint8), bitorder="little")
     assert np.array_equal(np.nonzero(bits)[0].astype(np.uint32), P_want)
     assert int(m.item()) == len(P_want)
     assert np.array_equal(bitmap_ranks_host(bp, l.astype(np.int64)), ra_want)
@@ -329,7 +331,7 @@ def test_a4_endpoint_bitmap_invalid_queries_mark_zero(R):
     wl[[5, 9]] = 0
     wr[[5, 9]] = 0
     P_want = np.unique(np.concatenate([wl, wr])).astype(np.uint32)
-    bits = np.unpackbits(np.ascontiguousarray(BP.cpu().numpy()[0::2]).view(np.uint8), bitorder="little")
+    bits = np.unpackbits(np.ascontiguousarray(BP.cpu().numpy()[:nbp]).view(np.uint8), bitorder="little")
     assert np.array_equal(np.nonzero(bits)[0].astype(np.uint32), P_want)
     assert int(m.item()) == len(P_want)
 
