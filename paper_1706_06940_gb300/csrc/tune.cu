@@ -75,6 +75,11 @@ rmq_status rmq_autotune(const int32_t *A, int64_t n, const int32_t *l, const int
         cudaGetLastError();
         flush = nullptr;
     }
+    if (flush && cudaMemsetAsync(flush, 0, flush_bytes, s) != cudaSuccess) {   // no read of unset memory
+        cudaGetLastError();
+        cudaFreeAsync(flush, s);
+        flush = nullptr;
+    }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         if (flush) cudaFreeAsync(flush, s);
@@ -93,6 +98,7 @@ rmq_status rmq_autotune(const int32_t *A, int64_t n, const int32_t *l, const int
                     k_l2_evict<<<(unsigned)(dev_info().sms * 8), 256, 0, s>>>(static_cast<const int4 *>(flush),
                                                                              (int64_t)(flush_bytes / 16),
                                                                              static_cast<int4 *>(flush));
+                    note_launches(1);
                 }
                 cudaEventRecord(e0, s);
                 st = rmq_batch_ex(A, n, l, r, q, out, &o, stream);
