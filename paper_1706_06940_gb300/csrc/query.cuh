@@ -565,35 +565,15 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
     __shared__ uint32_t queue[kQueryThreads / 32][kQueue];
     __shared__ PartPool pool;
     if (threadIdx.x == 0) pool.nparts = pool.nq = 0;   // visible after the barrier below
-    const int64_t n = len.get();
-    const int64_t nb = (n + (1ll << logk) - 1) >> logk;
-    const Coarse g = coarse_geom(nb, cap);
-    // the coarse table: copied when the caller keeps one, else built here
-    if (Cs) load_coarse(cs, Cs, (int)g.size());
-    else if (nb > 0) build_coarse(cs, T, nb, g);
-    const int bs = CON ? bucket_shift(n_a) : 0;
-    if (CON && nb > 0) {
-        for (int i = threadIdx.x; i < g.nbc; i += blockDim.x) cp[i] = __ldg(CP + i);
-        const int nbk = (int)bucket_count(n_a);
-        for (int i = threadIdx.x; i <= nbk; i += blockDim.x) cb[i] = __ldg(CB + i);
-    }
-    __syncthreads();
     const int lane = threadIdx.x & 31;
-    uint32_t *my = queue[threadIdx.x >> 5];
-    int nq = 0;   // queued (warp-uniform)
-    const int sh = logk + g.lc;
-    auto resolve = [&](int take) {
-        resolve_queued<Src, CON, VEC>(src, n, logk, T, nb, cs, g, L, R, BW, BC, out, my + nq - take, take, M1,
-                                      &pool);
-        nq -= take;
-    };
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     // RING: the l, r of the warp's next kRing steps are in flight at any
     // time: each lane copies its 16 bytes of l and of r into its slots of the
     // warp's ring (one commit group per step, empty past the end of the
     // batch).  Otherwise the next step's l, r are loaded into registers
-    // before the current step is processed.
+    // before the current step is processed.  The first loads are issued
+    // before the coarse table is built, so that they overlap its build.
     const int64_t stride = nwarps * 128;
     int4 *wring = ring + (threadIdx.x >> 5) * (kRing * 64);
     const uint32_t ring_sh = RING ? (uint32_t)__cvta_generic_to_shared(wring) : 0u;
@@ -617,6 +597,29 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
     } else {
         fetch(warp * 128 + lane * 4);
     }
+    const int64_t n = len.get();
+    const int64_t nb = (n + (1ll << logk) - 1) >> logk;
+    const Coarse g = coarse_geom(nb, cap);
+    // the contracted form's coarse index (read before the table is built,
+    // whose barriers it does not need)
+    const int bs = CON ? bucket_shift(n_a) : 0;
+    if (CON && nb > 0) {
+        for (int i = threadIdx.x; i < g.nbc; i += blockDim.x) cp[i] = __ldg(CP + i);
+        const int nbk = (int)bucket_count(n_a);
+        for (int i = threadIdx.x; i <= nbk; i += blockDim.x) cb[i] = __ldg(CB + i);
+    }
+    // the coarse table: copied when the caller keeps one, else built here
+    if (Cs) load_coarse(cs, Cs, (int)g.size());
+    else if (nb > 0) build_coarse(cs, T, nb, g);
+    __syncthreads();
+    uint32_t *my = queue[threadIdx.x >> 5];
+    int nq = 0;   // queued (warp-uniform)
+    const int sh = logk + g.lc;
+    auto resolve = [&](int take) {
+        resolve_queued<Src, CON, VEC>(src, n, logk, T, nb, cs, g, L, R, BW, BC, out, my + nq - take, take, M1,
+                                      &pool);
+        nq -= take;
+    };
     int slot = 0;
     const int32_t na = (int32_t)n_a;
     for (int64_t wb = warp * 128; wb < q; wb += stride) {
