@@ -126,6 +126,17 @@ def test_a3_a7_short_and_tie_heavy(R, hi):
     check(R, A, l, r, ks=(32, 512, 4096), kcons=(32, 512))
 
 
+@pytest.mark.parametrize("hi", [2**31, 50])
+def test_part_pool_full_and_not_full(R, hi):
+    """2,000 short queries run in one CTA of the query kernel, and most of them
+    leave edge parts: the first parts go to the CTA's pool (256 at most) and
+    are drained after phase A, the rest are drained at once by their warps."""
+    n = 1_000_000
+    A = W.uniform_array(n, 51, 0, hi)
+    l, r = W.log_width_queries(n, 2_000, 52, 100, 3_000)
+    check(R, A, l, r, ks=(512, 1024), kcons=(256,))
+
+
 def test_unaligned_pointers(R):
     n = 50_003
     A = W.uniform_array(n, 41, 0, 50)
