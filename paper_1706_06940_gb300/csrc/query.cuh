@@ -399,10 +399,11 @@ __device__ __forceinline__ uint32_t bitmap_rank(const uint32_t *__restrict__ BW,
 
 // Coarse block of A_Q holding the A_Q entry that begins at the last mark
 // <= p (p >= P_0): the last j with CP[j] <= p, searched between the bucket
-// bounds CB[p >> bs] and CB[(p >> bs) + 1] (usually equal or adjacent).
-__device__ __forceinline__ uint32_t coarse_of(const uint32_t *cp, const uint16_t *cb, int bs, uint32_t p) {
-    const uint32_t i = p >> bs;
-    uint32_t lo = cb[i], hi = cb[i + 1];
+// bounds CB[p >> bs] and CB[(p >> bs) + 1] (usually equal or adjacent),
+// which cbp[i] holds as one word (low and high 16 bits).
+__device__ __forceinline__ uint32_t coarse_of(const uint32_t *cp, const uint32_t *cbp, int bs, uint32_t p) {
+    const uint32_t pr = cbp[p >> bs];
+    uint32_t lo = pr & 0xffffu, hi = pr >> 16;
     while (lo < hi) {
         const uint32_t mid = (lo + hi + 1) >> 1;
         if (cp[mid] <= p) lo = mid;
@@ -561,7 +562,7 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
     int4 *ring = reinterpret_cast<int4 *>(query_dyn_smem);
     uint64_t *cs = query_dyn_smem + query_ring_bytes<CON, VECQ>() / sizeof(uint64_t);
     __shared__ uint32_t cp[CON ? kCoarseBlocksMax : 1];
-    __shared__ uint16_t cb[CON ? kBucketsMax : 1];
+    __shared__ uint32_t cbp[CON ? kBucketsMax : 1];   // bucket bounds (CB[i], CB[i + 1])
     __shared__ uint32_t queue[kQueryThreads / 32][kQueue];
     __shared__ PartPool pool;
     if (threadIdx.x == 0) pool.nparts = pool.nq = 0;   // visible after the barrier below
@@ -606,7 +607,8 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
     if (CON && nb > 0) {
         for (int i = threadIdx.x; i < g.nbc; i += blockDim.x) cp[i] = __ldg(CP + i);
         const int nbk = (int)bucket_count(n_a);
-        for (int i = threadIdx.x; i <= nbk; i += blockDim.x) cb[i] = __ldg(CB + i);
+        for (int i = threadIdx.x; i < nbk; i += blockDim.x)
+            cbp[i] = (uint32_t)__ldg(CB + i) | ((uint32_t)__ldg(CB + i + 1) << 16);
     }
     // the coarse table: copied when the caller keeps one, else built here
     if (Cs) load_coarse(cs, Cs, (int)g.size());
@@ -659,8 +661,8 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
             const bool use = ok && !single;
             uint32_t BL, BR;
             if (CON) {
-                BL = use ? coarse_of(cp, cb, bs, (uint32_t)lq[i]) : 0u;
-                BR = use ? coarse_of(cp, cb, bs, (uint32_t)rq[i] - 1u) : 0u;
+                BL = use ? coarse_of(cp, cbp, bs, (uint32_t)lq[i]) : 0u;
+                BR = use ? coarse_of(cp, cbp, bs, (uint32_t)rq[i] - 1u) : 0u;
             } else {
                 BL = use ? (uint32_t)lq[i] >> sh : 0u;
                 BR = use ? (uint32_t)rq[i] >> sh : 0u;
