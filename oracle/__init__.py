@@ -66,6 +66,12 @@ def _load():
     lib.oracle_contracted_query.restype = None
     lib.oracle_contracted_query.argtypes = [_i32p, _i64, _i32p, _i32p, _i32p, _i32p, _i32p,
                                             _i64, _i32p]
+    lib.oracle_lary_levels.restype = ctypes.c_int
+    lib.oracle_lary_levels.argtypes = [_i64, _i64]
+    lib.oracle_lary_block_table.restype = None
+    lib.oracle_lary_block_table.argtypes = [_i32p, _i64, _i64, _i64, _i32p]
+    lib.oracle_lary_query.restype = None
+    lib.oracle_lary_query.argtypes = [_i32p, _i64, _i64, _i64, _i32p, _i32p, _i32p, _i64, _i32p, _i32p]
     _lib = lib
     return lib
 
@@ -174,3 +180,30 @@ def contracted_pipeline(A, l, r) -> np.ndarray:
     P, ra, rb = rank_endpoints(pos, tag, len(l))
     AQ = contract(A, P)
     return contracted_query(A, AQ, l, r, ra, rb)
+
+
+def lary_levels(nb: int, ell: int) -> int:
+    """floor(log_ell nb) + 1 (0 for nb <= 0 or ell < 2)."""
+    return int(_load().oracle_lary_levels(int(nb), int(ell)))
+
+
+def lary_block_table(A, k: int, ell: int) -> np.ndarray:
+    """[levels, nb] positions of the minimum over ell^t blocks from block j (-1 if absent)."""
+    A = _i32(A)
+    nb = (len(A) + k - 1) // k
+    lv = lary_levels(nb, ell)
+    out = np.empty(max(lv * nb, 1), dtype=np.int32)
+    _load().oracle_lary_block_table(A, len(A), int(k), int(ell), out)
+    return out[: lv * nb].reshape(lv, nb)
+
+
+def lary_query(A, k: int, ell: int, l, r):
+    """Answers through the ell-ary block table (the Sec. 3.1 variant), and
+    the number of table values each query used."""
+    A, l, r = _i32(A), _i32(l), _i32(r)
+    T = np.ascontiguousarray(lary_block_table(A, k, ell).reshape(-1), dtype=np.int32)
+    T = T if len(T) else np.zeros(1, dtype=np.int32)
+    out = np.empty(len(l), dtype=np.int32)
+    used = np.empty(len(l), dtype=np.int32)
+    _load().oracle_lary_query(A, len(A), int(k), int(ell), T, l, r, len(l), out, used)
+    return out, used

@@ -312,3 +312,94 @@ ORACLE_API void oracle_contracted_query(const int32_t *A, int64_t n,
         out[i] = best;
     }
 }
+
+/* The candidate with the smaller value, and of equal values the one more to
+ * the left (candidates in any order). */
+static int32_t lex_min(const int32_t *A, int32_t a, int32_t b)
+{
+    if (A[a] != A[b]) return A[a] < A[b] ? a : b;
+    return a < b ? a : b;
+}
+
+/*
+ * The l-ary generalisation of the block sparse table (Sec. 3.1, the variant
+ * the paper describes but does not implement): level t holds, for each
+ * block B_j, the minimum over the l^t consecutive blocks whose leftmost
+ * block is B_j; levels t = 0 .. floor(log_l nb).  For l = 2 this is the
+ * block sparse table above.
+ */
+ORACLE_API int oracle_lary_levels(int64_t nb, int64_t ell)
+{
+    if (nb <= 0 || ell < 2) return 0;
+    int levels = 1;
+    for (int64_t span = ell; span <= nb; span *= ell) ++levels;
+    return levels;
+}
+
+/*
+ * The l-ary table written as its definition (a direct scan of each span).
+ * T has levels * nb entries, level-major; spans that would end past the
+ * last block are -1.
+ */
+ORACLE_API void oracle_lary_block_table(const int32_t *A, int64_t n, int64_t k, int64_t ell, int32_t *T)
+{
+    int64_t nb = (n + k - 1) / k;
+    int levels = oracle_lary_levels(nb, ell);
+    int64_t span = 1;
+    for (int t = 0; t < levels; ++t, span *= ell) {
+        for (int64_t j = 0; j < nb; ++j) {
+            if (j + span > nb) { T[(int64_t)t * nb + j] = -1; continue; }
+            int64_t lo = j * k, hi = (j + span) * k - 1;
+            if (hi > n - 1) hi = n - 1;
+            T[(int64_t)t * nb + j] = scan_min(A, lo, hi);
+        }
+    }
+}
+
+/*
+ * Queries over the l-ary table, in the steps of Sec. 3.1 step 4 with the
+ * variant's lookup: blocks bl = l / k and br = r / k; a query inside one
+ * block is scanned.  Otherwise the inner span of blocks bl+1 .. br-1, of
+ * length len, is covered by spans of the level t = floor(log_l len), of
+ * l^t blocks each, placed from bl+1 and then one more ending at br-1, so
+ * that at most l table values are compared.  The two end parts are scanned,
+ * and the leftmost minimum of the three parts is the answer.  T comes from
+ * oracle_lary_block_table; lookups[i] (may be NULL) receives the number of
+ * table values used.  Invalid queries answer -1.
+ */
+ORACLE_API void oracle_lary_query(const int32_t *A, int64_t n, int64_t k, int64_t ell, const int32_t *T,
+                                  const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
+                                  int32_t *lookups)
+{
+    int64_t nb = (n + k - 1) / k;
+    for (int64_t i = 0; i < q; ++i) {
+        int32_t used = 0;
+        if (!valid_query(n, l[i], r[i])) {
+            out[i] = -1;
+            if (lookups) lookups[i] = 0;
+            continue;
+        }
+        int64_t bl = l[i] / k, br = r[i] / k;
+        if (bl == br) {
+            out[i] = scan_min(A, l[i], r[i]);
+            if (lookups) lookups[i] = 0;
+            continue;
+        }
+        int32_t best = scan_min(A, l[i], (bl + 1) * k - 1);   /* left end part */
+        if (br - bl >= 2) {
+            int64_t a = bl + 1, b = br - 1, len = b - a + 1;
+            int t = 0;
+            int64_t span = 1;
+            while (span * ell <= len) { span *= ell; ++t; }
+            for (int64_t s = a;; s += span) {
+                int64_t start = s + span - 1 <= b ? s : b - span + 1;   /* the last one ends at b */
+                best = lex_min(A, best, T[(int64_t)t * nb + start]);
+                ++used;
+                if (start + span - 1 >= b) break;
+            }
+        }
+        best = lex_min(A, best, scan_min(A, br * k, r[i]));   /* right end part */
+        out[i] = best;
+        if (lookups) lookups[i] = used;
+    }
+}

@@ -235,6 +235,80 @@ def test_table2_level_count_reproduces_paper():
             assert abs(pct - float(printed)) <= 0.005 + 1e-9, (k, n, pct, printed)
 
 
+# ---------------------------------------------------------------- l-ary block table (Sec. 3.1 variant)
+
+@pytest.mark.parametrize("n,k,ell,hi", [(1, 1, 2, 9), (100, 1, 3, 4), (32 * 37 + 5, 32, 16, 3),
+                                        (5000, 8, 4, 1000), (64 * 64, 16, 2, 2)])
+def test_lary_block_table_vs_numpy(n, k, ell, hi):
+    """Level t, block j: numpy's first argmin over the ell^t blocks from j."""
+    A = W.uniform_array(n, 5 * n + k + ell, 0, hi)
+    T = oracle.lary_block_table(A, k, ell)
+    nb = -(-n // k)
+    levels = 1
+    while ell ** levels <= nb:
+        levels += 1
+    assert T.shape == (levels, nb)
+    for t in range(levels):
+        span = ell ** t
+        for j in range(nb):
+            if j + span > nb:
+                assert T[t, j] == -1
+                continue
+            lo, hi_ = j * k, min(n, (j + span) * k)
+            assert T[t, j] == lo + int(np.argmin(A[lo:hi_]))
+
+
+def test_lary_with_ell_2_is_the_block_sparse_table():
+    A = W.uniform_array(3000, 61, 0, 7)
+    for k in (1, 4, 32):
+        assert np.array_equal(oracle.lary_block_table(A, k, 2), oracle.block_sparse_table(A, k))
+
+
+@pytest.mark.parametrize("n", range(1, 7))
+def test_lary_query_exhaustive(n):
+    """Every array of length <= 6 over {0, 1, 2}, every range, several (k, ell):
+    the same answers as the brute force, with at most ell table values."""
+    l, r = all_ranges(n)
+    for A in itertools.product((0, 1, 2), repeat=n):
+        A = np.array(A, dtype=np.int32)
+        want = brute(A, l, r)
+        for k in (1, 2):
+            for ell in (2, 3, 4):
+                got, used = oracle.lary_query(A, k, ell, l, r)
+                assert np.array_equal(got, want), (A, k, ell)
+                assert used.max() <= ell
+
+
+@pytest.mark.parametrize("k,ell", [(1, 2), (1, 16), (3, 3), (8, 4), (64, 16)])
+def test_lary_query_random_and_lookup_bound(k, ell):
+    n, q = 20_000, 5_000
+    A = W.uniform_array(n, 71 + k + ell, 0, 100)
+    l, r = W.uniform_queries(n, q, 72)
+    ls, rs = W.log_width_queries(n, 2_000, 73, 1, 3_000)
+    l, r = np.concatenate([l, ls]), np.concatenate([r, rs])
+    got, used = oracle.lary_query(A, k, ell, l, r)
+    assert np.array_equal(got, oracle.rmq_naive(A, l, r))
+    assert used.max() <= ell
+    # a query whose inner span is ell^t blocks long uses exactly one value
+    nb = -(-n // k)
+    for t in range(1, 4):
+        L = ell ** t
+        if L + 2 > nb:
+            break
+        lo, hi = 0, (L + 1) * k   # blocks 0 and L + 1 are the end blocks
+        g, u = oracle.lary_query(A, k, ell, np.array([lo], np.int32), np.array([hi], np.int32))
+        assert u[0] == 1 and g[0] == oracle.rmq_naive(A, [lo], [hi])[0]
+
+
+def test_lary_levels_closed_form():
+    """floor(log_ell nb) + 1, the level count behind the variant's space bound."""
+    for nb in (1, 2, 15, 16, 17, 255, 256, 257, 97_657, 10**9):
+        for ell in (2, 3, 4, 16):
+            lv = oracle.lary_levels(nb, ell)
+            assert ell ** (lv - 1) <= nb < ell ** lv, (nb, ell, lv)
+    assert oracle.lary_levels(0, 2) == 0 and oracle.lary_levels(5, 1) == 0
+
+
 # ---------------------------------------------------------------- planted mutants
 
 def _mutant_rightmost(A, l, r):
