@@ -275,6 +275,17 @@ const char *rmq_strerror(rmq_status s);
  * with nb = ceil(n / k) (the memory model of Table 2).  -1 on bad arguments. */
 int64_t rmq_table_bytes(int64_t n, int32_t k);
 
+/* The plain form over the l-ary block sparse table (the variant of Sec. 3.1
+ * that the paper describes without implementing): level t holds the minimum
+ * of every l^t consecutive blocks, so a query's inner span is covered by at
+ * most l table values, and the table has floor(log_l nb) + 1 levels
+ * (nb = ceil(n / k)) instead of floor(log2 nb) + 1.  k: power of two in
+ * [32, 65536]; ell: power of two in [2, 256].  Same answers, error behaviour
+ * and ownership as rmq_batch_ex; its table (levels * nb * 8 bytes) comes from
+ * the stream-ordered pool.  One launch per level, one thread per query. */
+rmq_status rmq_batch_lary(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r,
+                          int64_t q, int32_t *out, int32_t k, int32_t ell, void *stream);
+
 /* Device workspace, in bytes, that one rmq_batch_ex call with these
  * arguments takes from the stream-ordered pool: the extra memory beside the
  * 4n bytes of A, as Table 2 reports it.  Plain form: levels 0..lc of the

@@ -441,6 +441,19 @@ int64_t rmq_table_bytes(int64_t n, int32_t k) {
     return table_entries(n, ilog2_host((uint64_t)k)) * 8;
 }
 
+rmq_status rmq_batch_lary(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
+                          int32_t k, int32_t ell, void *stream) {
+    if (check_batch_args(A, n, l, r, q, out, nullptr) != RMQ_OK) return RMQ_ERR_INVALID_ARG;
+    if (!pow2_in_range(k) || ell < 2 || ell > 256 || (ell & (ell - 1))) return RMQ_ERR_INVALID_ARG;
+    const int logk = ilog2_host((uint64_t)k), logell = ilog2_host((uint64_t)ell);
+    const int64_t nb = cdiv(n, 1ll << logk);
+    cudaStream_t s = as_stream(stream);
+    Workspace ws;
+    rmq_status st = ws.alloc((size_t)(lary_levels(nb, logell) * nb) * 8, s);
+    if (st != RMQ_OK) return st;
+    return cuda_status(run_lary(A, n, logk, logell, l, r, q, out, static_cast<uint64_t *>(ws.p), s));
+}
+
 int64_t rmq_batch_workspace_bytes(int64_t n, int64_t q, const rmq_opts *opts) {
     int32_t dummy = 0;
     if (check_batch_args(&dummy, n, &dummy, &dummy, q, &dummy, opts) != RMQ_OK) return -1;

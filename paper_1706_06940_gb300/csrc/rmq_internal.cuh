@@ -277,6 +277,12 @@ cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint
                                const int32_t *l, const int32_t *r, int64_t q, int32_t *out, cudaStream_t s,
                                const uint64_t *M1 = nullptr, int cap = kCoarseCap);
 
+// The l-ary block sparse table (lary.cu): levels of the table for nb blocks
+// and l = 2^logell; the whole batch with the table T (lary_levels * nb keys).
+int lary_levels(int64_t nb, int logell);
+cudaError_t run_lary(const int32_t *A, int64_t n, int logk, int logell, const int32_t *l, const int32_t *r,
+                     int64_t q, int32_t *out, uint64_t *T, cudaStream_t s);
+
 // Many arrays in one persistent launch (multi.cu).
 constexpr int kMultiMax = 1024;   // arrays per launch (their descriptors travel as a kernel parameter)
 int multi_logk(int64_t n);

@@ -100,6 +100,7 @@ _SIGS = {
     "rmq_strerror": (ctypes.c_char_p, [_i32]),
     "rmq_table_bytes": (_i64, [_i64, _i32]),
     "rmq_batch_workspace_bytes": (_i64, [_i64, _i64, ctypes.POINTER(rmq_opts)]),
+    "rmq_batch_lary": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, _i32, _i32, _vp]),
     "rmq_tune": (_i32, [_i64, _i64, ctypes.POINTER(rmq_opts)]),
     "rmq_block_minima": (_i32, [_vp, _i64, _i32, _vp, _vp]),
     "rmq_sparse_table_build": (_i32, [_vp, _i64, _vp]),
@@ -368,6 +369,13 @@ def rmq_strerror(status) -> str:
 
 def rmq_table_bytes(n: int, k: int) -> int:
     return int(load().rmq_table_bytes(int(n), int(k)))
+
+
+def rmq_batch_lary(A, l, r, out, k: int, ell: int, stream=None):
+    """The plain form over the ell-ary block sparse table (see include/rmq.h)."""
+    _check(load().rmq_batch_lary(_dptr(A, _i32t(), "A"), A.numel(), _dptr(l, _i32t(), "l"),
+                                 _dptr(r, _i32t(), "r"), l.numel(), _dptr(out, _i32t(), "out"),
+                                 int(k), int(ell), _stream(stream, A)))
 
 
 def rmq_batch_workspace_bytes(n: int, q: int, variant=0, k=0, k_con=0) -> int:
