@@ -189,6 +189,20 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
+def coarse_lc(nb, cap=4096):
+    """Levels 0 .. lc of a plain block table of nb blocks are kept in memory:
+    lc is the smallest shift whose coarse summary (nbc = ceil(nb / 2^lc)
+    coarse blocks, level t holding its nbc - 2^t + 1 defined entries) has at
+    most cap entries."""
+    lc = 0
+    while True:
+        nbc = -(-nb // (1 << lc))
+        lvc = nbc.bit_length()
+        if lvc * (nbc + 1) - ((1 << lvc) - 1) <= cap:
+            return lc
+        lc += 1
+
+
 def profiled_traffic(kernel_src_rel, summary_rel, n, k):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     the current source of the kernel (its sha256 is recorded there) and on
@@ -406,15 +420,7 @@ def run_ours(args, dist):
     # the block table keeps levels 0 .. lc (the coarse level above lives in
     # shared memory); with k >= 128 the block-minima pass also writes the
     # minima of every 128 cells (Sec. 3.3's small blocks)
-    # (the coarse summary: at most 4096 entries, level t holding its
-    # nbc - 2^t + 1 defined entries)
-    lc = 0
-    while True:
-        nbc = -(-nb // (1 << lc))
-        lvc = nbc.bit_length()
-        if lvc * (nbc + 1) - ((1 << lvc) - 1) <= 4096:
-            break
-        lc += 1
+    lc = coarse_lc(nb)
     m1 = -(-n // 128) if k >= 128 else 0
     bytes_a1 = 4 * n + 8 * nb + 8 * m1
     ms_a1 = stages["plain"]["block_minima"] if "plain" in stages else None

@@ -67,6 +67,18 @@ def test_plain_workspace_between_level_zero_and_the_full_table(lib, n, k):
     assert 8 * nb + m1 <= ws <= rmq.rmq_table_bytes(n, k) + m1
 
 
+@pytest.mark.parametrize("n,k", [(10**8, 1024), (10**8, 512), (10**9, 2048), (5000, 32), (1, 64),
+                                 (510 * 32, 32), (511 * 32, 32)])
+def test_bench_table_geometry_matches_the_library(lib, n, k):
+    """bench.py counts the plain form's bytes with its own copy of the coarse
+    geometry; it must give the library's workspace exactly."""
+    import bench
+    nb = -(-n // k)
+    m1 = -(-n // 128) if k >= 128 else 0
+    want = rmq.rmq_batch_workspace_bytes(n, 1000, rmq.Variant.PLAIN, k=k)
+    assert 8 * (nb * (bench.coarse_lc(nb) + 1) + m1) == want
+
+
 def test_contracted_workspace_holds_the_bitmap_and_a_q(lib):
     n = 10**9
     prev = 0
