@@ -330,14 +330,12 @@ __global__ void __launch_bounds__(kMT, 3) k_multi(const __grid_constant__ MultiP
             uint64_t best[4];
             Pending pl[4], pr[4];
             bool hl[4], hr[4], ok[4];
-            int32_t lq[4];
             bool bad = false;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int64_t qi = threadIdx.x * 4 + i;
                 const bool present = qi < qn;
                 const int32_t l = present ? p.L[qbase + qi] : 0, r = present ? p.R[qbase + qi] : -1;
-                lq[i] = l;
                 ok[i] = present && l >= 0 && r >= l && r < d.n;
                 bad |= present && !ok[i];
                 hl[i] = hr[i] = false;

@@ -204,7 +204,7 @@ extern "C" {
 rmq_status rmq_server_create(const rmq_server_opts *opts, rmq_server *out) {
     if (!out) return RMQ_ERR_INVALID_ARG;
     *out = nullptr;
-    rmq_server_opts o{0, 0, 0, 0};
+    rmq_server_opts o{};
     if (opts) o = *opts;
     if (o.budget_bytes < 0 || o.inflight < 0 || o.inflight > 64 || o.max_batch_queries < 0 || o.flags != 0)
         return RMQ_ERR_INVALID_ARG;
