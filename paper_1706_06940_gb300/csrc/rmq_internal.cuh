@@ -233,8 +233,9 @@ cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, 
 inline int64_t two_level_entries(int64_t nb, int cap = kCoarseCap) {
     return nb < 1 ? 0 : nb * (coarse_geom(nb, cap).lc + 1);
 }
-// Query kernel: kQueryCtasPerSm CTAs of kQueryThreads per SM (<= 80 KB
-// shared memory, <= 64 registers), one wave, 16 warps of 128 queries per step.
+// Query kernel: kQueryCtasPerSm CTAs of kQueryThreads per SM (<= 113 KB of
+// shared memory each: coarse table, l, r ring, queues and part pool; <= 64
+// registers), one wave, 16 warps of 128 queries per step.
 constexpr int kQueryThreads = 512;
 constexpr int kQueryCtasPerSm = 2;
 inline int64_t query_ctas(int64_t q, int sms) {
