@@ -1,26 +1,37 @@
 #!/usr/bin/env python3
 """Benchmark of batched leftmost-argmin RMQ (block-based sparse table) on GB300.
 
-Workload (default): the paper-shaped single array, A int32 n = 1e8 uniform in
-[0, 2^31), q = 1e7 queries with l, r uniform over [0, n) and l <= r.  One step
-answers the batch once with each form of the method -- plain BbST (block
-minima, sparse table, queries) and BbST_CON (endpoint sort, remap,
-contraction, table over A_Q, queries) -- so a step covers every stage of the
-hot path and answers 2q queries.  Inputs are resident in HBM before timing;
-L2 is flushed before each form, outside the timed events: a 256 MiB write, then a
-256 MiB read of another buffer so that the flush's dirty lines are written back
-before the form starts.  Each form is one rmq_batch_ex call between two
-events; the per-stage times (and the block-minima kernel time of the
-roofline) come from rmq_batch_timed calls on the same batch right after the
-timed region, since events between the kernels of a call cost it the overlap
-of programmatic launches.
+Default run (what `python bench.py` measures):
+
+* The headline workload, the paper-shaped single array: A int32 n = 1e8
+  uniform in [0, 2^31), q = 1e7 queries with l, r uniform over [0, n) and
+  l <= r.  One step answers the batch once with each form of the method --
+  plain BbST (block minima, sparse table, queries) and BbST_CON (endpoint
+  marks, ranks, contraction, table over A_Q, queries) -- so a step covers
+  every stage of the hot path and answers 2q queries.  Inputs are resident in
+  HBM before timing; L2 is flushed before each form, outside the timed
+  events: a 256 MiB write, then a 256 MiB read of another buffer so that the
+  flush's dirty lines are written back before the form starts.  Each form is
+  one rmq_batch_ex call between two events.  The per-stage times (one
+  kernel, or a kernel and its memset, per stage) come from rmq_batch_timed
+  calls on the same batch right after the timed region, since events between
+  the kernels of a call cost it the overlap of programmatic launches.  The
+  edge-scan work S comes from rmq_batch_counted (an instrumented query kernel)
+  on the same batch, outside the timed region.
+* Then the other workloads, each as an object of the same JSON line:
+  config1 (n = 1e6, q = 1e3: per-call latency), config3 (tie-heavy, short
+  ranges), config4 (512 uneven arrays in one persistent launch replayed from
+  a CUDA graph) and config5 (64 resident arrays served by the library's
+  continuous-batching server against one call per request).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload all|single|c1|c3|multi|served]
 
 Prints one JSON line (rank 0).  With --impl reference the CPU oracle (naive
-per-query scan, all host cores) answers a bounded sample of the same batch.
-Under torchrun every rank answers its own batch (weak scaling, no collective
-on the data path); the slowest rank's time is reported.
+per-query scan, all host cores) answers a bounded sample of the headline
+batch.  Under torchrun every rank answers its own batch (weak scaling, no
+collective on the data path); the slowest rank's time is reported, and the
+other workloads run at N = 1 only.
 """
 from __future__ import annotations
 
@@ -46,14 +57,15 @@ L2_FLUSH_BYTES = 256 << 20
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["single", "multi", "served"], default="single",
-                   help="single: one n=1e8 array (default); multi: 512 uneven arrays in one launch; "
-                        "served: 64 resident arrays, Poisson request stream")
-    p.add_argument("--duration", type=float, default=2.0, help="served: seconds of arrivals")
-    p.add_argument("--rate", type=float, default=1e4, help="served: requests per second")
+    p.add_argument("--workload", choices=["all", "single", "c1", "c3", "multi", "served"], default="all",
+                   help="all: the headline workload plus configs 1, 3, 4 and 5 in one line (default); "
+                        "single: the headline workload only; c1, c3, multi, served: one other workload")
+    p.add_argument("--served-requests", type=int, default=8000, help="served: requests in the pool")
+    p.add_argument("--served-clients", type=int, default=16, help="served: closed-loop client threads")
+    p.add_argument("--served-window", type=float, default=0.8, help="served: seconds of each open-loop arm")
     p.add_argument("--arrays", type=int, default=512)
     p.add_argument("--n", "--array-size", dest="n", type=float, default=1e8)
     p.add_argument("--q", "--num-queries", dest="q", type=float, default=1e7)
@@ -203,24 +215,31 @@ def coarse_lc(nb, cap=4096):
         lc += 1
 
 
-def profiled_traffic(kernel_src_rel, summary_rel, n, k):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current source of the kernel (its sha256 is recorded there) and on
-    this workload's n and k (recorded as workload_n, workload_k)."""
+def profiled_traffic(kernel, kernel_src_rel, want):
+    """DRAM bytes per launch of `kernel` from a committed ncu summary under
+    profiles/ that names it (a line "kernel: <name>"), if it was taken on the
+    current source of the file that holds the kernel (its sha256 is recorded
+    there) and on this workload (every "workload_<key>: <value>" line of the
+    summary must equal want[key])."""
+    import glob
     try:
-        text = open(os.path.join(ROOT, summary_rel)).read()
         src = open(os.path.join(ROOT, kernel_src_rel), "rb").read()
     except OSError:
         return None
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", text)
-    h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
-    wn = re.search(r"workload_n:\s*([0-9]+)", text)
-    wk = re.search(r"workload_k:\s*([0-9]+)", text)
-    if not m or not h or h.group(1) != hashlib.sha256(src).hexdigest():
-        return None
-    if not wn or not wk or int(wn.group(1)) != n or int(wk.group(1)) != k:
-        return None
-    return int(m.group(1))
+    sha = hashlib.sha256(src).hexdigest()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        text = open(path).read()
+        if not re.search(r"^kernel:\s*%s\s*$" % re.escape(kernel), text, re.M):
+            continue
+        m = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", text)
+        h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+        if not m or not h or h.group(1) != sha:
+            continue
+        wl = dict(re.findall(r"^workload_(\w+):\s*([0-9]+)\s*$", text, re.M))
+        if any(str(int(want.get(key, -1))) != v for key, v in wl.items()) or not wl:
+            continue
+        return int(m.group(1))
+    return None
 
 
 def cpu_baseline(A, l, r, budget_s):
@@ -246,67 +265,82 @@ def cpu_baseline(A, l, r, budget_s):
                       % (s2, len(l), width, dt2)}
 
 
-# ----------------------------------------------------------------- reference arm
 
-def run_reference(args, dist):
-    """The CPU oracle on bounded samples of the same batch, rank 0 only."""
-    if dist.rank != 0:
-        return
+
+def flush_l2(flush, flush_rd, it):
+    """Evict the batch from L2: a write of 256 MiB, then a read of another
+    256 MiB buffer, so that the write's dirty lines are written back first."""
+    flush.fill_(it & 0xFF)
+    flush_rd.max()
+
+
+def distinct_endpoints(n, l, r):
+    """m: the number of distinct endpoint positions of a batch (host)."""
     import numpy as np
+    mark = np.zeros(n, dtype=bool)
+    mark[l] = True
+    mark[r] = True
+    return int(np.count_nonzero(mark))
 
-    import oracle
-    oracle.build()
-    n, q = int(args.n), int(args.q)
-    A, l, r = workload(n, q, args.seed, 0, args.array)
-    threads = oracle.max_threads()
-    per_step = max(0.2, min(2.0, 90.0 / max(args.steps + args.warmup, 1)))
-    s = max(threads, 8)
-    t0 = time.perf_counter()
-    oracle.rmq_naive(A, l[:s], r[:s])
-    rate = s / max(time.perf_counter() - t0, 1e-6)
-    per = int(min(q, max(threads, per_step * rate)))
-    cursor = 0
-    times, answered = [], 0
-    for i in range(args.warmup + args.steps):
-        idx = (np.arange(cursor, cursor + per) % q)
-        cursor += per
-        t0 = time.perf_counter()
-        oracle.rmq_naive(A, l[idx], r[idx])
-        dt = time.perf_counter() - t0
-        if i >= args.warmup:
-            times.append(dt)
-            answered += per
-    total = sum(times)
-    value = answered / total
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * total / max(len(times), 1), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": workload_name(n, q, args.array), "n": n, "q": q, "seed": args.seed,
-                   "sample_queries_per_step": per},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": "naive oracle, %d queries of the batch per step, %d timed steps"
-                                   % (per, len(times))},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+
+def coarse_lc_con(nbq):
+    return coarse_lc(nbq, cap=6656)
+
+
+def form_bytes(n, q, k, k_con, m, counts):
+    """Algorithmic bytes of each stage of each form (per call), the kernels
+    that run it, and the whole forms' HBM terms (n cells, q queries, block
+    sizes k and k_con, m distinct endpoints, counts from rmq_batch_counted).
+
+    Plain (Sec. 3.2): A read once (4n), levels 0..lc of the block table
+    written (8 nb (lc + 1)), the minima of every 128 cells when k >= 128
+    (Sec. 3.3), l, r read and out written (12q), and the edge scans: S cells
+    of A (4S) and the 128-cell minima they read.
+    Contracted (Sec. 3.1): l, r read by the marking (8q) and W bit words
+    written (4W, W = ceil(n/32) + 1); the ranks read the words and write their
+    counts (8W); the contraction reads A, the words and counts, and writes
+    A_Q (4n + 8W + 8(m - 1)); the table over A_Q reads A_Q and writes its
+    levels; the queries read l, r, write out (12q), and read S keys of A_Q
+    and the ranks of their open queries.
+    """
+    nb = -(-n // k)
+    lc = coarse_lc(nb)
+    m1 = -(-n // 128) if k >= 128 else 0
+    W = -(-n // 32) + 1
+    mq = max(m - 1, 1)
+    nbq = -(-mq // k_con)
+    lcq = coarse_lc_con(nbq)
+    cp, cc = counts.get("plain", {}), counts.get("contracted", {})
+    S_p = cp.get("scan_elems", 0)
+    S_c = cc.get("scan_elems", 0)
+    stages = {
+        "plain": {
+            "block_minima": ("k_block_min_warp" if k >= 128 else "k_block_min_group",
+                             "block_min.cu", 4 * n + 8 * nb + 8 * m1),
+            "sparse_table": ("k_st_round", "sparse_table.cu", 8 * nb * (lc + 1)),
+            "queries": ("k_query_two<SrcI32>", "query.cuh",
+                        12 * q + 4 * S_p + 8 * cp.get("m1_reads", 0)),
+        },
+        "contracted": {
+            "mark": ("memset + k_mark_endpoints", "contract.cu", 8 * q + 4 * W),
+            "rank": ("k_bits_partial + k_bits_final", "contract.cu", 8 * W),
+            "contract": ("k_contract", "contract.cu", 4 * n + 8 * W + 8 * mq),
+            "table_AQ": ("k_block_min_warp<SrcU64> + k_st_round", "block_min.cu", 8 * mq + 8 * nbq * (lcq + 1)),
+            "queries": ("k_query_two<SrcU64, CON>", "query.cuh",
+                        12 * q + 8 * S_c + 4 * cc.get("rank_reads", 0)),
+        },
     }
-    print(json.dumps(line), flush=True)
+    hbm_plain = 4 * n + 8 * nb * (lc + 1) + 8 * m1 + 12 * q + 4 * S_p
+    # the contracted form's algorithmic minimum as the measurement model
+    # states it (one pass over A between the extreme endpoints, l and r read,
+    # 2q sorted 8-byte pairs written and read once, A_Q, its table, out)
+    con_min = 4 * n + 8 * q + 32 * q + 8 * m + 8 * nbq * (lcq + 1) + 4 * q
+    return stages, hbm_plain, con_min, {"nb": nb, "lc": lc, "m1": m1, "W": W, "m": m, "nbq": nbq, "lcq": lcq}
 
 
-# ----------------------------------------------------------------- our arm
+# ----------------------------------------------------------------- headline workload
 
-def run_ours(args, dist):
-    import numpy as np
-    import torch
-
-    import __graft_entry__
-    if dist.rank == 0:
-        __graft_entry__.build()
-    dist.barrier()
-    from paper_1706_06940_gb300 import rmq
-
-    rmq.load()
-    torch.cuda.set_device(dist.local)
+def run_main(args, dist, rmq, torch, np):
     dev = torch.device("cuda", dist.local)
     n, q = int(args.n), int(args.q)
     A, l, r = workload(n, q, args.seed, dist.rank, args.array)
@@ -316,35 +350,31 @@ def run_ours(args, dist):
             "contracted": torch.empty(q, dtype=torch.int32, device=dev)}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     flush_rd = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    forms = ["plain", "contracted"] if args.variant == "both" else [args.variant]
     # block sizes: measured on this batch over 32..4096 (the autotuner), unless given
     tune_ms = {}
     k, k_con = args.k, args.k_con
-    run_forms = ["plain", "contracted"] if args.variant == "both" else [args.variant]
     if not k:
         k = rmq.rmq_tune(n, q)["k"]
-        if "plain" in run_forms:
+        if "plain" in forms:
             best, tune_ms["plain"] = rmq.rmq_autotune(dA, dl, dr, outs["plain"], variant=1, k_min=32, k_max=4096)
             k = best["k"]
     if not k_con:
         k_con = rmq.rmq_tune(n, q)["k_con"]
-        if "contracted" in run_forms:
+        if "contracted" in forms:
             best, tune_ms["contracted"] = rmq.rmq_autotune(dA, dl, dr, outs["contracted"], variant=2, k_min=32,
                                                            k_max=4096)
             k_con = best["k_con"]
-    forms = ["plain", "contracted"] if args.variant == "both" else [args.variant]
     nev = {"plain": 4, "contracted": 6}
     vcode = {"plain": rmq.Variant.PLAIN, "contracted": rmq.Variant.CONTRACTED}
     stream = torch.cuda.current_stream(dev)
 
     # a step is one rmq_batch_ex call per form (the public entry point),
-    # bracketed by two events; the per-stage breakdown comes from separate
-    # rmq_batch_timed calls after the timed region (events between the
-    # kernels of a call cost it the overlap of programmatic launches)
+    # bracketed by two events
     def one_step(it):
         evs = {}
         for f in forms:
-            flush.fill_(it & 0xFF)
-            flush_rd.max()
+            flush_l2(flush, flush_rd, it)
             evs[f] = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
             evs[f][0].record(stream)
             rmq.rmq_batch_ex(dA, dl, dr, outs[f], variant=vcode[f], k=k, k_con=k_con)
@@ -354,8 +384,7 @@ def run_ours(args, dist):
     def staged_step(it):
         evs = {}
         for f in forms:
-            flush.fill_(it & 0xFF)
-            flush_rd.max()
+            flush_l2(flush, flush_rd, it)
             evs[f] = [torch.cuda.Event(enable_timing=True) for _ in range(nev[f])]
             rmq.rmq_batch_timed(dA, dl, dr, outs[f], evs[f], variant=vcode[f], k=k, k_con=k_con)
         return evs
@@ -394,8 +423,7 @@ def run_ours(args, dist):
     for evs in all_evs:
         for f in forms:
             form_ms[f] += evs[f][0].elapsed_time(evs[f][1]) / args.steps
-    # per-stage device times (ms) from calls with events at the stage
-    # boundaries, outside the timed region
+    # per-stage device times (ms) from calls with events at the stage boundaries
     stage_names = {"plain": ["block_minima", "sparse_table", "queries"],
                    "contracted": ["mark", "rank", "contract", "table_AQ", "queries"]}
     stages = {f: {s: 0.0 for s in stage_names[f]} for f in forms}
@@ -409,42 +437,56 @@ def run_ours(args, dist):
             for j, s in enumerate(stage_names[f]):
                 stages[f][s] += e[j].elapsed_time(e[j + 1]) / n_staged
             staged_ms[f] += e[0].elapsed_time(e[-1]) / n_staged
+    # the work of the open queries (edge scans S, table gathers), counted by
+    # the instrumented query kernel on the same batch
+    counts = {}
+    for f in forms:
+        cnt_out = torch.empty(q, dtype=torch.int32, device=dev)
+        counts[f] = rmq.rmq_batch_counted(dA, dl, dr, cnt_out, variant=vcode[f], k=k, k_con=k_con)
+        if not torch.equal(cnt_out, outs[f]):
+            raise RuntimeError("%s form: the instrumented kernel's answers differ" % f)
     ms_step = sum(form_ms.values())
     ms_step_max = dist.max(ms_step)
     units = 2 * q if len(forms) == 2 else q
     value = dist.world * units / (ms_step_max * 1e-3)
 
-    # roofline of the dominant single kernel: block minima over A (plain a1)
+    # per-kernel roofline of every stage, and the dominant kernel
     peak, peak_kind = measured_peak_hbm()
-    nb = -(-n // k)
-    # the block table keeps levels 0 .. lc (the coarse level above lives in
-    # shared memory); with k >= 128 the block-minima pass also writes the
-    # minima of every 128 cells (Sec. 3.3's small blocks)
-    lc = coarse_lc(nb)
-    m1 = -(-n // 128) if k >= 128 else 0
-    bytes_a1 = 4 * n + 8 * nb + 8 * m1
-    ms_a1 = stages["plain"]["block_minima"] if "plain" in stages else None
-    roof = None
-    if ms_a1:
-        ach = bytes_a1 / (ms_a1 * 1e-3) / 1e9
-        roof = {"kernel": "k_block_min_warp (block minima over A, plain step a1)", "bound": "hbm",
-                "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "peak_kind": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
-                else "fallback 6.8 TB/s",
-                "algorithmic_bytes_per_launch": bytes_a1,
-                "kernel_time": "CUDA events around the block-minima stage of %d rmq_batch_timed calls on "
-                               "the same batch, same stream, right after the timed region" % n_staged,
-                "traffic": profiled_traffic("paper_1706_06940_gb300/csrc/block_min.cu",
-                                            "profiles/block_minima_n1e8.md", n, k)}
-    # device workspace of each form (the extra memory of Table 2)
+    m = distinct_endpoints(n, l, r)
+    sb, hbm_b, con_min_b, geo = form_bytes(n, q, k, k_con, m, counts)
+    per_kernel = []
+    for f in forms:
+        for s in stage_names[f]:
+            kern, src, b = sb[f][s]
+            ms = stages[f][s]
+            gbs = b / (ms * 1e-3) / 1e9 if ms > 0 else None
+            per_kernel.append({"form": f, "stage": s, "kernel": kern, "source": src, "ms": ms,
+                               "algorithmic_bytes": b, "gbs": gbs, "frac": gbs / peak if gbs else None})
+    dom = max(per_kernel, key=lambda e: e["ms"])
+    dom_src = "paper_1706_06940_gb300/csrc/" + dom["source"]
+    roof = {"kernel": "%s (%s form, stage %s)" % (dom["kernel"], dom["form"], dom["stage"]),
+            "bound": "hbm", "achieved": dom["gbs"], "peak": peak, "unit": "GB/s", "frac": dom["frac"],
+            "peak_kind": ("measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                          else "fallback 6.8 TB/s"),
+            "algorithmic_bytes_per_launch": dom["algorithmic_bytes"],
+            "kernel_time": "CUDA events around the %s stage of %d rmq_batch_timed calls on the same batch, same "
+                           "stream, right after the timed region; the dominant kernel is the stage with the largest "
+                           "time of the step" % (dom["stage"], n_staged),
+            "traffic": profiled_traffic(dom["kernel"], dom_src, {"n": n, "q": q, "k": k, "k_con": k_con}),
+            "per_kernel": per_kernel}
     ws_bytes = {f: rmq.rmq_batch_workspace_bytes(n, q, vcode[f], k=k, k_con=k_con) for f in forms}
-    # whole-form HBM accounting (algorithmic bytes of the plain form)
     hbm_plain = None
     if "plain" in form_ms:
-        b = 4 * n + 8 * (nb * (lc + 1) + m1) + 12 * q
-        hbm_plain = {"algorithmic_bytes": b, "gbs": b / (form_ms["plain"] * 1e-3) / 1e9,
-                     "frac_of_measured": b / (form_ms["plain"] * 1e-3) / 1e9 / peak,
-                     "frac_of_8tbs_nominal": b / (form_ms["plain"] * 1e-3) / 1e9 / 8000.0}
+        gbs = hbm_b / (form_ms["plain"] * 1e-3) / 1e9
+        hbm_plain = {"algorithmic_bytes": hbm_b, "S_cells": counts["plain"]["scan_elems"], "gbs": gbs,
+                     "frac_of_measured": gbs / peak, "frac_of_8tbs_nominal": gbs / 8000.0,
+                     "terms": "4n + 8 nb (lc+1) + 8 ceil(n/128) + 12q + 4S"}
+    hbm_con = None
+    if "contracted" in form_ms:
+        gbs = con_min_b / (form_ms["contracted"] * 1e-3) / 1e9
+        hbm_con = {"algorithmic_bytes_min": con_min_b, "m": m, "S_keys": counts["contracted"]["scan_elems"],
+                   "gbs": gbs, "frac_of_measured": gbs / peak,
+                   "terms": "4n + 8q + 32q + 8m + 8 nbq (lcq+1) + 4q (the measurement model's B_min)"}
 
     # end to end: host buffers through rmq_batch_host, copies inside the timing
     e2e = None
@@ -465,59 +507,187 @@ def run_ours(args, dist):
                "h2d_bytes_per_step": len(forms) * (4 * n + 8 * q),
                "d2h_bytes_per_step": len(forms) * 4 * q,
                "ms_per_step": 1e3 * dt / args.e2e_steps, "buffers": "pinned host"}
+        del pA, pl, pr, pout
 
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(A, l, r, args.cpu_seconds)
 
-    if dist.rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": workload_name(n, q, args.array), "n": n, "q": q, "seed": args.seed,
-                       "forms": forms, "k": k, "k_con": k_con, "k_autotuned": {"range": [32, 4096],
-                                                                           "best_ms": tune_ms},
-                       "l2": "flushed before each form (outside the timed events) by a 256 MiB write, then a 256 MiB "
-                             "read of another buffer (the write's dirty lines leave L2 before the form); "
-                             "A alone (%.0f MB) exceeds L2" % (4 * n / 1e6),
-                       "parallelism": "replicas" if dist.world > 1 else "single GPU"},
-            "forms": {f: {"ms": form_ms[f], "queries_per_s": q / (form_ms[f] * 1e-3),
-                          "stages_ms": stages[f], "staged_call_ms": staged_ms[f]} for f in forms},
-            "hbm_plain": hbm_plain,
-            "memory": {f: {"workspace_bytes": ws_bytes[f], "pct_of_4n": 100.0 * ws_bytes[f] / (4 * n)}
-                       for f in forms},
-            "roofline": roof,
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            "gpu_launches": launches,
-            "clocks": clk,
-            "wall_s_timed_region": t_wall,
-        }
-        print(json.dumps(line), flush=True)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": workload_name(n, q, args.array), "n": n, "q": q, "seed": args.seed,
+                   "forms": forms, "k": k, "k_con": k_con, "k_autotuned": {"range": [32, 4096],
+                                                                       "best_ms": tune_ms},
+                   "l2": "flushed before each form (outside the timed events) by a 256 MiB write, then a 256 MiB "
+                         "read of another buffer (the write's dirty lines leave L2 before the form); "
+                         "A alone (%.0f MB) exceeds L2" % (4 * n / 1e6),
+                   "parallelism": "replicas" if dist.world > 1 else "single GPU"},
+        "forms": {f: {"ms": form_ms[f], "queries_per_s": q / (form_ms[f] * 1e-3),
+                      "stages_ms": stages[f], "staged_call_ms": staged_ms[f],
+                      "open_query_work": counts[f]} for f in forms},
+        "hbm_plain": hbm_plain,
+        "hbm_contracted": hbm_con,
+        "memory": {f: {"workspace_bytes": ws_bytes[f], "pct_of_4n": 100.0 * ws_bytes[f] / (4 * n)}
+                   for f in forms},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "wall_s_timed_region": t_wall,
+    }
+    del dA, dl, dr, outs, flush, flush_rd
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return line
 
 
-def run_multi(args, dist):
+# ----------------------------------------------------------------- config 1
+
+def run_config1(args, rmq, torch, np, dev):
+    """A int32 n = 1e6 uniform in [0, 2^31), q = 1e3 uniform queries: a
+    launch-latency-bound call.  Both forms autotuned; the best one is timed
+    per call (events around one rmq_batch_ex, L2 flushed before each) and as
+    one call replayed from a CUDA graph."""
+    import oracle
+    n, q = 1_000_000, 1000
+    A = W().uniform_array(n, 1001)
+    l, r = W().uniform_queries(n, q, 1002)
+    dA = torch.from_numpy(A).to(dev)
+    dl, dr = torch.from_numpy(l).to(dev), torch.from_numpy(r).to(dev)
+    out = torch.empty(q, dtype=torch.int32, device=dev)
+    best, tune_ms = rmq.rmq_autotune(dA, dl, dr, out, variant=0, k_min=32, k_max=4096)
+    opts = dict(variant=int(best["variant"]), k=best["k"], k_con=best["k_con"])
+    rmq.rmq_batch_ex(dA, dl, dr, out, **opts)
+    torch.cuda.synchronize()
+    if rmq.rmq_stream_status() != rmq.Status.OK or not np.array_equal(out.cpu().numpy(), oracle.rmq_naive(A, l, r)):
+        raise RuntimeError("config 1: answers differ from the oracle")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    flush_rd = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    s = torch.cuda.current_stream(dev)
+    reps = 100
+    direct = []
+    for i in range(reps):
+        flush_l2(flush, flush_rd, i)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        rmq.rmq_batch_ex(dA, dl, dr, out, **opts)
+        e1.record(s)
+        direct.append((e0, e1))
+    # the same call captured once and replayed
+    gs = torch.cuda.Stream(dev)
+    with torch.cuda.stream(gs):
+        rmq.rmq_batch_ex(dA, dl, dr, out, stream=gs.cuda_stream, **opts)    # pool warm on this stream
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=gs):
+        rmq.rmq_batch_ex(dA, dl, dr, out, stream=gs.cuda_stream, **opts)
+    replay = []
+    with torch.cuda.stream(gs):
+        for i in range(reps):
+            flush_l2(flush, flush_rd, i)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(gs)
+            g.replay()
+            e1.record(gs)
+            replay.append((e0, e1))
+    # host-side latency of one synchronous call (enqueue, run, wait)
+    host = []
+    for i in range(reps):
+        t0 = time.perf_counter()
+        rmq.rmq_batch_ex(dA, dl, dr, out, **opts)
+        torch.cuda.current_stream(dev).synchronize()
+        host.append(time.perf_counter() - t0)
+    torch.cuda.synchronize()
+    d_ms = statistics.median(a.elapsed_time(b) for a, b in direct)
+    g_ms = statistics.median(a.elapsed_time(b) for a, b in replay)
+    if not np.array_equal(out.cpu().numpy(), oracle.rmq_naive(A, l, r)):
+        raise RuntimeError("config 1: graph replay answers differ from the oracle")
+    return {"workload": "plain RMQ: A int32 n=1e6 uniform in [0,2^31), q=1000 uniform queries (l<=r)",
+            "choice": {"variant": best["variant"].name, "k": best["k"], "k_con": best["k_con"],
+                       "autotune_best_ms": tune_ms},
+            "call_ms_median": d_ms, "queries_per_s": q / (d_ms * 1e-3),
+            "graph_replay_ms_median": g_ms, "graph_queries_per_s": q / (g_ms * 1e-3),
+            "host_sync_call_ms_median": 1e3 * statistics.median(host),
+            "l2": "flushed before every timed call", "calls": reps,
+            "oracle": "naive oracle on all 1000 queries: identical"}
+
+
+# ----------------------------------------------------------------- config 3
+
+def run_config3(args, rmq, torch, np, dev, peak):
+    """A int32 n = 1e8 values uniform in [0, 1000) (many ties), q = 1e7
+    queries of width log-uniform in [1, 1e4], l uniform: edge scans and the
+    leftmost tie-break dominate.  Both forms autotuned over 32..4096; each
+    form's best is timed (L2 flushed before each call) and its open-query work
+    counted, so that the edge-scan bytes enter its HBM fraction."""
+    import oracle
+    n, q = 100_000_000, 10_000_000
+    A = W().uniform_array(n, 1003, 0, 1000)
+    l, r = W().log_width_queries(n, q, 1004, 1, 10_000)
+    dA = torch.from_numpy(A).to(dev)
+    dl, dr = torch.from_numpy(l).to(dev), torch.from_numpy(r).to(dev)
+    out = torch.empty(q, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    flush_rd = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    s = torch.cuda.current_stream(dev)
+    res = {}
+    idx = np.random.default_rng(6).choice(q, size=4000, replace=False)
+    want = oracle.rmq_naive(A, l[idx], r[idx])
+    m = distinct_endpoints(n, l, r)
+    for form, v in (("plain", 1), ("contracted", 2)):
+        best, tms = rmq.rmq_autotune(dA, dl, dr, out, variant=v, k_min=32, k_max=4096)
+        opts = dict(variant=v, k=best["k"], k_con=best["k_con"])
+        times = []
+        for i in range(max(5, min(args.steps, 10))):
+            flush_l2(flush, flush_rd, i)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            rmq.rmq_batch_ex(dA, dl, dr, out, **opts)
+            e1.record(s)
+            times.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = statistics.median(a.elapsed_time(b) for a, b in times)
+        if not np.array_equal(out.cpu().numpy()[idx], want):
+            raise RuntimeError("config 3, %s form: answers differ from the oracle" % form)
+        cnt = rmq.rmq_batch_counted(dA, dl, dr, out, **opts)
+        k = best["k"] if form == "plain" else 1024
+        k_con = best["k_con"] if form == "contracted" else 256
+        sb, hbm_b, con_min_b, geo = form_bytes(n, q, k, k_con, m, {form: cnt})
+        b = hbm_b if form == "plain" else con_min_b + 8 * cnt["scan_elems"] + 4 * cnt["rank_reads"]
+        gbs = b / (ms * 1e-3) / 1e9
+        res[form] = {"k": best["k"] if form == "plain" else best["k_con"], "ms": ms,
+                     "queries_per_s": q / (ms * 1e-3), "open_query_work": cnt,
+                     "algorithmic_bytes": b, "gbs": gbs, "frac_of_measured": gbs / peak}
+    bestf = min(res, key=lambda f: res[f]["ms"])
+    return {"workload": "tie-heavy and short ranges: A int32 n=1e8 values uniform in [0,1000), q=1e7 queries "
+                        "of width log-uniform in [1,1e4], l uniform",
+            "best_form": bestf, "queries_per_s": res[bestf]["queries_per_s"], "forms": res,
+            "bytes": "plain: 4n + 8 nb (lc+1) + 8 ceil(n/128) + 12q + 4S (S cells scanned); contracted: the "
+                     "measurement model's B_min + 8S (S keys of A_Q scanned) + the rank reads of open queries",
+            "l2": "flushed before every timed call", "oracle": "naive oracle on 4000 sampled queries: identical"}
+
+
+def W():
+    from paper_1706_06940_gb300 import workloads
+    return workloads
+
+
+# ----------------------------------------------------------------- config 4
+
+def run_config4(args, rmq, torch, np, dev, peak, seed):
     """512 arrays, n log-uniform in [1e4, 1e7] (uniform int32 values), q
     log-uniform in [10, 1e5] uniform queries each: one persistent launch
     (rmq_batch_multi, replayed from a CUDA graph) against one rmq_batch call
     per array on the same stream."""
-    import numpy as np
-    import torch
-
-    import __graft_entry__
-    if dist.rank == 0:
-        __graft_entry__.build()
-    dist.barrier()
-    from paper_1706_06940_gb300 import rmq, workloads as W
-
-    torch.cuda.set_device(dist.local)
-    dev = torch.device("cuda", dist.local)
-    ns, qs = W.uneven_batch(args.arrays, args.seed + 7919 * dist.rank)
+    import oracle
+    ns, qs = W().uneven_batch(args.arrays, seed)
     dA, ls, rs = [], [], []
     for h, (n, q) in enumerate(zip(ns, qs)):
-        dA.append(torch.from_numpy(W.uniform_array(int(n), args.seed + 17 * h)).to(dev))
-        l, r = W.uniform_queries(int(n), int(q), args.seed + 17 * h + 1)
+        dA.append(torch.from_numpy(W().uniform_array(int(n), seed + 17 * h)).to(dev))
+        l, r = W().uniform_queries(int(n), int(q), seed + 17 * h + 1)
         ls.append(l)
         rs.append(r)
     L = torch.from_numpy(np.concatenate(ls)).to(dev)
@@ -543,80 +713,262 @@ def run_multi(args, dist):
             rmq.rmq_batch(dA[h], L[a:b], R[a:b], out_seq[a:b], stream=s.cuda_stream)
 
     with torch.cuda.stream(s):
-        for _ in range(args.warmup):
+        for _ in range(3):
             g.replay()
             seq_calls()
     torch.cuda.synchronize()
-    if rmq.rmq_stream_status() != rmq.Status.OK:
-        raise RuntimeError("device status after warm-up")
+    if rmq.rmq_stream_status(s.cuda_stream) != rmq.Status.OK:
+        raise RuntimeError("config 4: device status after warm-up")
     if not torch.equal(out, out_seq):
-        raise RuntimeError("multi-array launch and per-array calls disagree")
-    import oracle
+        raise RuntimeError("config 4: the multi-array launch and the per-array calls disagree")
     for h in np.random.default_rng(3).choice(len(dA), 8, replace=False):
         a, b = int(offs[h]), int(offs[h + 1])
         if b > a:
             idx = np.random.default_rng(int(h)).choice(b - a, min(32, b - a), replace=False)
             want = oracle.rmq_naive(dA[h].cpu().numpy(), ls[h][idx], rs[h][idx])
             if not np.array_equal(out[a:b].cpu().numpy()[idx], want):
-                raise RuntimeError("multi-array answers differ from the oracle on array %d" % h)
-    clocks = ClockSampler(dist.local)
-    clocks.start()
-    time.sleep(0.3)
-    dist.barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+                raise RuntimeError("config 4: multi-array answers differ from the oracle on array %d" % h)
+    steps = max(5, min(args.steps, 20))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     with torch.cuda.stream(s):
         for e0, e1 in ev:
             e0.record(s)
             g.replay()
             e1.record(s)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    launches_graph = kernels_per_replay * args.steps   # graph replays launch the captured kernels
-    ms_multi = sum(e0.elapsed_time(e1) for e0, e1 in ev) / args.steps
-    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(max(3, args.steps // 10))]
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
     with torch.cuda.stream(s):
         for e0, e1 in ev2:
             e0.record(s)
             seq_calls()
             e1.record(s)
     torch.cuda.synchronize()
-    clk = clocks.stop(t0, t1)
-    ms_seq = sum(e0.elapsed_time(e1) for e0, e1 in ev2) / len(ev2)
-    ms_max = dist.max(ms_multi)
-    peak, peak_kind = measured_peak_hbm()
-    nbytes = 0
-    for n, q in zip(ns, qs):
-        if q > 0:
-            nbytes += 4 * int(n)
-    nbytes += 12 * qtot
-    if dist.rank == 0:
-        line = {
-            "metric": METRIC, "value": dist.world * qtot / (ms_max * 1e-3), "unit": UNIT, "n_gpus": dist.world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": "batched uneven: %d int32 arrays, n log-uniform in [1e4,1e7] (sum %d), q "
-                                   "log-uniform in [10,1e5] (sum %d), uniform values and queries; one persistent "
-                                   "launch replayed from a CUDA graph" % (len(dA), int(ns.sum()), qtot),
-                       "arrays": len(dA), "sum_n": int(ns.sum()), "sum_q": qtot,
-                       "l2": "inputs (%.1f GB) exceed L2" % (4e-9 * ns.sum())},
+    ms_multi = statistics.median(e0.elapsed_time(e1) for e0, e1 in ev)
+    ms_seq = statistics.median(e0.elapsed_time(e1) for e0, e1 in ev2)
+    nbytes = sum(4 * int(n) for n, q in zip(ns, qs) if q > 0) + 12 * qtot
+    gbs = nbytes / (ms_multi * 1e-3) / 1e9
+    return {"workload": "batched uneven: %d int32 arrays, n log-uniform in [1e4,1e7] (sum %d), q log-uniform in "
+                        "[10,1e5] (sum %d), uniform values and queries; one persistent launch replayed from a CUDA "
+                        "graph" % (len(dA), int(ns.sum()), qtot),
+            "ms": ms_multi, "queries_per_s": qtot / (ms_multi * 1e-3), "kernels_per_replay": kernels_per_replay,
             "per_array_calls": {"ms": ms_seq, "queries_per_s": qtot / (ms_seq * 1e-3),
                                 "speedup_of_one_launch": ms_seq / ms_multi},
-            "hbm": {"algorithmic_bytes": nbytes, "gbs": nbytes / (ms_multi * 1e-3) / 1e9,
-                    "frac_of_measured": nbytes / (ms_multi * 1e-3) / 1e9 / peak, "peak": peak,
-                    "peak_kind": peak_kind},
-            "gpu_launches": launches_graph, "clocks": clk,
-        }
-        print(json.dumps(line), flush=True)
+            "hbm": {"algorithmic_bytes": nbytes, "terms": "4 sum(n) + 12 sum(q)", "gbs": gbs,
+                    "frac_of_measured": gbs / peak},
+            "l2": "inputs (%.1f GB) exceed L2; graph replays back to back" % (4e-9 * ns.sum()),
+            "oracle": "naive oracle on 32 queries of 8 sampled arrays: identical; all answers equal the "
+                      "per-array calls'"}
 
 
-def run_served(args, dist):
+# ----------------------------------------------------------------- config 5
+
+def run_config5(args, rmq, torch, np, dev, seed):
     """64 resident arrays totalling 4e9 cells (n log-uniform in [1e6, 2e8],
-    rescaled), requests arriving as a Poisson stream, each on a random array
-    with a log-uniform batch of [1, 1e5] uniform queries.  The library's
-    server (continuous batching over several streams) against one rmq_query
-    per request in arrival order on one stream, on the same arrival trace."""
+    rescaled), admitted into the library's server by a memory budget.
+    Requests: a random array, a batch log-uniform in [1, 1e5] of uniform
+    queries, in pinned host buffers shared by both arms.
+
+    * capacity (closed loop): client threads each submit a request and wait
+      for it before the next, over the whole request pool; the server
+      (continuous batching over several streams) against the plain path, one
+      rmq_query_host call per request on one stream, one request at a time.
+    * open loop: Poisson arrivals at the configuration's 1e4 requests/s and
+      at higher rates; latency is arrival to answers in the host buffer.
+    """
+    import oracle
+    sizes = W().served_array_sizes(64, 4_000_000_000, seed)
+    gen = torch.Generator(device=dev)
+    dA = []
+    for h, n in enumerate(sizes):
+        gen.manual_seed(seed + 31 * h)
+        dA.append(torch.randint(0, 2**31 - 1, (int(n),), dtype=torch.int32, device=dev, generator=gen))
+    torch.cuda.synchronize()                    # the arrays are written before the server reads them
+    free0, _ = torch.cuda.mem_get_info(dev)
+    budget = int(free0 * 0.8)
+    srv = rmq.Server(budget_bytes=budget, inflight=4)
+    t_adm = time.perf_counter()
+    ids = [srv.admit(A) for A in dA]
+    t_adm = time.perf_counter() - t_adm
+    adm = srv.stats()
+    handles = [rmq.rmq_build(A) for A in dA]
+    torch.cuda.synchronize()
+    g = np.random.default_rng(seed + 1)
+    R = args.served_requests
+    arr = g.integers(0, len(dA), R)
+    qs = W().log_uniform_ints(g, R, 1, 1e5)
+    offs = np.concatenate([[0], np.cumsum(qs)])
+    qtot = int(offs[-1])
+    pin = lambda: torch.empty(qtot, dtype=torch.int32).pin_memory().numpy()
+    Lp, Rp, Os, Op = pin(), pin(), pin(), pin()
+    for i in range(R):
+        n = int(sizes[arr[i]])
+        a = g.integers(0, n, int(qs[i]), dtype=np.int64)
+        b = g.integers(0, n, int(qs[i]), dtype=np.int64)
+        Lp[offs[i]:offs[i + 1]] = np.minimum(a, b)
+        Rp[offs[i]:offs[i + 1]] = np.maximum(a, b)
+    req = [(int(arr[i]), slice(int(offs[i]), int(offs[i + 1]))) for i in range(R)]
+
+    def served_closed(nreq, clients):
+        lat = np.zeros(nreq)
+
+        def client(c):
+            for i in range(c, nreq, clients):
+                h, sl = req[i]
+                t = srv.submit(ids[h], Lp[sl], Rp[sl], Os[sl])
+                lat[i] = srv.wait(t)
+
+        th = [threading.Thread(target=client, args=(c,)) for c in range(clients)]
+        t0 = time.perf_counter()
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        return time.perf_counter() - t0, lat
+
+    def percall_closed(nreq):
+        lat = np.zeros(nreq)
+        t0 = time.perf_counter()
+        for i in range(nreq):
+            h, sl = req[i]
+            t1 = time.perf_counter()
+            rmq.rmq_query_host(handles[h], Lp[sl], Rp[sl], Op[sl])
+            lat[i] = time.perf_counter() - t1
+        return time.perf_counter() - t0, lat
+
+    def served_open(rate, window):
+        nreq = min(R, int(rate * window))
+        arrive = np.cumsum(np.random.default_rng(seed + 2).exponential(1.0 / rate, nreq))
+        tickets = [None] * nreq
+        lag = np.zeros(nreq)
+        lat = np.zeros(nreq)
+
+        def waiter():
+            for i in range(nreq):
+                while tickets[i] is None:
+                    time.sleep(20e-6)
+                lat[i] = srv.wait(tickets[i]) + lag[i]
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        t0 = time.perf_counter()
+        for i in range(nreq):
+            while time.perf_counter() - t0 < arrive[i]:
+                pass
+            h, sl = req[i]
+            lag[i] = time.perf_counter() - t0 - arrive[i]
+            tickets[i] = srv.submit(ids[h], Lp[sl], Rp[sl], Os[sl])
+        th.join()
+        wall = time.perf_counter() - t0
+        return nreq, int(offs[nreq]), wall, lat
+
+    def percall_open(rate, window):
+        nreq = min(R, int(rate * window))
+        arrive = np.cumsum(np.random.default_rng(seed + 2).exponential(1.0 / rate, nreq))
+        lat = np.zeros(nreq)
+        t0 = time.perf_counter()
+        for i in range(nreq):
+            while time.perf_counter() - t0 < arrive[i]:
+                pass
+            h, sl = req[i]
+            rmq.rmq_query_host(handles[h], Lp[sl], Rp[sl], Op[sl])
+            lat[i] = time.perf_counter() - t0 - arrive[i]
+        return nreq, int(offs[nreq]), time.perf_counter() - t0, lat
+
+    pct = lambda a, p: float(np.percentile(a, p) * 1e3)
+    # warm both paths (pools, staging), then the capacity arms over the whole pool
+    served_closed(min(R, 200), args.served_clients)
+    percall_closed(min(R, 50))
+    wall_s, lat_s = served_closed(R, args.served_clients)
+    wall_p, lat_p = percall_closed(R)
+    if not np.array_equal(Os, Op):
+        raise RuntimeError("config 5: served and per-call answers differ")
+    for i in np.random.default_rng(seed + 3).choice(R, 16, replace=False):
+        h, sl = req[i]
+        idx = np.random.default_rng(int(i)).choice(sl.stop - sl.start, min(16, sl.stop - sl.start), replace=False)
+        want = oracle.rmq_naive(dA[h].cpu().numpy(), Lp[sl][idx], Rp[sl][idx])
+        if not np.array_equal(Os[sl][idx], want):
+            raise RuntimeError("config 5: served answers differ from the oracle on request %d" % i)
+    cap_s, cap_p = qtot / wall_s, qtot / wall_p
+    open_arms = []
+    for rate in (1e4, 3e4, 1e5):
+        nr, nq, wall, lat = served_open(rate, args.served_window)
+        nr2, nq2, wall2, lat2 = percall_open(rate, args.served_window)
+        open_arms.append({"rate_req_per_s": rate, "requests": nr,
+                          "served": {"queries_per_s": nq / wall, "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99)},
+                          "one_request_per_call": {"queries_per_s": nq2 / wall2, "p50_ms": pct(lat2, 50),
+                                                   "p99_ms": pct(lat2, 99)}})
+    st = srv.stats()
+    srv.close()
+    for hd in handles:
+        hd.free()
+    del dA
+    torch.cuda.empty_cache()
+    return {"workload": "served: 64 resident int32 arrays totalling %d cells (n log-uniform in [1e6,2e8], "
+                        "rescaled), requests on a random array with a batch log-uniform in [1,1e5] of uniform "
+                        "queries (l<=r)" % int(sizes.sum()),
+            "admission": {"budget_bytes": budget, "reserved_bytes": adm["table_bytes_in_use"],
+                          "resident_arrays": adm["resident_arrays"], "admit_s": t_adm},
+            "capacity": {"requests": R, "queries": qtot,
+                         "served": {"clients": args.served_clients, "queries_per_s": cap_s,
+                                    "requests_per_s": R / wall_s, "p50_ms": pct(lat_s, 50), "p99_ms": pct(lat_s, 99)},
+                         "one_request_per_call": {"queries_per_s": cap_p, "requests_per_s": R / wall_p,
+                                                  "p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99)},
+                         "served_over_per_call": cap_s / cap_p},
+            "open_loop": open_arms, "batches": st["batches"],
+            "oracle": "all answers of both arms identical; naive oracle on 16 queries of 16 sampled requests"}
+
+
+# ----------------------------------------------------------------- reference arm
+
+def run_reference(args, dist):
+    """The CPU oracle on bounded samples of the headline batch, rank 0 only.
+    Each step answers at least 16 queries per host thread, so that every
+    thread has work (the oracle hands out one query at a time)."""
+    if dist.rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    n, q = int(args.n), int(args.q)
+    A, l, r = workload(n, q, args.seed, 0, args.array)
+    threads = oracle.max_threads()
+    per_step = max(0.2, min(2.0, 90.0 / max(args.steps + args.warmup, 1)))
+    s = 4 * threads
+    t0 = time.perf_counter()
+    oracle.rmq_naive(A, l[:s], r[:s])
+    rate = s / max(time.perf_counter() - t0, 1e-6)
+    per = int(min(q, max(16 * threads, per_step * rate)))
+    cursor = 0
+    times, answered = [], 0
+    for i in range(args.warmup + args.steps):
+        idx = (np.arange(cursor, cursor + per) % q)
+        cursor += per
+        t0 = time.perf_counter()
+        oracle.rmq_naive(A, l[idx], r[idx])
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            answered += per
+    total = sum(times)
+    value = answered / total
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / max(len(times), 1), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": workload_name(n, q, args.array), "n": n, "q": q, "seed": args.seed,
+                   "sample_queries_per_step": per},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "naive oracle, %d queries of the batch per step (at least 16 per thread), "
+                                   "%d timed steps" % (per, len(times))},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- driver
+
+def run_ours(args, dist):
     import numpy as np
     import torch
 
@@ -624,116 +976,44 @@ def run_served(args, dist):
     if dist.rank == 0:
         __graft_entry__.build()
     dist.barrier()
-    from paper_1706_06940_gb300 import rmq, workloads as W
+    from paper_1706_06940_gb300 import rmq
 
+    rmq.load()
     torch.cuda.set_device(dist.local)
     dev = torch.device("cuda", dist.local)
-    sizes = W.served_array_sizes(64, 4_000_000_000, args.seed + 7919 * dist.rank)
-    gen = torch.Generator(device=dev)
-    dA = []
-    for h, n in enumerate(sizes):
-        gen.manual_seed(args.seed + 31 * h)
-        dA.append(torch.randint(0, 2**31 - 1, (int(n),), dtype=torch.int32, device=dev, generator=gen))
-    torch.cuda.synchronize()                    # the arrays are written before the server reads them
-    free0, _ = torch.cuda.mem_get_info(dev)
-    srv = rmq.Server(budget_bytes=int(free0 * 0.8), inflight=4)
-    t_adm = time.perf_counter()
-    ids = [srv.admit(A) for A in dA]
-    t_adm = time.perf_counter() - t_adm
-    g = np.random.default_rng(args.seed + 1)
-    nreq = int(args.rate * args.duration)
-    arrive = np.cumsum(g.exponential(1.0 / args.rate, nreq))
-    arr = g.integers(0, len(dA), nreq)
-    qs = W.log_uniform_ints(g, nreq, 1, 1e5)
-    reqs = []
-    for i in range(nreq):
-        n = int(sizes[arr[i]])
-        a = g.integers(0, n, int(qs[i]), dtype=np.int64)
-        b = g.integers(0, n, int(qs[i]), dtype=np.int64)
-        reqs.append((int(arr[i]), np.minimum(a, b).astype(np.int32), np.maximum(a, b).astype(np.int32)))
-    qtot = int(qs.sum())
+    peak, _ = measured_peak_hbm()
 
-    def served_run():
-        outs = [np.empty(len(l), np.int32) for _, l, _ in reqs]
-        tickets = [None] * nreq
-        lat = np.zeros(nreq)
-        done_t = [0.0]
-
-        def waiter():
-            for i in range(nreq):
-                while tickets[i] is None:
-                    time.sleep(20e-6)
-                lat[i] = srv.wait(tickets[i])
-            done_t[0] = time.perf_counter()
-
-        th = threading.Thread(target=waiter)
-        th.start()
+    def guarded(name, fn, *a):
         t0 = time.perf_counter()
-        for i, (h, l, r) in enumerate(reqs):
-            while time.perf_counter() - t0 < arrive[i]:
-                pass
-            tickets[i] = srv.submit(ids[h], l, r, outs[i])
-        th.join()
-        return lat, done_t[0] - t0, outs
+        try:
+            res = fn(*a)
+        except Exception as e:          # recorded in the line, which still prints
+            res = {"error": "%s: %s" % (type(e).__name__, e)}
+        res["bench_wall_s"] = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        return res
 
-    handles = [rmq.rmq_build(A) for A in dA]
-    torch.cuda.synchronize()
-    s = torch.cuda.Stream(dev)
-
-    def fifo_run():
-        lat = np.zeros(nreq)
-        outs = []
-        t0 = time.perf_counter()
-        with torch.cuda.stream(s):
-            for i, (h, l, r) in enumerate(reqs):
-                while time.perf_counter() - t0 < arrive[i]:
-                    pass
-                dl = torch.from_numpy(l).to(dev, non_blocking=False)
-                dr = torch.from_numpy(r).to(dev, non_blocking=False)
-                out = torch.empty(len(l), dtype=torch.int32, device=dev)
-                rmq.rmq_query(handles[h], dl, dr, out, stream=s.cuda_stream)
-                o = out.cpu()
-                lat[i] = time.perf_counter() - t0 - arrive[i]
-                outs.append(o.numpy())
-        return lat, time.perf_counter() - t0, outs
-
-    clocks = ClockSampler(dist.local)
-    clocks.start()
-    lat_s, wall_s, outs_s = served_run()
-    clk = clocks.stop()
-    lat_f, wall_f, outs_f = fifo_run()
-    st = srv.stats()
-    for i in range(0, nreq, max(1, nreq // 200)):
-        if not np.array_equal(outs_s[i], outs_f[i]):
-            raise RuntimeError("served and per-request answers differ on request %d" % i)
-    import oracle
-    for i in g.choice(nreq, 16, replace=False):
-        h, l, r = reqs[i]
-        idx = g.choice(len(l), min(len(l), 16), replace=False)
-        if not np.array_equal(outs_s[i][idx], oracle.rmq_naive(dA[h].cpu().numpy(), l[idx], r[idx])):
-            raise RuntimeError("served answers differ from the oracle on request %d" % i)
-    srv.close()
-    for hd in handles:
-        hd.free()
+    if args.workload in ("all", "single"):
+        line = run_main(args, dist, rmq, torch, np)
+        if args.workload == "all":
+            if dist.world == 1:
+                line["config1"] = guarded("config1", run_config1, args, rmq, torch, np, dev)
+                line["config3"] = guarded("config3", run_config3, args, rmq, torch, np, dev, peak)
+                line["config4"] = guarded("config4", run_config4, args, rmq, torch, np, dev, peak, args.seed + 2)
+                line["config5"] = guarded("config5", run_config5, args, rmq, torch, np, dev, args.seed + 3)
+            else:
+                line["other_configs"] = "configs 1, 3, 4 and 5 run at N = 1 only"
+        if dist.rank == 0:
+            print(json.dumps(line), flush=True)
+        return
+    fn = {"c1": lambda: run_config1(args, rmq, torch, np, dev),
+          "c3": lambda: run_config3(args, rmq, torch, np, dev, peak),
+          "multi": lambda: run_config4(args, rmq, torch, np, dev, peak, args.seed + 2),
+          "served": lambda: run_config5(args, rmq, torch, np, dev, args.seed + 3)}[args.workload]
+    res = fn()
     if dist.rank == 0:
-        pct = lambda a, p: float(np.percentile(a, p) * 1e3)
-        line = {
-            "metric": METRIC, "value": qtot / wall_s, "unit": UNIT, "n_gpus": dist.world, "steps": nreq,
-            "warmup": 0, "ms_per_step": 1e3 * wall_s / nreq, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": "served: 64 resident int32 arrays totalling %d cells (n log-uniform in "
-                                   "[1e6,2e8], rescaled), Poisson arrivals at %g req/s for %g s, batch log-uniform "
-                                   "in [1,1e5] uniform queries on a random array" % (int(sizes.sum()), args.rate,
-                                                                                      args.duration),
-                       "requests": nreq, "queries": qtot, "admit_s": t_adm},
-            "served": {"queries_per_s": qtot / wall_s, "p50_ms": pct(lat_s, 50), "p99_ms": pct(lat_s, 99),
-                       "max_ms": float(lat_s.max() * 1e3), "batches": st["batches"], "wall_s": wall_s},
-            "one_request_per_call": {"queries_per_s": qtot / wall_f, "p50_ms": pct(lat_f, 50),
-                                     "p99_ms": pct(lat_f, 99), "max_ms": float(lat_f.max() * 1e3),
-                                     "wall_s": wall_f},
-            "clocks": clk,
-        }
-        print(json.dumps(line), flush=True)
+        print(json.dumps({"workload_only": args.workload, **res}), flush=True)
 
 
 def main():
@@ -742,10 +1022,6 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, dist)
-        elif args.workload == "multi":
-            run_multi(args, dist)
-        elif args.workload == "served":
-            run_served(args, dist)
         else:
             run_ours(args, dist)
     finally:

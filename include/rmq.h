@@ -33,7 +33,7 @@
  *     to -1 on the device and a sticky device error word is raised, which
  *     rmq_stream_status reports as RMQ_ERR_QUERY_RANGE.  l and r are never
  *     swapped.
- *   - Sizes: 1 <= n <= 2^31 - 1, 0 <= q <= 2^30 (q == 0 is a no-op).
+ *   - Sizes: 1 <= n <= 2^31 - 1, 0 <= q <= 2^31 - 1 (q == 0 is a no-op).
  *   - A is int32; arrays that are 16-byte aligned are read with 128-bit
  *     loads, others with 32-bit loads (same results).
  *   - Workspace comes from the device's stream-ordered memory pool
@@ -133,6 +133,28 @@ rmq_status rmq_batch_host(const int32_t *A_host, int64_t n, const int32_t *l_hos
                           const int32_t *r_host, int64_t q, int32_t *out_host,
                           const rmq_opts *opts, void *stream);
 
+/* Work that the queries left open by the coarse level did, as counted by
+ * rmq_batch_counted.  scan_elems is the S of the algorithmic-bytes model:
+ * elements read by partial-block scans (Sec. 3.1 step 4), int32 cells of A
+ * for the plain form, 8-byte keys of A_Q for the contracted form. */
+typedef struct {
+    int64_t open_queries;  /* queries finished on the block table (not settled by the coarse level) */
+    int64_t table_reads;   /* 8-byte block-table entries they gathered */
+    int64_t m1_reads;      /* 8-byte small-block minima they read (plain form, k >= 128; Sec. 3.3) */
+    int64_t scan_elems;    /* elements read by partial-block scans (whole 16-byte vectors) */
+    int64_t rank_reads;    /* 4-byte endpoint-bitmap words and counts read for their ranks (contracted) */
+} rmq_scan_stats;
+
+/* rmq_batch_ex through an instrumented query kernel that also counts the
+ * work of its open queries into *stats (host), for the measurement of the
+ * edge-scan bytes; answers are the same as rmq_batch_ex's.  Slower than
+ * rmq_batch_ex (a measurement tool, not a serving path); waits for the
+ * stream.  A, l, r and out must be 16-byte aligned (RMQ_ERR_INVALID_ARG
+ * otherwise). */
+rmq_status rmq_batch_counted(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r,
+                             int64_t q, int32_t *out, const rmq_opts *opts, void *stream,
+                             rmq_scan_stats *stats);
+
 /* Plain-BbST batch that allocates no device memory (the paper has no
  * counterpart: this is a deployment variant of rmq_batch_ex with the plain
  * form).  Some callers cannot call cudaMalloc: hosts that reserve all device
@@ -149,8 +171,11 @@ rmq_status rmq_batch_host(const int32_t *A_host, int64_t n, const int32_t *l_hos
  *   Returns RMQ_ERR_SCRATCH_LIMIT, enqueuing nothing, when the table for (n, k)
  *   needs more than RMQ_NOALLOC_TABLE_ENTRIES entries (rmq_table_bytes(n, k) / 8).
  * The first call on a device looks up the buffer's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls on a device share the one buffer, and every entry a call
+ * device, with that device current).  That lookup loads the library's module
+ * on the device, which is when the driver commits the buffer's memory: make
+ * the first call at start-up, before the caller's allocator takes the rest of
+ * device memory and before any stream capture.  A call with q == 0 (l, r, out
+ * may be NULL) performs only this set-up.  All calls on a device share the one buffer, and every entry a call
  * reads is written by that call first, so leftovers of earlier calls do not
  * matter; but calls whose work overlaps on the GPU (other streams, or other
  * threads) race on the buffer and must be serialised by the caller. */
@@ -187,6 +212,14 @@ rmq_status rmq_build(const int32_t *A, int64_t n, const rmq_opts *opts, void *st
 rmq_status rmq_query(rmq_handle h, const int32_t *l, const int32_t *r, int64_t q,
                      int32_t *out, void *stream);
 
+/* rmq_query on HOST buffers (pageable or pinned): copies l, r to the device,
+ * answers, copies out back and returns after out_host is written
+ * (synchronous); one request per call.  Device buffers come from the
+ * stream-ordered pool.  Returns what rmq_stream_status returns after the
+ * call (RMQ_ERR_QUERY_RANGE for invalid queries, which answer -1). */
+rmq_status rmq_query_host(rmq_handle h, const int32_t *l_host, const int32_t *r_host, int64_t q,
+                          int32_t *out_host, void *stream);
+
 /* Queries of H requests against resident handles in ONE kernel launch:
  * request h asks q_counts[h] queries (consecutive in l, r, out; positions
  * relative to hs[h]'s array).  A handle may appear in several requests.
@@ -205,14 +238,16 @@ void rmq_free(rmq_handle h);
 
 /* ---------------------------------------------------------------- serving
  * A continuous-batching request server over resident arrays (host threads
- * inside the library).  Arrays are admitted while the array plus an upper
- * bound of its tables fit the memory budget.  Each submitted request (an
- * array id and HOST buffers l, r, out of q entries) is queued; a scheduler
- * thread packs all pending requests into one batch per tick and runs it on
- * one of several streams (upload, one rmq_query_multi launch, download) while
- * earlier batches are still running; a completion thread copies the answers
- * into the requests' out buffers.  The caller keeps l, r, out alive and
- * unmodified until rmq_server_wait returns for the ticket. */
+ * inside the library).  An array holds 4n bytes plus exactly the tables
+ * rmq_build allocates for it (rmq_handle_bytes) against the memory budget.
+ * Each submitted request (an array id and HOST buffers l, r, out of q
+ * entries) is queued; a scheduler thread packs all pending requests into one
+ * batch per tick and runs it on one of several streams (upload, one
+ * multi-request query launch, download) while earlier batches are still
+ * running; a completion thread copies the answers into the requests' out
+ * buffers.  The caller keeps l, r, out alive and unmodified until
+ * rmq_server_wait returns for the ticket.  A request's array stays resident
+ * from submit until its answers are copied: rmq_server_evict waits for that. */
 typedef struct rmq_server_s *rmq_server;
 
 typedef struct {
@@ -238,18 +273,35 @@ rmq_status rmq_server_create(const rmq_server_opts *opts, rmq_server *out);
  * like rmq_build); k = 0 picks it.  The build runs on the server's own stream,
  * so A must be completely written before the call (synchronize the stream
  * that wrote it).  Waits for the build.  RMQ_ERR_BUDGET (and nothing is
- * built) when it does not fit the budget. */
+ * built) when it does not fit the budget now; RMQ_ERR_OOM when the device
+ * has no memory left for its tables. */
 rmq_status rmq_server_admit(rmq_server s, const int32_t *A, int64_t n, int32_t k, int32_t *id_out);
 
-/* Release an array's tables once no queued or running request uses it. */
+/* rmq_server_admit that, when the array does not fit the budget now, waits
+ * up to timeout_s seconds for evictions to free enough of it (RMQ_ERR_BUDGET
+ * if they do not, or at once if the array alone exceeds the budget). */
+rmq_status rmq_server_admit_wait(rmq_server s, const int32_t *A, int64_t n, int32_t k, double timeout_s,
+                                 int32_t *id_out);
+
+/* Release an array's tables.  From the call on, new requests on id are
+ * refused (RMQ_ERR_INVALID_ARG); the call waits until every request already
+ * submitted on id has completed, then frees the tables.  RMQ_ERR_INVALID_ARG
+ * for an unknown id or one already being evicted. */
 rmq_status rmq_server_evict(rmq_server s, int32_t id);
 
-/* Queue a request of q queries on array id; returns a ticket at once. */
+/* Queue a request of q queries on array id; returns a ticket at once.
+ * RMQ_ERR_INVALID_ARG for an unknown or evicted id, or q above the server's
+ * max_batch_queries. */
 rmq_status rmq_server_submit(rmq_server s, int32_t id, const int32_t *l_host, const int32_t *r_host, int64_t q,
                              int32_t *out_host, int64_t *ticket_out);
 
 /* Wait until the ticket's answers are in its out buffer; *latency_s = time
- * from submit to answers (seconds, may be NULL).  Each ticket is waited once. */
+ * from submit to answers (seconds, may be NULL).  Each ticket is waited once.
+ * Returns RMQ_ERR_QUERY_RANGE when some query of this request had l < 0,
+ * r >= n or l > r (checked on the host when the request is batched; those
+ * answers are -1, the others are valid), RMQ_ERR_CUDA when its batch
+ * failed on the device, RMQ_ERR_INVALID_ARG when the server was destroyed
+ * before it ran. */
 rmq_status rmq_server_wait(rmq_server s, int64_t ticket, double *latency_s);
 
 rmq_status rmq_server_stats_get(rmq_server s, rmq_server_stats *out);
@@ -259,9 +311,14 @@ void rmq_server_destroy(rmq_server s);
 
 /* ----------------------------------------------------------- diagnostics */
 
-/* Wait for `stream`, then report and clear the sticky device error word of
- * the current device (errors raised by any call on this device since the
- * last report): RMQ_OK, RMQ_ERR_QUERY_RANGE or RMQ_ERR_TIMEOUT. */
+/* Wait for `stream`, then report and clear its sticky device error word:
+ * the errors raised by this library's calls on this stream (on the current
+ * device) since the last report: RMQ_OK, RMQ_ERR_QUERY_RANGE or
+ * RMQ_ERR_TIMEOUT (RMQ_ERR_CUDA if the stream itself failed).  Each stream
+ * has a word of its own, so calls on other streams neither raise nor
+ * consume it.  NULL and cudaStreamLegacy share the legacy stream's word; a
+ * device keeps words for 255 other streams, and streams beyond those share
+ * words round-robin. */
 rmq_status rmq_stream_status(void *stream);
 
 /* Number of kernel launches this library has issued in the process so far

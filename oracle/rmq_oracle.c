@@ -61,7 +61,7 @@ ORACLE_API void oracle_rmq_naive(const int32_t *A, int64_t n,
     int64_t i;
 #ifdef _OPENMP
     if (nthreads <= 0) nthreads = omp_get_max_threads();
-#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
 #endif
     for (i = 0; i < q; ++i) {
         int32_t lo = l[i], hi = r[i];

@@ -13,18 +13,60 @@
 
 namespace rmq {
 
-// Sticky per-device error word (ERR_* bits), raised by kernels, read and
-// cleared by rmq_stream_status.
-__device__ unsigned g_err_word;
+// Sticky error words (ERR_* bits), one per stream slot on each device:
+// raised by kernels, read and cleared by rmq_stream_status on the stream.
+__device__ unsigned g_err_words[kErrSlots];
 
 namespace {
 
 std::atomic<int64_t> g_launches{0};
-constexpr int kMaxDev = 64;
-std::mutex g_mu;
+std::once_flag g_dev_once[kMaxDev];
 int g_sms[kMaxDev];
-unsigned *g_err_ptr[kMaxDev];
-bool g_pool_done[kMaxDev];
+unsigned *g_err_base[kMaxDev];
+
+// Stream -> error-word slot of one device.  Slot 0 is the legacy default
+// stream; other streams get slots 1 .. kErrSlots - 1 in order of first use,
+// and once those are taken, further streams share them round-robin.
+struct ErrSlots {
+    std::mutex mu;
+    uintptr_t stream[kErrSlots] = {};
+    int used = 1;
+    int next_shared = 1;
+    int slot_of(uintptr_t s) {
+        if (s == 0 || s == 1) return 0;   // NULL and cudaStreamLegacy: the legacy stream
+        std::lock_guard<std::mutex> lk(mu);
+        for (int i = 1; i < used; ++i)
+            if (stream[i] == s) return i;
+        if (used < kErrSlots) {
+            stream[used] = s;
+            return used++;
+        }
+        const int i = next_shared;
+        next_shared = next_shared + 1 < kErrSlots ? next_shared + 1 : 1;
+        return i;
+    }
+};
+ErrSlots g_slots[kMaxDev];
+
+// Once per device: its SM count and the address of its error words.
+void device_setup(int d) {
+    once_per_device(g_dev_once, d, [d] {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || sms <= 0) {
+            cudaGetLastError();
+            sms = 148;
+        }
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_err_words) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        if (d >= 0 && d < kMaxDev) {
+            g_sms[d] = sms;
+            g_err_base[d] = static_cast<unsigned *>(p);
+        }
+    });
+}
 
 }  // namespace
 
@@ -34,47 +76,37 @@ DevInfo dev_info() {
     int d = 0;
     cudaGetDevice(&d);
     if (d < 0 || d >= kMaxDev) return DevInfo{d, 148};
-    if (g_sms[d] == 0) {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (g_sms[d] == 0) {
-            int sms = 0;
-            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || sms <= 0) sms = 148;
-            g_sms[d] = sms;
-        }
-    }
+    device_setup(d);
     return DevInfo{d, g_sms[d]};
 }
 
-unsigned *err_word_ptr() {
+unsigned *err_word_ptr(cudaStream_t s) {
     int d = 0;
     cudaGetDevice(&d);
     if (d < 0 || d >= kMaxDev) return nullptr;
-    if (!g_err_ptr[d]) {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_err_ptr[d]) {
-            void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_err_word) == cudaSuccess) g_err_ptr[d] = static_cast<unsigned *>(p);
-        }
-    }
-    return g_err_ptr[d];
+    device_setup(d);
+    if (!g_err_base[d]) return nullptr;
+    return g_err_base[d] + g_slots[d].slot_of(reinterpret_cast<uintptr_t>(s));
 }
 
 namespace {
 
 // Workspace from the device's default stream-ordered pool; freed memory
 // stays cached in the pool for the next call.
+std::once_flag g_pool_once[kMaxDev];
+
 void pool_setup() {
     int d = 0;
     cudaGetDevice(&d);
-    if (d < 0 || d >= kMaxDev || g_pool_done[d]) return;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (g_pool_done[d]) return;
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, d) == cudaSuccess) {
-        uint64_t thr = ~0ull;
-        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-    }
-    g_pool_done[d] = true;
+    once_per_device(g_pool_once, d, [d] {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, d) == cudaSuccess) {
+            uint64_t thr = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        } else {
+            cudaGetLastError();
+        }
+    });
 }
 
 struct Workspace {
@@ -118,7 +150,7 @@ namespace {
 cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
 
 constexpr int64_t kMaxN = 2147483647ll;
-constexpr int64_t kMaxQ = 1ll << 30;
+constexpr int64_t kMaxQ = 2147483647ll;   // positions and query indices fit in int32
 
 rmq_status check_batch_args(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q,
                             const int32_t *out, const rmq_opts *opts) {
@@ -158,7 +190,7 @@ int64_t plain_table_keys(int64_t n, int logk) { return two_level_entries(cdiv(n,
 int64_t plain_m1_keys(int64_t n, int logk) { return logk >= 7 ? cdiv(n, 128) : 0; }
 
 rmq_status batch_plain(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
-                       int logk, cudaStream_t s, Stages *sg) {
+                       int logk, cudaStream_t s, Stages *sg, unsigned long long *counts = nullptr) {
     const int64_t nb = cdiv(n, 1ll << logk);
     Workspace ws;
     const int64_t te = plain_table_keys(n, logk);
@@ -173,28 +205,28 @@ rmq_status batch_plain(const int32_t *A, int64_t n, const int32_t *l, const int3
     sg->mark(s);
     if ((e = launch_sparse_table(T, Len{n, nullptr}, logk, nb, s, true)) != cudaSuccess) return cuda_status(e);
     sg->mark(s);
-    e = launch_query_plain(A, n, logk, T, nullptr, l, r, q, out, s, M1);
+    e = launch_query_plain(A, n, logk, T, nullptr, l, r, q, out, s, M1, kCoarseCap, counts);
     sg->mark(s);
     return cuda_status(e);
 }
 
 rmq_status batch_contracted(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
-                            int logk_con, cudaStream_t s, Stages *sg) {
+                            int logk_con, cudaStream_t s, Stages *sg, unsigned long long *counts = nullptr) {
     Workspace ws;
     rmq_status st = ws.alloc(con_workspace_bytes(n, q, logk_con), s);
     if (st != RMQ_OK) return st;
-    return cuda_status(run_contracted(A, n, l, r, q, out, logk_con, ws.p, s, sg));
+    return cuda_status(run_contracted(A, n, l, r, q, out, logk_con, ws.p, s, sg, counts));
 }
 
 rmq_status batch_dispatch(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
-                          const rmq_opts *opts, cudaStream_t s, Stages *sg) {
+                          const rmq_opts *opts, cudaStream_t s, Stages *sg, unsigned long long *counts = nullptr) {
     rmq_status st = check_batch_args(A, n, l, r, q, out, opts);
     if (st != RMQ_OK) return st;
     if (q == 0) return RMQ_OK;
     const rmq_opts o = resolve_opts(n, q, opts);
     if (o.variant == RMQ_VARIANT_CONTRACTED)
-        return batch_contracted(A, n, l, r, q, out, ilog2_host((uint64_t)o.k_con), s, sg);
-    return batch_plain(A, n, l, r, q, out, ilog2_host((uint64_t)o.k), s, sg);
+        return batch_contracted(A, n, l, r, q, out, ilog2_host((uint64_t)o.k_con), s, sg, counts);
+    return batch_plain(A, n, l, r, q, out, ilog2_host((uint64_t)o.k), s, sg, counts);
 }
 
 }  // namespace
@@ -211,6 +243,7 @@ struct rmq_handle_s {
 };
 
 namespace rmq {
+int64_t handle_bytes_for(int64_t n, int logk) { return (two_level_entries(cdiv(n, 1ll << logk)) + kCoarseCap) * 8; }
 const int32_t *h_array(rmq_handle h) { return h->A; }
 const uint64_t *h_table(rmq_handle h) { return h->T; }
 const uint64_t *h_coarse(rmq_handle h) { return h->Cs; }
@@ -239,6 +272,34 @@ rmq_status rmq_batch_timed(const int32_t *A, int64_t n, const int32_t *l, const 
     sg.ev = reinterpret_cast<cudaEvent_t *>(const_cast<void **>(events));
     sg.n = n_events;
     return batch_dispatch(A, n, l, r, q, out, opts, as_stream(stream), &sg);
+}
+
+rmq_status rmq_batch_counted(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q,
+                             int32_t *out, const rmq_opts *opts, void *stream, rmq_scan_stats *stats) {
+    if (!stats) return RMQ_ERR_INVALID_ARG;
+    rmq_status st = check_batch_args(A, n, l, r, q, out, opts);
+    if (st != RMQ_OK) return st;
+    *stats = rmq_scan_stats{};
+    if (q == 0) return RMQ_OK;
+    if (((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(l) | reinterpret_cast<uintptr_t>(r) |
+          reinterpret_cast<uintptr_t>(out)) & 15) != 0)
+        return RMQ_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    Workspace ws;
+    if ((st = ws.alloc(CNT_N * sizeof(unsigned long long), s)) != RMQ_OK) return st;
+    unsigned long long *c = static_cast<unsigned long long *>(ws.p);
+    if (cudaMemsetAsync(c, 0, CNT_N * sizeof(unsigned long long), s) != cudaSuccess) return RMQ_ERR_CUDA;
+    Stages none;
+    if ((st = batch_dispatch(A, n, l, r, q, out, opts, s, &none, c)) != RMQ_OK) return st;
+    unsigned long long h[CNT_N] = {};
+    if (cudaMemcpyAsync(h, c, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RMQ_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return RMQ_ERR_CUDA;
+    stats->open_queries = (int64_t)h[CNT_OPEN];
+    stats->table_reads = (int64_t)h[CNT_TABLE];
+    stats->m1_reads = (int64_t)h[CNT_M1];
+    stats->scan_elems = (int64_t)h[CNT_ELEMS];
+    stats->rank_reads = (int64_t)h[CNT_RANKS];
+    return RMQ_OK;
 }
 
 int64_t rmq_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
@@ -334,7 +395,7 @@ rmq_status rmq_build(const int32_t *A, int64_t n, const rmq_opts *opts, void *st
     h->logk = logk;
     h->nb = cdiv(n, 1ll << logk);
     const int64_t te = two_level_entries(h->nb);
-    h->bytes = (te + kCoarseCap) * 8;
+    h->bytes = handle_bytes_for(n, logk);
     cudaGetDevice(&h->device);
     cudaError_t e = cudaMalloc(&h->T, (size_t)h->bytes);
     if (e != cudaSuccess) {
@@ -359,6 +420,29 @@ rmq_status rmq_query(rmq_handle h, const int32_t *l, const int32_t *r, int64_t q
     if (q == 0) return RMQ_OK;
     if (!l || !r || !out) return RMQ_ERR_INVALID_ARG;
     return cuda_status(launch_query_plain(h->A, h->n, h->logk, h->T, h->Cs, l, r, q, out, as_stream(stream)));
+}
+
+rmq_status rmq_query_host(rmq_handle h, const int32_t *l_host, const int32_t *r_host, int64_t q, int32_t *out_host,
+                          void *stream) {
+    if (!h || q < 0 || q > kMaxQ) return RMQ_ERR_INVALID_ARG;
+    if (q == 0) return RMQ_OK;
+    if (!l_host || !r_host || !out_host) return RMQ_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    const size_t bq = (size_t)q * 4, pad = (bq + 255) & ~(size_t)255;
+    {
+        Workspace ws;
+        rmq_status st = ws.alloc(3 * pad, s);
+        if (st != RMQ_OK) return st;
+        char *base = static_cast<char *>(ws.p);
+        int32_t *dl = reinterpret_cast<int32_t *>(base), *dr = reinterpret_cast<int32_t *>(base + pad),
+                *dout = reinterpret_cast<int32_t *>(base + 2 * pad);
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync(dl, l_host, bq, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
+        if ((e = cudaMemcpyAsync(dr, r_host, bq, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
+        if ((st = rmq_query(h, dl, dr, q, dout, stream)) != RMQ_OK) return st;
+        if ((e = cudaMemcpyAsync(out_host, dout, bq, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_status(e);
+    }
+    return rmq_stream_status(stream);
 }
 
 rmq_status rmq_query_multi(const rmq_handle *hs, const int64_t *q_counts, int32_t H, const int32_t *l,
@@ -408,14 +492,16 @@ void rmq_free(rmq_handle h) {
 }
 
 rmq_status rmq_stream_status(void *stream) {
-    if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return RMQ_ERR_CUDA;
-    unsigned *p = err_word_ptr();
+    cudaStream_t s = as_stream(stream);
+    unsigned *p = err_word_ptr(s);
     if (!p) return RMQ_ERR_CUDA;
+    // read and clear the stream's own word in the stream's order, after its work
     unsigned w = 0;
-    if (cudaMemcpy(&w, p, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return RMQ_ERR_CUDA;
+    if (cudaMemcpyAsync(&w, p, sizeof(w), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RMQ_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return RMQ_ERR_CUDA;
     if (w) {
-        const unsigned zero = 0;
-        if (cudaMemcpy(p, &zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess) return RMQ_ERR_CUDA;
+        if (cudaMemsetAsync(p, 0, sizeof(w), s) != cudaSuccess) return RMQ_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return RMQ_ERR_CUDA;
     }
     if (w & ERR_TIMEOUT) return RMQ_ERR_TIMEOUT;
     if (w & ERR_QUERY_RANGE) return RMQ_ERR_QUERY_RANGE;

@@ -737,7 +737,7 @@ cudaError_t sort_endpoints(const int32_t *l, const int32_t *r, int64_t q, int64_
     const DevInfo di = dev_info();
     uint32_t *pk = (P & 1) ? tk : pos_out, *pv = (P & 1) ? tv : tag_out;
     const int64_t pctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(q, kT), (int64_t)di.sms * 8));
-    unsigned *err = err_word_ptr();
+    unsigned *err = err_word_ptr(s);
     if (!err) return cudaErrorUnknown;
     k_pack<<<(unsigned)pctas, kT, 0, s>>>(l, r, q, n, pk, pv, err);
     note_launches(1);
@@ -808,17 +808,17 @@ cudaError_t contract_bitmap(const int32_t *A, int64_t n, const uint32_t *BW, con
     const int64_t ntA = cdiv(n, kATile);
     const DevInfo di = dev_info();
     SrcI32 src{A};
-    static bool attr[64] = {false};
-    static int occ[64] = {0};
-    if (di.device >= 0 && di.device < 64 && !attr[di.device]) {
+    static std::once_flag once[kMaxDev];
+    static int occ[kMaxDev];
+    int per_sm = 1;   // one resident wave
+    once_per_device(once, di.device, [&] {
         cudaFuncSetAttribute(k_contract<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kContractSmem);
         cudaFuncSetAttribute(k_contract<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kContractSmem);
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_contract<true>, kT, kContractSmem);
-        occ[di.device] = std::max(1, per_sm);
-        attr[di.device] = true;
-    }
-    const int per_sm = (di.device >= 0 && di.device < 64) ? occ[di.device] : 1;   // one resident wave
+        int o = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_contract<true>, kT, kContractSmem);
+        if (di.device >= 0 && di.device < kMaxDev) occ[di.device] = std::max(1, o);
+    });
+    if (di.device >= 0 && di.device < kMaxDev) per_sm = occ[di.device];
     const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(ntA, kT / 32), (int64_t)di.sms * per_sm));
     if ((reinterpret_cast<uintptr_t>(A) & 15) == 0)
         launch_pdl(k_contract<true>, (unsigned)ctas, kT, kContractSmem, s, src, n, BW, BC, m_dev, ntA, AQ);
@@ -835,7 +835,7 @@ size_t endpoint_bitmap_workspace_bytes(int64_t n) { return bitmap_aux_bytes(n); 
 cudaError_t endpoint_bitmap(const int32_t *l, const int32_t *r, int64_t q, int64_t n, uint32_t *BW, uint32_t *BC,
                             int64_t *m_dev, uint64_t *AQ, void *ws, cudaStream_t s, Stages *st, int logk_q,
                             uint32_t *CP, uint16_t *CB) {
-    unsigned *err = err_word_ptr();
+    unsigned *err = err_word_ptr(s);
     if (!err) return cudaErrorUnknown;
     // only the bit words need clearing: k_bits_final writes every count
     cudaError_t e = cudaMemsetAsync(BW, 0, (size_t)bitmap_entries(n) * sizeof(uint32_t), s);
@@ -887,7 +887,8 @@ size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con) {
 }
 
 cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q,
-                           int32_t *out, int logk_con, void *ws, cudaStream_t s, Stages *st) {
+                           int32_t *out, int logk_con, void *ws, cudaStream_t s, Stages *st,
+                           unsigned long long *counts) {
     const int64_t mq_max = std::max<int64_t>(std::min<int64_t>(2 * q, n) - 1, 1);
     const int64_t nbq = cdiv(mq_max, 1ll << logk_con);
     const int64_t lv = coarse_geom(nbq, kCoarseCapCon).lc + 1;
@@ -921,15 +922,22 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
     const int64_t qctas = query_ctas(q, di.sms);                                                        // step 4
     // m is known on the device only: room for the largest coarse table
     const size_t smem = (size_t)kCoarseCapCon * sizeof(uint64_t);
-    if (vecq)
+    unsigned long long *no_counts = nullptr;
+    if (counts) {   // the instrumented kernel (aligned l, r, out only)
+        if (!vecq) return cudaErrorInvalidValue;
+        e = launch_query_two<SrcU64, true, true, true, Count>(di.device, (unsigned)qctas,
+                                                              smem + query_ring_bytes<true, true>(), s, src, lenq,
+                                                              logk_con, kCoarseCapCon, T, nullptr, l, r, BW, BC, CP, CB,
+                                                              nullptr, n, out, q, nullptr, counts);
+    } else if (vecq)
         e = launch_query_two<SrcU64, true, true, true>(di.device, (unsigned)qctas,
                                                        smem + query_ring_bytes<true, true>(), s, src, lenq, logk_con,
                                                        kCoarseCapCon, T, nullptr, l, r, BW, BC, CP, CB, nullptr, n,
-                                                       out, q, nullptr);
+                                                       out, q, nullptr, no_counts);
     else
         e = launch_query_two<SrcU64, true, false, true>(di.device, (unsigned)qctas, smem, s, src, lenq, logk_con,
                                                         kCoarseCapCon, T, nullptr, l, r, BW, BC, CP, CB, nullptr, n,
-                                                        out, q, nullptr);
+                                                        out, q, nullptr, no_counts);
     if (e != cudaSuccess) return e;
     note_launches(1);
     e = cudaGetLastError();

@@ -106,7 +106,7 @@ cudaError_t run_lary(const int32_t *A, int64_t n, int logk, int logell, const in
     const int64_t nb = cdiv(n, (int64_t)1 << logk);
     const int levels = lary_levels(nb, logell);
     const DevInfo di = dev_info();
-    unsigned *err = err_word_ptr();
+    unsigned *err = err_word_ptr(s);
     if (!err) return cudaErrorUnknown;
     cudaError_t e = launch_block_minima_i32(A, n, logk, T, s);
     if (e != cudaSuccess) return e;

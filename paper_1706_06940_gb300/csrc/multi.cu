@@ -413,7 +413,7 @@ size_t multi_workspace_bytes(const int64_t *n, const int64_t *q, const int32_t *
 cudaError_t launch_multi(const int32_t *const *A, const int64_t *n, const int64_t *q, const int32_t *logk, int H,
                          const int32_t *l, const int32_t *r, int32_t *out, uint32_t flags, void *ws, cudaStream_t s) {
     const DevInfo di = dev_info();
-    unsigned *err = err_word_ptr();
+    unsigned *err = err_word_ptr(s);
     if (!err) return cudaErrorUnknown;
     MultiParams *p = new MultiParams();
     p->H = H;
@@ -436,19 +436,21 @@ cudaError_t launch_multi(const int32_t *const *A, const int64_t *n, const int64_
     for (int h = 0; h < H; ++h) p->d[h] = MultiDesc{A[h], (int32_t)n[h], (int32_t)q[h], logk[h], 0};
     cudaError_t e = cudaMemsetAsync(base, 0, ctl, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->Cs, 0xff, (size_t)H * kCoarseCap * 8, s);
-    static bool attr[64] = {false};
-    if (e == cudaSuccess && di.device >= 0 && di.device < 64 && !attr[di.device]) {
-        e = cudaFuncSetAttribute(k_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMultiSmem);
-        attr[di.device] = true;
-    }
-    static int occ[64] = {0};
-    if (e == cudaSuccess && di.device >= 0 && di.device < 64 && occ[di.device] == 0) {
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi, kMT, kMultiSmem);
-        occ[di.device] = std::max(1, per_sm);
-    }
+    static std::once_flag once[kMaxDev];
+    static int occ[kMaxDev];
+    static cudaError_t attr_err[kMaxDev];
+    once_per_device(once, di.device, [&] {
+        const cudaError_t ea = cudaFuncSetAttribute(k_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMultiSmem);
+        int o = 0;
+        if (ea == cudaSuccess) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_multi, kMT, kMultiSmem);
+        if (di.device >= 0 && di.device < kMaxDev) {
+            attr_err[di.device] = ea;
+            occ[di.device] = std::max(1, o);
+        }
+    });
+    if (e == cudaSuccess && di.device >= 0 && di.device < kMaxDev) e = attr_err[di.device];
     if (e == cudaSuccess) {
-        const int ctas = (di.device >= 0 && di.device < 64 ? occ[di.device] : 1) * di.sms;
+        const int ctas = (di.device >= 0 && di.device < kMaxDev ? occ[di.device] : 1) * di.sms;
         k_multi<<<ctas, kMT, kMultiSmem, s>>>(*p);
         note_launches(1);
         e = cudaGetLastError();
@@ -588,7 +590,7 @@ __global__ void __launch_bounds__(kMT, 3) k_query_handles(const __grid_constant_
 cudaError_t launch_query_handles(const QueryReq *reqs, int H, const int32_t *l, const int32_t *r, int32_t *out,
                                  cudaStream_t s) {
     const DevInfo di = dev_info();
-    unsigned *err = err_word_ptr();
+    unsigned *err = err_word_ptr(s);
     if (!err) return cudaErrorUnknown;
     ReqParams *p = new ReqParams();
     p->H = H;

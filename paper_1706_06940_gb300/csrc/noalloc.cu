@@ -57,7 +57,7 @@ using namespace rmq;
 #pragma GCC visibility push(default)
 extern "C" rmq_status rmq_batch_noalloc(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q,
                                         int32_t *out, int32_t k, void *stream) {
-    if (!A || n <= 0 || n > 2147483647ll || q < 0 || q > (1ll << 30)) return RMQ_ERR_INVALID_ARG;
+    if (!A || n <= 0 || n > 2147483647ll || q < 0 || q > 2147483647ll) return RMQ_ERR_INVALID_ARG;
     if (q > 0 && (!l || !r || !out)) return RMQ_ERR_INVALID_ARG;
     if (k != 0 && !noalloc_k_ok(k)) return RMQ_ERR_INVALID_ARG;
     int logk;
@@ -71,9 +71,11 @@ extern "C" rmq_status rmq_batch_noalloc(const int32_t *A, int64_t n, const int32
         while (logk <= MAX_LOGK && noalloc_entries(n, logk) > RMQ_NOALLOC_TABLE_ENTRIES) ++logk;
         if (logk > MAX_LOGK) return RMQ_ERR_SCRATCH_LIMIT;
     }
-    if (q == 0) return RMQ_OK;
+    // the buffer's address on this device (the first call per device looks it
+    // up, which loads this module and commits the buffer); q == 0 does only that
     uint64_t *T = nullptr;
     if (noalloc_table(&T) != cudaSuccess) return RMQ_ERR_CUDA;
+    if (q == 0) return RMQ_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t nb = cdiv(n, 1ll << logk);
     // Every table entry the queries read is written by these launches first,

@@ -6,6 +6,19 @@
 
 namespace rmq {
 
+// Work counters of the instrumented query kernel (rmq_batch_counted), which
+// counts what phase B reads: NoCount compiles to nothing; Count keeps each
+// thread's counts in registers, and the kernel adds them up at its end.
+struct NoCount {
+    static constexpr bool on = false;
+    __device__ __forceinline__ void add(int, int64_t) const {}
+};
+struct Count {
+    static constexpr bool on = true;
+    mutable unsigned long long v[CNT_N] = {0, 0, 0, 0, 0};
+    __device__ __forceinline__ void add(int i, int64_t x) const { v[i] += (unsigned long long)x; }
+};
+
 // A partial-block scan still to do: inclusive index range [lo, hi] of the
 // source sequence, and the hi32 of the block minimum that contains it (the
 // smallest value the scan can possibly meet).
@@ -47,11 +60,14 @@ struct PartPool {
 //     otherwise the partial block is queued for a scan.
 //   * bl == br: the block minimum answers if it lies in the range, else the
 //     range is scanned.
+template <class Ctr = NoCount>
 __device__ __forceinline__ uint64_t resolve_query(const uint64_t *__restrict__ T, int64_t nb, int logk,
                                                   int64_t lo, int64_t hi, uint32_t la, uint32_t ra,
-                                                  Pending &pl, Pending &pr, bool &hl, bool &hr) {
+                                                  Pending &pl, Pending &pr, bool &hl, bool &hr,
+                                                  const Ctr &ctr = Ctr{}) {
     const int64_t bl = lo >> logk, br = hi >> logk;
     const unsigned long long *Tu = reinterpret_cast<const unsigned long long *>(T);
+    ctr.add(CNT_TABLE, bl == br ? 1 : (br - bl >= 2 ? 4 : 2));
     if (bl == br) {
         const uint64_t t0 = __ldg(Tu + bl);
         const uint32_t p = key_pos(t0);
@@ -122,8 +138,9 @@ __device__ __forceinline__ uint64_t resolve_coarse(const uint64_t *cs, const Coa
 // call it with the same arguments).  Lanes read consecutive 16-byte vectors;
 // the scan stops early once some lane has met the value `lb`, the minimum of
 // the enclosing block: nothing further right can then be smaller.
-template <class Src, bool VEC>
-__device__ __forceinline__ uint64_t warp_scan_min(const Src &src, int64_t n, int64_t lo, int64_t hi, uint32_t lb) {
+template <class Src, bool VEC, class Ctr = NoCount>
+__device__ __forceinline__ uint64_t warp_scan_min(const Src &src, int64_t n, int64_t lo, int64_t hi, uint32_t lb,
+                                                  const Ctr &ctr = Ctr{}) {
     constexpr int EPV = Src::EPV;
     const int lane = threadIdx.x & 31;
     uint64_t best = KEY_MAX;
@@ -136,6 +153,7 @@ __device__ __forceinline__ uint64_t warp_scan_min(const Src &src, int64_t n, int
             const int64_t vi = v0 + x * 32 + lane;
             if (vi <= vhi) {
                 uint64_t kk[EPV];
+                ctr.add(CNT_ELEMS, EPV);
                 if (vi < nvfull) {
                     src.template vec<VEC>(vi, kk);
                 } else {
@@ -160,13 +178,15 @@ __device__ __forceinline__ uint64_t warp_scan_min(const Src &src, int64_t n, int
 // Minimum key of A[lo .. hi] (clipped to [0, n)) over the lanes' vectors
 // vlo + lane, vlo + lane + 32, ...: a part of at most 128 cells costs one
 // load per lane (two for the lane at an unaligned end).
-template <bool VEC>
-__device__ __forceinline__ uint64_t lane_part_min(const SrcI32 &src, int64_t n, int64_t lo, int64_t hi) {
+template <bool VEC, class Ctr = NoCount>
+__device__ __forceinline__ uint64_t lane_part_min(const SrcI32 &src, int64_t n, int64_t lo, int64_t hi,
+                                                  const Ctr &ctr = Ctr{}) {
     const int lane = threadIdx.x & 31;
     uint64_t m = KEY_MAX;
     const int64_t nvfull = n / 4;
     for (int64_t vi = lo / 4 + lane; vi <= hi / 4; vi += 32) {
         uint64_t kk[4];
+        ctr.add(CNT_ELEMS, 4);
         if (vi < nvfull) {
             src.template vec<VEC>(vi, kk);
         } else {
@@ -188,15 +208,16 @@ __device__ __forceinline__ uint64_t lane_part_min(const SrcI32 &src, int64_t n, 
 // taken when it lies in the range, else (and only when it could matter) its
 // part of at most 128 cells is scanned.  Two rounds of loads at most: M1,
 // then the end parts.  The whole warp calls it with the same arguments.
-template <bool VEC>
+template <bool VEC, class Ctr = NoCount>
 __device__ __forceinline__ uint64_t warp_range_min_m1(const SrcI32 &src, const uint64_t *__restrict__ M1,
-                                                      int64_t n, int64_t lo, int64_t hi) {
+                                                      int64_t n, int64_t lo, int64_t hi, const Ctr &ctr = Ctr{}) {
     const int lane = threadIdx.x & 31;
     const unsigned long long *Mu = reinterpret_cast<const unsigned long long *>(M1);
     const int64_t ml = lo >> 7, mh = hi >> 7;
     uint64_t best = KEY_MAX;
     bool scan_l = false, scan_r = false;
     int64_t l_end = hi, r_beg = lo;
+    if (lane == 0) ctr.add(CNT_M1, mh - ml + 1);   // the loads below, counted once per warp
     if (ml == mh) {
         const uint64_t e0 = __ldg(Mu + ml);
         const uint32_t p = key_pos(e0);
@@ -219,8 +240,8 @@ __device__ __forceinline__ uint64_t warp_range_min_m1(const SrcI32 &src, const u
         r_beg = mh << 7;
     }
     uint64_t sc = KEY_MAX;
-    if (scan_l) sc = lane_part_min<VEC>(src, n, lo, l_end);
-    if (scan_r) sc = kmin(sc, lane_part_min<VEC>(src, n, r_beg, hi));
+    if (scan_l) sc = lane_part_min<VEC>(src, n, lo, l_end, ctr);
+    if (scan_r) sc = kmin(sc, lane_part_min<VEC>(src, n, r_beg, hi, ctr));
     return kmin(best, warp_min(sc));
 }
 
@@ -231,9 +252,10 @@ __device__ __forceinline__ uint64_t warp_range_min_m1(const SrcI32 &src, const u
 // 16-byte vectors, two per lane), so that their latencies overlap.
 // With M1 (the int32 source only), a scan of a part of a block goes through
 // warp_range_min_m1 instead.
-template <class Src, bool VEC>
+template <class Src, bool VEC, class Ctr = NoCount>
 __device__ __forceinline__ void warp_drain_scans(const Src &src, int64_t n, bool has, const Pending &p,
-                                                 uint64_t &best, const uint64_t *M1 = nullptr) {
+                                                 uint64_t &best, const uint64_t *M1 = nullptr,
+                                                 const Ctr &ctr = Ctr{}) {
     constexpr int EPV = Src::EPV;
     const int lane = threadIdx.x & 31;
     unsigned pend = __ballot_sync(0xffffffffu, has);
@@ -256,9 +278,9 @@ __device__ __forceinline__ void warp_drain_scans(const Src &src, int64_t n, bool
             const uint32_t lb = __shfl_sync(0xffffffffu, p.lb, s);
             uint64_t v;
             if constexpr (EPV == 4) {
-                v = M1 ? warp_range_min_m1<VEC>(src, M1, n, lo, hi) : warp_scan_min<Src, VEC>(src, n, lo, hi, lb);
+                v = M1 ? warp_range_min_m1<VEC>(src, M1, n, lo, hi, ctr) : warp_scan_min<Src, VEC>(src, n, lo, hi, lb, ctr);
             } else {
-                v = warp_scan_min<Src, VEC>(src, n, lo, hi, lb);
+                v = warp_scan_min<Src, VEC>(src, n, lo, hi, lb, ctr);
             }
             if (lane == s) best = kmin(best, v);
             continue;
@@ -291,6 +313,7 @@ __device__ __forceinline__ void warp_drain_scans(const Src &src, int64_t n, bool
                     const int64_t vi = v0 + u * ts + tl;
                     if (vi <= vhi) {
                         uint64_t kk[EPV];
+                        ctr.add(CNT_ELEMS, EPV);
                         if (vi < nvfull) {
                             src.template vec<VEC>(vi, kk);
                         } else {
@@ -415,14 +438,14 @@ __device__ __forceinline__ uint32_t coarse_of(const uint32_t *cp, const uint32_t
 // Phase B of the query kernel for `take` (<= 32) queued queries whose indices
 // are at q_ids: each lane resolves one on the fine table, then the warp runs
 // the edge scans.
-template <class Src, bool CON, bool VEC>
+template <class Src, bool CON, bool VEC, class Ctr>
 __device__ __forceinline__ void resolve_queued(const Src src, int64_t n, int logk, const uint64_t *__restrict__ T,
                                             int64_t nb, const uint64_t *cs, const Coarse g,
                                             const int32_t *__restrict__ L, const int32_t *__restrict__ R,
                                             const uint32_t *__restrict__ BW, const uint32_t *__restrict__ BC,
                                             int32_t *__restrict__ out,
                                             const uint32_t *q_ids, int take, const uint64_t *M1,
-                                            PartPool *pool) {
+                                            PartPool *pool, const Ctr &ctr) {
     const int lane = threadIdx.x & 31;
     const int sh = logk + g.lc;
     const bool has = lane < take;
@@ -432,27 +455,29 @@ __device__ __forceinline__ void resolve_queued(const Src src, int64_t n, int log
     uint32_t qid = 0;
     if (has) {
         qid = q_ids[lane];
+        ctr.add(CNT_OPEN, 1);
+        if (CON) ctr.add(CNT_RANKS, 4);   // bit word and count of each end
         const int32_t l = L[qid], r = R[qid];
         const int64_t lo = CON ? (int64_t)bitmap_rank(BW, BC, (uint32_t)l) : l;
         const int64_t hi = CON ? (int64_t)bitmap_rank(BW, BC, (uint32_t)r) - 1 : r;
         int sub;
         best = resolve_coarse(cs, g, logk, (uint32_t)lo, (uint32_t)hi, (uint32_t)l, (uint32_t)r, sub);
         if (sub == SUB_WHOLE) {
-            best = resolve_query(T, nb, logk, lo, hi, (uint32_t)l, (uint32_t)r, pl, pr, hl, hr);
+            best = resolve_query(T, nb, logk, lo, hi, (uint32_t)l, (uint32_t)r, pl, pr, hl, hr, ctr);
         } else if (sub != SUB_NONE) {
             Pending unused;
             bool unused_flag = false;
             if (sub & SUB_LEFT) {
                 const int64_t end_l = (((lo >> sh) + 1) << sh) - 1;
                 best = kmin(best, resolve_query(T, nb, logk, lo, end_l, (uint32_t)l, 0xffffffffu, pl, unused, hl,
-                                                unused_flag));
+                                                unused_flag, ctr));
             }
             if (sub & SUB_RIGHT) {
                 // a part inside one block records its scan in the first slot
                 const int64_t start_r = (hi >> sh) << sh;
                 Pending a, b;
                 bool ha = false, hb = false;
-                best = kmin(best, resolve_query(T, nb, logk, start_r, hi, 0u, (uint32_t)r, a, b, ha, hb));
+                best = kmin(best, resolve_query(T, nb, logk, start_r, hi, 0u, (uint32_t)r, a, b, ha, hb, ctr));
                 if (ha) { pr = a; hr = true; }
                 if (hb) { pr = b; hr = true; }
             }
@@ -485,8 +510,8 @@ __device__ __forceinline__ void resolve_queued(const Src src, int64_t n, int log
             ++w;
         }
     }
-    warp_drain_scans<Src, VEC>(src, n, hl && !defer, pl, best, M1);
-    warp_drain_scans<Src, VEC>(src, n, hr && !defer, pr, best, M1);
+    warp_drain_scans<Src, VEC>(src, n, hl && !defer, pl, best, M1, ctr);
+    warp_drain_scans<Src, VEC>(src, n, hr && !defer, pr, best, M1, ctr);
     if (has && !defer) out[qid] = (int32_t)key_pos(best);
     __syncwarp();
 }
@@ -494,9 +519,9 @@ __device__ __forceinline__ void resolve_queued(const Src src, int64_t n, int log
 // The CTA's warps drain the pooled edge parts (warp w takes parts w, w + W,
 // ...), then write the pooled queries' answers.  Called by all threads of
 // the CTA, after every warp has finished its queries.
-template <class Src, bool VEC>
+template <class Src, bool VEC, class Ctr>
 __device__ __forceinline__ void drain_pool(const Src src, int64_t n, const uint64_t *M1, PartPool *pool,
-                                           int32_t *__restrict__ out) {
+                                           int32_t *__restrict__ out, const Ctr &ctr) {
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int parts = min(pool->nparts, kPoolParts);
@@ -505,9 +530,10 @@ __device__ __forceinline__ void drain_pool(const Src src, int64_t n, const uint6
         if (lo > hi) continue;   // reserved, unused
         uint64_t v;
         if constexpr (Src::EPV == 4) {
-            v = M1 ? warp_range_min_m1<VEC>(src, M1, n, lo, hi) : warp_scan_min<Src, VEC>(src, n, lo, hi, pool->lb[p]);
+            v = M1 ? warp_range_min_m1<VEC>(src, M1, n, lo, hi, ctr)
+                   : warp_scan_min<Src, VEC>(src, n, lo, hi, pool->lb[p], ctr);
         } else {
-            v = warp_scan_min<Src, VEC>(src, n, lo, hi, pool->lb[p]);
+            v = warp_scan_min<Src, VEC>(src, n, lo, hi, pool->lb[p], ctr);
         }
         if (lane == 0) atomicMin(&pool->best[pool->q[p]], (unsigned long long)v);
     }
@@ -540,7 +566,7 @@ __host__ __device__ constexpr size_t query_ring_bytes() {
     return query_uses_ring<CON, VECQ>() ? (size_t)(kQueryThreads / 32) * kQueryRing * 2 * 32 * 16 : 0;
 }
 
-template <class Src, bool CON, bool VECQ, bool VEC>
+template <class Src, bool CON, bool VECQ, bool VEC, class Ctr = NoCount>
 __global__ void __launch_bounds__(kQueryThreads, kQueryCtasPerSm)
 k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
                                                     const uint64_t *__restrict__ Cs,
@@ -549,8 +575,9 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
                                                     const uint32_t *__restrict__ CP,
                                                     const uint16_t *__restrict__ CB, const uint64_t *__restrict__ M1,
                                                     int64_t n_a, int32_t *__restrict__ out, int64_t q,
-                                                    unsigned *err) {
+                                                    unsigned *err, unsigned long long *counts) {
     pdl_wait();
+    const Ctr ctr{};
     // Phase A answers the queries the coarse table settles.  Each warp queues
     // the others (their indices) in its own shared-memory queue, and as soon
     // as 32 are queued it resolves them (phase B: fine table and edge scans),
@@ -619,7 +646,7 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
     const int sh = logk + g.lc;
     auto resolve = [&](int take) {
         resolve_queued<Src, CON, VEC>(src, n, logk, T, nb, cs, g, L, R, BW, BC, out, my + nq - take, take, M1,
-                                      &pool);
+                                      &pool, ctr);
         nq -= take;
     };
     int slot = 0;
@@ -701,23 +728,34 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
     }
     if (nq > 0) resolve(nq);
     if (RING) cp_async_wait<0>();   // no copy is left in flight (all were empty)
-    drain_pool<Src, VEC>(src, n, M1, &pool, out);
+    drain_pool<Src, VEC>(src, n, M1, &pool, out, ctr);
+    if constexpr (Ctr::on) {   // the instrumented kernel: one atomic per warp and counter
+#pragma unroll
+        for (int i = 0; i < CNT_N; ++i) {
+            unsigned long long v = ctr.v[i];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane == 0 && v) atomicAdd(counts + i, v);
+        }
+    }
 }
 
 // Launches k_query_two with `smem` bytes of dynamic shared memory (the ring
 // plus at most kCoarseCapMax keys of coarse table); the first launch of each
 // instantiation on a device raises the kernel's limit to that maximum.
-template <class Src, bool CON, bool VECQ, bool VEC, class... Args>
+template <class Src, bool CON, bool VECQ, bool VEC, class Ctr = NoCount, class... Args>
 inline cudaError_t launch_query_two(int device, unsigned ctas, size_t smem, cudaStream_t s, Args... args) {
-    static bool raised[64] = {false};
-    auto kern = k_query_two<Src, CON, VECQ, VEC>;
-    if (device < 0 || device >= 64 || !raised[device]) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-            (int)(query_ring_bytes<CON, VECQ>() + kCoarseCapMax * sizeof(uint64_t)));
-        if (e != cudaSuccess) return e;
-        if (device >= 0 && device < 64) raised[device] = true;
-    }
+    static std::once_flag once[kMaxDev];
+    static cudaError_t raised[kMaxDev];
+    auto kern = k_query_two<Src, CON, VECQ, VEC, Ctr>;
+    cudaError_t e = cudaSuccess;
+    once_per_device(once, device, [&] {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(query_ring_bytes<CON, VECQ>() + kCoarseCapMax * sizeof(uint64_t)));
+        if (device >= 0 && device < kMaxDev) raised[device] = e;
+    });
+    if (device >= 0 && device < kMaxDev) e = raised[device];
+    if (e != cudaSuccess) return e;
     return launch_pdl(kern, ctas, kQueryThreads, smem, s, args...);
 }
 

@@ -5,6 +5,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+#include <utility>
+
 #include "../../include/rmq.h"
 
 namespace rmq {
@@ -12,6 +15,10 @@ namespace rmq {
 constexpr uint64_t KEY_MAX = ~0ull;
 constexpr int MIN_LOGK = 5;    // k >= 32
 constexpr int MAX_LOGK = 16;   // k <= 65536
+
+// Counters of the instrumented query kernel (rmq_batch_counted), in the
+// order of rmq_scan_stats.
+enum : int { CNT_OPEN = 0, CNT_TABLE, CNT_M1, CNT_ELEMS, CNT_RANKS, CNT_N };
 
 // Bits of the sticky device error word.
 constexpr unsigned ERR_QUERY_RANGE = 1u;
@@ -204,12 +211,28 @@ struct Stages {
 // Process-wide count of kernel launches issued by this library.
 void note_launches(int count);
 
+// One-time set-up per device (kernel attributes, occupancy, symbol
+// addresses): f runs once per device and process, and a thread that calls
+// while another runs it waits for it; what f stores is then visible to every
+// caller.  Devices beyond kMaxDev run f on every call.
+constexpr int kMaxDev = 64;
+template <class F>
+inline void once_per_device(std::once_flag (&flags)[kMaxDev], int dev, F &&f) {
+    if (dev >= 0 && dev < kMaxDev) std::call_once(flags[dev], std::forward<F>(f));
+    else f();
+}
+
 struct DevInfo {
     int device;
     int sms;
 };
 DevInfo dev_info();                      // current device, cached SM count
-unsigned *err_word_ptr();                // device address of the sticky error word (current device)
+// Device address of the sticky error word (ERR_* bits) of stream s on the
+// current device.  Each stream has a word of its own (up to kErrSlots - 1
+// streams per device; more streams share words), so that the errors of one
+// stream's calls are reported by rmq_stream_status on that stream only.
+constexpr int kErrSlots = 256;
+unsigned *err_word_ptr(cudaStream_t s);
 
 inline int ilog2_host(uint64_t x) { int t = -1; while (x) { x >>= 1; ++t; } return t; }
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -274,9 +297,13 @@ __host__ __device__ inline int64_t bucket_count(int64_t n) { return ((n - 1) >> 
 // built by every query CTA from level lc of T.
 // M1 (optional): the 128-cell minima of A, used for the partial-block parts.
 // cap: the coarse geometry the table was built for (kCoarseCap when Cs is given).
+// counts (optional): 5 device counters; when given, the instrumented kernel
+// runs and adds its work counts there (rmq_scan_stats order; aligned
+// buffers only, else cudaErrorInvalidValue).
 cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint64_t *T, const uint64_t *Cs,
                                const int32_t *l, const int32_t *r, int64_t q, int32_t *out, cudaStream_t s,
-                               const uint64_t *M1 = nullptr, int cap = kCoarseCap);
+                               const uint64_t *M1 = nullptr, int cap = kCoarseCap,
+                               unsigned long long *counts = nullptr);
 
 // The l-ary block sparse table (lary.cu): levels of the table for nb blocks
 // and l = 2^logell; the whole batch with the table T (lary_levels * nb keys).
@@ -308,6 +335,9 @@ cudaError_t launch_query_handles(const QueryReq *reqs, int H, const int32_t *l, 
 // Measured choices of the autotuner (tune.cu).
 bool tuned_lookup(int64_t n, int64_t q, rmq_opts *out);
 
+// Device bytes rmq_build allocates for an array of n cells with blocks of
+// 2^logk cells (levels 0 .. lc of the block table and the coarse summary).
+int64_t handle_bytes_for(int64_t n, int logk);
 // Internals of a resident handle (api.cu), for the multi-request paths.
 const int32_t *h_array(rmq_handle h);
 const uint64_t *h_table(rmq_handle h);
@@ -318,7 +348,8 @@ int32_t h_logk(rmq_handle h);
 // Contracted form (contract.cu).
 size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con);
 cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q,
-                           int32_t *out, int logk_con, void *ws, cudaStream_t s, Stages *st);
+                           int32_t *out, int logk_con, void *ws, cudaStream_t s, Stages *st,
+                           unsigned long long *counts = nullptr);
 cudaError_t sort_endpoints(const int32_t *l, const int32_t *r, int64_t q, int64_t n, uint32_t *pos_out,
                            uint32_t *tag_out, void *ws, size_t ws_bytes, cudaStream_t s);
 size_t sort_workspace_bytes(int64_t q);

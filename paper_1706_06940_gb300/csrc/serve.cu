@@ -4,14 +4,21 @@
 // table) plus the array itself fit in a device-memory budget; their tables
 // stay resident until evicted.  Requests (an array id and host l, r, out
 // buffers) are queued on submit.  A scheduler thread packs every pending
-// request into one batch per tick -- one multi-request query launch
-// (rmq_query_multi) between an upload and a download on one of several
-// streams -- while earlier batches are still on the GPU, so new requests are
-// admitted as slots free up and their work overlaps on the device.  A
-// completion thread waits for each batch's event, copies the answers into the
-// requests' buffers and records each request's latency (submit to answers).
-#include <condition_variable>
+// request into one batch per tick -- one multi-request query launch between
+// an upload and a download on one of several streams -- while earlier
+// batches are still on the GPU, so new requests are admitted as slots free up
+// and their work overlaps on the device.  A completion thread waits for each
+// batch's event, copies the answers into the requests' buffers and records
+// each request's latency (submit to answers).
+//
+// Lifetime of an array's tables: a request pins its array from the moment the
+// scheduler takes it off the queue (under the server lock, where its table
+// pointers are also resolved) until the completion thread has copied its
+// answers.  rmq_server_evict first closes the array to new requests, then
+// waits until no queued request names it and no taken request pins it, and
+// only then frees the tables.
 #include <chrono>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -41,12 +48,16 @@ struct Slot {
     int32_t *h_l = nullptr, *h_r = nullptr, *h_out = nullptr;   // pinned staging
     int32_t *d_l = nullptr, *d_r = nullptr, *d_out = nullptr;   // device staging
     std::vector<Request> reqs;
+    std::vector<QueryReq> qr;     // the requests' table pointers, resolved when they were taken
     std::vector<int64_t> offs;
 };
 
 struct Resident {
     rmq_handle h;
     int64_t bytes;
+    int64_t n;
+    int64_t pinned = 0;    // requests taken off the queue and not yet completed
+    bool closing = false;  // evict has begun: no new requests
 };
 
 }  // namespace
@@ -59,7 +70,7 @@ struct rmq_server_s {
     int64_t budget = 0, in_use = 0;
     int64_t cap = 0;                       // queries per batch
     std::mutex mu;
-    std::condition_variable cv_sched, cv_done, cv_slot;
+    std::condition_variable cv_sched, cv_done, cv_slot, cv_budget;
     std::deque<Request> pending;
     std::vector<Slot> slots;
     std::deque<int> free_slots, inflight;
@@ -75,63 +86,84 @@ struct rmq_server_s {
 
 namespace {
 
+// Copies q entries of l and r into the staging buffers and reports whether
+// every query is valid for an array of n cells (0 <= l <= r < n).
+bool stage_and_check(const int32_t *l, const int32_t *r, int64_t q, int64_t n, int32_t *dl, int32_t *dr) {
+    bool ok = true;
+    for (int64_t i = 0; i < q; ++i) {
+        const int32_t a = l[i], b = r[i];
+        dl[i] = a;
+        dr[i] = b;
+        ok &= a >= 0 && b >= a && (int64_t)b < n;
+    }
+    return ok;
+}
+
 void scheduler(rmq_server_s *S) {
     cudaSetDevice(S->device);
     for (;;) {
         int si;
-        std::vector<Request> batch;
+        std::vector<int64_t> arr_n;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv_sched.wait(lk, [&] { return S->stop || (!S->pending.empty() && !S->free_slots.empty()); });
             if (S->stop) return;
             si = S->free_slots.front();
             S->free_slots.pop_front();
+            Slot &sl = S->slots[si];
+            sl.reqs.clear();
+            sl.qr.clear();
             int64_t total = 0;
-            while (!S->pending.empty() && (int)batch.size() < kReqMax) {
+            while (!S->pending.empty() && (int)sl.reqs.size() < kReqMax) {
                 const Request &rq = S->pending.front();
-                if (!batch.empty() && total + rq.q > S->cap) break;
+                if (!sl.reqs.empty() && total + rq.q > S->cap) break;
+                // the array cannot be freed while the request pins it
+                Resident &res = S->arrays.at(rq.array);
+                res.pinned += 1;
+                const rmq_handle h = res.h;
+                sl.qr.push_back(QueryReq{h_array(h), h_table(h), h_coarse(h), h_n(h), rq.q, h_logk(h)});
+                arr_n.push_back(res.n);
                 total += rq.q;
-                batch.push_back(rq);
+                sl.reqs.push_back(rq);
                 S->pending.pop_front();
             }
         }
         Slot &sl = S->slots[si];
-        sl.reqs = batch;
         sl.offs.assign(1, 0);
-        std::vector<QueryReq> qr;
-        rmq_status st = RMQ_OK;
-        {
-            std::lock_guard<std::mutex> lk(S->mu);
-            for (const Request &rq : batch) {
-                auto it = S->arrays.find(rq.array);
-                const rmq_handle h = it->second.h;
-                qr.push_back(QueryReq{h_array(h), h_table(h), h_coarse(h), h_n(h), rq.q, h_logk(h)});
-            }
-        }
-        for (const Request &rq : batch) {
+        std::vector<int64_t> bad_tickets;
+        for (size_t i = 0; i < sl.reqs.size(); ++i) {
+            const Request &rq = sl.reqs[i];
             const int64_t o = sl.offs.back();
-            std::memcpy(sl.h_l + o, rq.l, (size_t)rq.q * 4);
-            std::memcpy(sl.h_r + o, rq.r, (size_t)rq.q * 4);
+            if (!stage_and_check(rq.l, rq.r, rq.q, arr_n[i], sl.h_l + o, sl.h_r + o)) bad_tickets.push_back(rq.ticket);
             sl.offs.push_back(o + rq.q);
         }
         const int64_t total = sl.offs.back();
         cudaError_t e = cudaMemcpyAsync(sl.d_l, sl.h_l, (size_t)total * 4, cudaMemcpyHostToDevice, sl.stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(sl.d_r, sl.h_r, (size_t)total * 4, cudaMemcpyHostToDevice, sl.stream);
         int64_t qdone = 0;
-        for (size_t g0 = 0; e == cudaSuccess && g0 < qr.size(); g0 += kReqMax) {
-            const int cnt = (int)std::min<size_t>(kReqMax, qr.size() - g0);
+        for (size_t g0 = 0; e == cudaSuccess && g0 < sl.qr.size(); g0 += kReqMax) {
+            const int cnt = (int)std::min<size_t>(kReqMax, sl.qr.size() - g0);
             int64_t qg = 0;
-            for (int i = 0; i < cnt; ++i) qg += qr[g0 + i].q;
-            e = launch_query_handles(qr.data() + g0, cnt, sl.d_l + qdone, sl.d_r + qdone, sl.d_out + qdone, sl.stream);
+            for (int i = 0; i < cnt; ++i) qg += sl.qr[g0 + i].q;
+            e = launch_query_handles(sl.qr.data() + g0, cnt, sl.d_l + qdone, sl.d_r + qdone, sl.d_out + qdone,
+                                     sl.stream);
             qdone += qg;
         }
         if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_out, sl.d_out, (size_t)total * 4, cudaMemcpyDeviceToHost, sl.stream);
+        if (e == cudaSuccess && !bad_tickets.empty()) {
+            // the invalid queries were reported per request above (from the
+            // host check); the kernels also raised the slot stream's error
+            // word, which is cleared here so that it reports nothing later
+            unsigned *ew = err_word_ptr(sl.stream);
+            if (ew) e = cudaMemsetAsync(ew, 0, sizeof(unsigned), sl.stream);
+        }
         if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
-        if (e != cudaSuccess) st = RMQ_ERR_CUDA;
         {
             std::lock_guard<std::mutex> lk(S->mu);
-            if (st != RMQ_OK)
-                for (const Request &rq : batch) S->failed[rq.ticket] = st;
+            if (e != cudaSuccess)
+                for (const Request &rq : sl.reqs) S->failed[rq.ticket] = RMQ_ERR_CUDA;
+            else
+                for (int64_t t : bad_tickets) S->failed[t] = RMQ_ERR_QUERY_RANGE;
             S->inflight.push_back(si);
             S->stats.batches += 1;
         }
@@ -163,8 +195,11 @@ void completer(rmq_server_s *S) {
                     S->finished[rq.ticket] = std::chrono::duration<double>(now - rq.t_submit).count();
                 S->stats.requests += 1;
                 S->stats.queries += rq.q;
+                auto it = S->arrays.find(rq.array);
+                if (it != S->arrays.end()) it->second.pinned -= 1;
             }
             sl.reqs.clear();
+            sl.qr.clear();
             S->free_slots.push_back(si);
         }
         S->cv_sched.notify_all();
@@ -182,6 +217,7 @@ void destroy_server(rmq_server_s *S) {
     S->cv_slot.notify_all();
     S->cv_sched.notify_all();
     S->cv_done.notify_all();
+    S->cv_budget.notify_all();
     if (S->sched.joinable()) S->sched.join();
     if (S->compl_.joinable()) S->compl_.join();
     cudaSetDevice(S->device);
@@ -194,6 +230,57 @@ void destroy_server(rmq_server_s *S) {
     }
     for (auto &kv : S->arrays) rmq_free(kv.second.h);
     delete S;
+}
+
+// Bytes an admitted array holds against the budget: its cells and exactly the
+// tables rmq_build allocates for it.
+int64_t admit_bytes(int64_t n, int32_t k) { return 4 * n + handle_bytes_for(n, ilog2_host((uint64_t)k)); }
+
+rmq_status admit_impl(rmq_server S, const int32_t *A, int64_t n, int32_t k, double timeout_s, int32_t *id_out) {
+    if (!S || !A || n <= 0 || n > 2147483647ll || !id_out) return RMQ_ERR_INVALID_ARG;
+    if (k != 0 && (k < 32 || k > 65536 || (k & (k - 1)))) return RMQ_ERR_INVALID_ARG;
+    cudaSetDevice(S->device);
+    rmq_opts o{RMQ_VARIANT_PLAIN, k, 0, 0};
+    if (!k) {
+        rmq_opts t;
+        rmq_tune(n, 0, &t);
+        o.k = t.k;
+    }
+    const int64_t bytes = admit_bytes(n, o.k);
+    {
+        // reserve the array's bytes; with a timeout, wait for evictions to free them
+        std::unique_lock<std::mutex> lk(S->mu);
+        if (S->budget > 0 && bytes > S->budget) return RMQ_ERR_BUDGET;
+        auto fits = [&] { return S->stop || S->budget <= 0 || S->in_use + bytes <= S->budget; };
+        if (!fits()) {
+            if (timeout_s <= 0) return RMQ_ERR_BUDGET;
+            if (!S->cv_budget.wait_for(lk, std::chrono::duration<double>(timeout_s), fits) || S->stop)
+                return RMQ_ERR_BUDGET;
+        }
+        S->in_use += bytes;
+    }
+    rmq_handle h = nullptr;
+    cudaStream_t bs = nullptr;
+    rmq_status st = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) == cudaSuccess ? RMQ_OK : RMQ_ERR_CUDA;
+    if (st == RMQ_OK) st = rmq_build(A, n, &o, bs, &h);
+    if (st == RMQ_OK && cudaStreamSynchronize(bs) != cudaSuccess) st = RMQ_ERR_CUDA;
+    if (bs) cudaStreamDestroy(bs);
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (st != RMQ_OK) {
+        S->in_use -= bytes;
+        if (h) rmq_free(h);
+        S->cv_budget.notify_all();
+        return st;
+    }
+    const int32_t id = S->next_id++;
+    Resident res;
+    res.h = h;
+    res.bytes = bytes;
+    res.n = n;
+    S->arrays[id] = res;
+    S->stats.table_bytes_in_use = S->in_use;
+    *id_out = id;
+    return RMQ_OK;
 }
 
 }  // namespace
@@ -236,40 +323,13 @@ rmq_status rmq_server_create(const rmq_server_opts *opts, rmq_server *out) {
 }
 
 rmq_status rmq_server_admit(rmq_server S, const int32_t *A, int64_t n, int32_t k, int32_t *id_out) {
-    if (!S || !A || n <= 0 || !id_out) return RMQ_ERR_INVALID_ARG;
-    cudaSetDevice(S->device);
-    rmq_opts o{RMQ_VARIANT_PLAIN, k, 0, 0};
-    {
-        // reserve: the array's own cells and an upper bound of its tables
-        std::lock_guard<std::mutex> lk(S->mu);
-        rmq_opts t;
-        rmq_tune(n, 0, &t);
-        const int32_t kk = k ? k : t.k;
-        const int64_t tb = rmq_table_bytes(n, kk);
-        if (tb < 0) return RMQ_ERR_INVALID_ARG;
-        const int64_t bytes = 4 * n + tb + 8 * kCoarseCap;
-        if (S->budget > 0 && S->in_use + bytes > S->budget) return RMQ_ERR_BUDGET;
-        S->in_use += bytes;
-        o.k = kk;
-    }
-    rmq_handle h = nullptr;
-    cudaStream_t bs = nullptr;
-    cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
-    rmq_status st = rmq_build(A, n, &o, bs, &h);
-    if (st == RMQ_OK && cudaStreamSynchronize(bs) != cudaSuccess) st = RMQ_ERR_CUDA;
-    cudaStreamDestroy(bs);
-    std::lock_guard<std::mutex> lk(S->mu);
-    const int64_t bytes = 4 * n + rmq_table_bytes(n, o.k) + 8 * kCoarseCap;
-    if (st != RMQ_OK) {
-        S->in_use -= bytes;
-        if (h) rmq_free(h);
-        return st;
-    }
-    const int32_t id = S->next_id++;
-    S->arrays[id] = Resident{h, bytes};
-    S->stats.table_bytes_in_use = S->in_use;
-    *id_out = id;
-    return RMQ_OK;
+    return admit_impl(S, A, n, k, 0.0, id_out);
+}
+
+rmq_status rmq_server_admit_wait(rmq_server S, const int32_t *A, int64_t n, int32_t k, double timeout_s,
+                                 int32_t *id_out) {
+    if (timeout_s < 0) return RMQ_ERR_INVALID_ARG;
+    return admit_impl(S, A, n, k, timeout_s, id_out);
 }
 
 rmq_status rmq_server_evict(rmq_server S, int32_t id) {
@@ -278,11 +338,13 @@ rmq_status rmq_server_evict(rmq_server S, int32_t id) {
     {
         std::unique_lock<std::mutex> lk(S->mu);
         auto it = S->arrays.find(id);
-        if (it == S->arrays.end()) return RMQ_ERR_INVALID_ARG;
-        // wait until no queued or running request uses the array
+        if (it == S->arrays.end() || it->second.closing) return RMQ_ERR_INVALID_ARG;
+        it->second.closing = true;   // new submits on id are refused from here on
+        // wait until no queued request names the array and no taken one pins it
         S->cv_slot.wait(lk, [&] {
-            for (const Request &rq : S->pending) if (rq.array == id) return false;
-            for (int si : S->inflight) for (const Request &rq : S->slots[si].reqs) if (rq.array == id) return false;
+            if (it->second.pinned > 0) return false;
+            for (const Request &rq : S->pending)
+                if (rq.array == id) return false;
             return true;
         });
         h = it->second.h;
@@ -292,6 +354,7 @@ rmq_status rmq_server_evict(rmq_server S, int32_t id) {
     }
     cudaSetDevice(S->device);
     rmq_free(h);
+    S->cv_budget.notify_all();
     return RMQ_OK;
 }
 
@@ -300,7 +363,8 @@ rmq_status rmq_server_submit(rmq_server S, int32_t id, const int32_t *l_host, co
     if (!S || !ticket_out || q < 0) return RMQ_ERR_INVALID_ARG;
     if (q > 0 && (!l_host || !r_host || !out_host)) return RMQ_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(S->mu);
-    if (!S->arrays.count(id) || q > S->cap) return RMQ_ERR_INVALID_ARG;
+    auto it = S->arrays.find(id);
+    if (it == S->arrays.end() || it->second.closing || q > S->cap) return RMQ_ERR_INVALID_ARG;
     const int64_t t = S->next_ticket++;
     *ticket_out = t;
     if (q == 0) {

@@ -112,15 +112,14 @@ cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, 
     if (cap < 1 || cap > kCoarseCapMax || (Cs && cap != kCoarseCap)) return cudaErrorInvalidValue;
     const int top = two ? coarse_geom(nb_max, cap).lc : (nb_max >= 2 ? ilog2_host((uint64_t)nb_max) : 0);
     const int kcap = two ? cap : 0;
-    static bool attr_done[64] = {false};
+    static std::once_flag once[kMaxDev];
     const DevInfo di = dev_info();
     const size_t smem0 = 2ull * (kS0 + (1 << kLV0)) * 1 * sizeof(uint64_t);
     const size_t smem1 = 2ull * (kS1 + (1 << kLV1)) * 32 * sizeof(uint64_t);
-    if (di.device < 64 && !attr_done[di.device]) {
+    once_per_device(once, di.device, [&] {
         cudaFuncSetAttribute(k_st_round<1, kLV0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem0);
         cudaFuncSetAttribute(k_st_round<32, kLV1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
-        attr_done[di.device] = true;
-    }
+    });
     {
         const int64_t ctas = cdiv(nb_max, kS0);
         if (top > 0) {

@@ -61,6 +61,11 @@ class rmq_server_stats(ctypes.Structure):
                 ("table_bytes_in_use", ctypes.c_int64), ("resident_arrays", ctypes.c_int64)]
 
 
+class rmq_scan_stats(ctypes.Structure):
+    _fields_ = [("open_queries", ctypes.c_int64), ("table_reads", ctypes.c_int64), ("m1_reads", ctypes.c_int64),
+                ("scan_elems", ctypes.c_int64), ("rank_reads", ctypes.c_int64)]
+
+
 class rmq_opts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("k", ctypes.c_int32),
                 ("k_con", ctypes.c_int32), ("flags", ctypes.c_int32)]
@@ -75,6 +80,8 @@ _SIGS = {
     "rmq_batch_timed": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, ctypes.POINTER(rmq_opts), _vp,
                                ctypes.POINTER(_vp), _i32]),
     "rmq_launch_count": (_i64, []),
+    "rmq_batch_counted": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, ctypes.POINTER(rmq_opts), _vp,
+                                 ctypes.POINTER(rmq_scan_stats)]),
     "rmq_batch_noalloc": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, _i32, _vp]),
     "rmq_batch_multi": (_i32, [ctypes.c_void_p, _i32, _vp, _vp, _vp, ctypes.POINTER(rmq_opts), _vp]),
     "rmq_autotune": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, ctypes.POINTER(rmq_opts),
@@ -85,6 +92,7 @@ _SIGS = {
     "rmq_query_multi": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _vp]),
     "rmq_server_create": (_i32, [ctypes.POINTER(rmq_server_opts), ctypes.POINTER(_vp)]),
     "rmq_server_admit": (_i32, [_vp, _vp, _i64, _i32, ctypes.POINTER(_i32)]),
+    "rmq_server_admit_wait": (_i32, [_vp, _vp, _i64, _i32, ctypes.c_double, ctypes.POINTER(_i32)]),
     "rmq_server_evict": (_i32, [_vp, _i32]),
     "rmq_server_submit": (_i32, [_vp, _i32, _vp, _vp, _i64, _vp, ctypes.POINTER(_i64)]),
     "rmq_server_wait": (_i32, [_vp, _i64, ctypes.POINTER(ctypes.c_double)]),
@@ -93,6 +101,7 @@ _SIGS = {
     "rmq_batch_host": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, ctypes.POINTER(rmq_opts), _vp]),
     "rmq_build": (_i32, [_vp, _i64, ctypes.POINTER(rmq_opts), _vp, ctypes.POINTER(_vp)]),
     "rmq_query": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp]),
+    "rmq_query_host": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp]),
     "rmq_handle_bytes": (_i64, [_vp]),
     "rmq_handle_k": (_i32, [_vp]),
     "rmq_free": (None, [_vp]),
@@ -203,6 +212,17 @@ def rmq_batch_timed(A, l, r, out, events, variant=0, k=0, k_con=0, stream=None):
                                   ctypes.byref(o), _stream(stream, A), arr, len(handles)))
 
 
+def rmq_batch_counted(A, l, r, out, variant=0, k=0, k_con=0, stream=None) -> dict:
+    """rmq_batch_ex through the instrumented query kernel; returns the work
+    counts of the open queries (rmq_scan_stats as a dict).  Waits."""
+    o = _opts(variant, k, k_con)
+    st = rmq_scan_stats()
+    _check(load().rmq_batch_counted(_dptr(A, _i32t(), "A"), A.numel(), _dptr(l, _i32t(), "l"),
+                                    _dptr(r, _i32t(), "r"), l.numel(), _dptr(out, _i32t(), "out"),
+                                    ctypes.byref(o), _stream(stream, A), ctypes.byref(st)))
+    return {f: int(getattr(st, f)) for f, _ in rmq_scan_stats._fields_}
+
+
 def rmq_batch_noalloc(A, l, r, out, k=0, stream=None):
     """Plain-form batch whose table sits in the library's fixed device buffer
     (no device allocation); see include/rmq.h."""
@@ -283,6 +303,14 @@ def rmq_query(h: Handle, l, r, out, stream=None):
                             _dptr(out, _i32t(), "out"), _stream(stream, l)))
 
 
+def rmq_query_host(h: Handle, l, r, out, stream=None):
+    """One request on host buffers (numpy int32; out written in place); waits."""
+    for name, a in (("l", l), ("r", r), ("out", out)):
+        if not (isinstance(a, np.ndarray) and a.dtype == np.int32 and a.flags.c_contiguous):
+            raise ValueError("%s must be a C-contiguous numpy int32 array" % name)
+    _check(load().rmq_query_host(h.ptr, l.ctypes.data, r.ctypes.data, len(l), out.ctypes.data, _stream(stream)))
+
+
 def rmq_query_multi(handles, qs, l, r, out, stream=None):
     """Queries of several requests against resident handles in one launch."""
     H = len(handles)
@@ -308,6 +336,14 @@ class Server:
     def admit(self, A, k=0) -> int:
         i = ctypes.c_int32()
         _check(load().rmq_server_admit(self.ptr, _dptr(A, _i32t(), "A"), A.numel(), int(k), ctypes.byref(i)))
+        self._arrays[i.value] = A
+        return i.value
+
+    def admit_wait(self, A, timeout_s, k=0) -> int:
+        """admit, waiting up to timeout_s seconds for evictions to free budget."""
+        i = ctypes.c_int32()
+        _check(load().rmq_server_admit_wait(self.ptr, _dptr(A, _i32t(), "A"), A.numel(), int(k),
+                                            float(timeout_s), ctypes.byref(i)))
         self._arrays[i.value] = A
         return i.value
 

@@ -98,7 +98,7 @@ def test_workspace_bytes_rejects_bad_arguments(lib):
     assert rmq.rmq_batch_workspace_bytes(100, 0) == 0
 
 
-@pytest.mark.parametrize("n,q", [(1, 1), (1000, 10), (10**6, 1000), (10**8, 10**7), (2**31 - 1, 2**30)])
+@pytest.mark.parametrize("n,q", [(1, 1), (1000, 10), (10**6, 1000), (10**8, 10**7), (2**31 - 1, 2**31 - 1)])
 def test_tune_returns_valid_options(lib, n, q):
     t = rmq.rmq_tune(n, q)
     for k in (t["k"], t["k_con"]):
@@ -124,7 +124,7 @@ def test_host_checks_reject_bad_arguments_before_any_device_work(lib):
     assert lib.rmq_batch(p, 2**31, p, p, 5, p, None) == E              # n too large
     assert lib.rmq_batch(p, 10, None, p, 5, p, None) == E              # null l with q > 0
     assert lib.rmq_batch(p, 10, p, p, -1, p, None) == E                # q < 0
-    assert lib.rmq_batch(p, 10, p, p, 2**30 + 1, p, None) == E         # q too large
+    assert lib.rmq_batch(p, 10, p, p, 2**31, p, None) == E             # q too large (2^31 - 1 is the limit)
     assert lib.rmq_batch_ex(p, 10, p, p, 5, p, ctypes.byref(bad_k), None) == E
     assert lib.rmq_batch_ex(p, 10, p, p, 5, p, ctypes.byref(bad_v), None) == E
     assert lib.rmq_batch_ex(p, 10, p, p, 5, p, ctypes.byref(bad_f), None) == E

@@ -1,0 +1,129 @@
+"""Boundary behaviour of the C ABI on the GPU: per-stream error words, first
+calls from several threads at once, and a batch above q = 2^30."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1706_06940_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1706_06940_gb300 import rmq
+    return rmq
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_error_words_are_per_stream(R, variant):
+    n, q = 50_000, 1000
+    A = torch.from_numpy(W.uniform_array(n, 600, 0, 100)).to(DEV)
+    l, r = W.uniform_queries(n, q, 601)
+    bad_l, bad_r = l.copy(), r.copy()
+    bad_l[17], bad_r[17] = 10, 9
+    s_bad, s_good = torch.cuda.Stream(DEV), torch.cuda.Stream(DEV)
+    outs = []
+    for s, (ll, rr) in ((s_bad, (bad_l, bad_r)), (s_good, (l, r))):
+        with torch.cuda.stream(s):
+            dl, dr = torch.from_numpy(ll).to(DEV), torch.from_numpy(rr).to(DEV)
+            out = torch.full((q,), -7, dtype=torch.int32, device=DEV)
+            R.rmq_batch_ex(A, dl, dr, out, variant=variant, k=256, k_con=64, stream=s.cuda_stream)
+            outs.append(out)
+    # the good stream does not see the bad stream's error, and reading it
+    # does not consume the bad stream's report
+    assert R.rmq_stream_status(s_good.cuda_stream) == R.Status.OK
+    assert R.rmq_stream_status(s_bad.cuda_stream) == R.Status.ERR_QUERY_RANGE
+    assert R.rmq_stream_status(s_bad.cuda_stream) == R.Status.OK          # cleared by the report
+    assert R.rmq_stream_status() == R.Status.OK
+    got_bad, got_good = outs[0].cpu().numpy(), outs[1].cpu().numpy()
+    assert got_bad[17] == -1
+    want = oracle.rmq_naive(A.cpu().numpy(), l, r)
+    assert np.array_equal(got_good, want)
+    keep = np.arange(q) != 17
+    assert np.array_equal(got_bad[keep], want[keep])
+
+
+FIRST_CALLS = r"""
+import sys, threading
+import numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+import oracle
+from paper_1706_06940_gb300 import rmq, workloads as W
+rmq.load()
+torch.cuda.init()
+n, q = 300_000, 5000
+A_host = W.uniform_array(n, 700, 0, 1000)
+A = torch.from_numpy(A_host).cuda()
+l, r = W.uniform_queries(n, q, 701)
+want = oracle.rmq_naive(A_host, l, r)
+dl, dr = torch.from_numpy(l).cuda(), torch.from_numpy(r).cuda()
+torch.cuda.synchronize()
+start = threading.Barrier(8)
+res = [None] * 8
+def work(i):
+    torch.cuda.set_device(0)
+    s = torch.cuda.Stream()
+    out = torch.full((q,), -7, dtype=torch.int32, device="cuda")
+    start.wait()
+    # the first library calls of the process, from 8 threads at once: the
+    # one-time set-up (kernel attributes, occupancy, error words) races here
+    rmq.rmq_batch_ex(A, dl, dr, out, variant=1 + i % 2, k=64 << (i % 4), k_con=32 << (i % 3), stream=s.cuda_stream)
+    st = rmq.rmq_stream_status(s.cuda_stream)
+    res[i] = (st, out.cpu().numpy())
+th = [threading.Thread(target=work, args=(i,)) for i in range(8)]
+for t in th: t.start()
+for t in th: t.join()
+for st, got in res:
+    assert st == rmq.Status.OK, st
+    assert np.array_equal(got, want)
+print("first-calls ok")
+"""
+
+
+def test_first_calls_from_eight_threads(R):
+    oracle.build()
+    p = subprocess.run([sys.executable, "-c", FIRST_CALLS, ROOT], capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stdout[-2000:] + p.stderr[-2000:]
+    assert "first-calls ok" in p.stdout
+
+
+@pytest.mark.slow
+def test_batch_above_2_to_the_30_queries(R):
+    """q = 2^30 + 4099 (the former limit was 2^30): both forms agree on every
+    answer, and a sample matches the oracle, including the last queries."""
+    if torch.cuda.get_device_properties(0).total_memory < 64 * 2**30:
+        pytest.skip("needs about 30 GB of device memory")
+    n = 1_000_003
+    q = 2**30 + 4099
+    A_host = W.uniform_array(n, 800, 0, 1 << 16)
+    A = torch.from_numpy(A_host).to(DEV)
+    g = torch.Generator(device=DEV)
+    g.manual_seed(801)
+    a = torch.randint(0, n, (q,), dtype=torch.int32, device=DEV, generator=g)
+    b = torch.randint(0, n, (q,), dtype=torch.int32, device=DEV, generator=g)
+    l, r = torch.minimum(a, b), torch.maximum(a, b)
+    del a, b
+    out_p = torch.full((q,), -7, dtype=torch.int32, device=DEV)
+    R.rmq_batch_ex(A, l, r, out_p, variant=1, k=1024)
+    assert R.rmq_stream_status() == R.Status.OK
+    out_c = torch.full((q,), -7, dtype=torch.int32, device=DEV)
+    R.rmq_batch_ex(A, l, r, out_c, variant=2, k_con=512)
+    assert R.rmq_stream_status() == R.Status.OK
+    assert torch.equal(out_p, out_c)
+    idx = np.concatenate([np.random.default_rng(802).choice(q, 2000, replace=False), np.arange(q - 64, q)])
+    it = torch.from_numpy(idx).to(DEV)
+    ls, rs = l[it].cpu().numpy(), r[it].cpu().numpy()
+    assert np.array_equal(out_p[it].cpu().numpy(), oracle.rmq_sparse_table(A_host, ls, rs))

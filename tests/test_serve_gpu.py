@@ -111,3 +111,124 @@ def test_query_multi_over_handles(R):
     assert R.rmq_stream_status() == R.Status.OK
     for h in hs:
         h.free()
+
+
+def test_evict_waits_for_its_requests_and_refuses_new_ones(R):
+    """Two threads submit on two arrays while a third evicts one of them and
+    re-admits its data under a new id.  Every accepted request completes with
+    the right answers; once evict has begun, submits on the old id are
+    refused; when evict returns, every accepted request on that id has its
+    answers in its out buffer already."""
+    ns = [2_000_000, 1_500_000]
+    arrays = [W.uniform_array(n, 400 + i, 0, 1 << 20) for i, n in enumerate(ns)]
+    dA = [torch.from_numpy(A).to(DEV) for A in arrays]
+    srv = R.Server(inflight=3, max_batch_queries=1 << 16)
+    ids = [srv.admit(A) for A in dA]
+    rng = np.random.default_rng(11)
+    accepted = []          # (array index, id, ticket, l, r, out)
+    refused = []
+    lock = threading.Lock()
+    evict_started = threading.Event()
+    evicted_done = []
+
+    def producer(h, count, seed):
+        g = np.random.default_rng(seed)
+        for j in range(count):
+            cur = ids[h]
+            q = int(g.integers(1, 5000))
+            l, r = W.uniform_queries(ns[h], q, seed * 1000 + j)
+            out = np.full(q, -7, np.int32)
+            try:
+                t = srv.submit(cur, l, r, out)
+            except R.RmqError as e:
+                assert e.status == R.Status.ERR_INVALID_ARG
+                with lock:
+                    refused.append(cur)
+                continue
+            with lock:
+                accepted.append((h, cur, t, l, r, out))
+
+    def evictor():
+        evict_started.wait()
+        old = ids[0]
+        srv.evict(old)
+        # every request accepted on the old id has completed by now
+        with lock:
+            mine = [a for a in accepted if a[1] == old]
+        evicted_done.append((old, all((a[5] != -7).all() for a in mine), len(mine)))
+        ids[0] = srv.admit(dA[0])
+
+    th = [threading.Thread(target=producer, args=(0, 300, 21)), threading.Thread(target=producer, args=(1, 300, 22)),
+          threading.Thread(target=evictor)]
+    for t in th:
+        t.start()
+    while True:
+        with lock:
+            if len(accepted) >= 60:
+                break
+    evict_started.set()
+    for t in th:
+        t.join()
+    old, complete, n_old = evicted_done[0]
+    assert complete and n_old > 0
+    assert all(x == old for x in refused)
+    for h, _, t, l, r, out in accepted:
+        srv.wait(t)
+        idx = rng.choice(len(l), min(len(l), 24), replace=False)
+        assert np.array_equal(out[idx], oracle.rmq_naive(arrays[h], l[idx], r[idx]))
+    with pytest.raises(R.RmqError):
+        srv.evict(old)                                   # already gone
+    srv.close()
+
+
+def test_invalid_query_is_reported_for_its_request_only(R):
+    n = 100_000
+    A = W.uniform_array(n, 501, 0, 100)
+    dA = torch.from_numpy(A).to(DEV)
+    srv = R.Server(inflight=2)
+    a = srv.admit(dA)
+    reqs = []
+    for j in range(6):
+        l, r = W.uniform_queries(n, 300, 510 + j)
+        if j == 3:
+            l[7], r[7] = 50, 40           # l > r
+            l[9], r[9] = 5, n             # r >= n
+        reqs.append((l, r, np.full(300, -7, np.int32)))
+    tickets = [srv.submit(a, l, r, out) for l, r, out in reqs]
+    for j, t in enumerate(tickets):
+        l, r, out = reqs[j]
+        if j == 3:
+            with pytest.raises(R.RmqError) as ei:
+                srv.wait(t)
+            assert ei.value.status == R.Status.ERR_QUERY_RANGE
+            assert out[7] == -1 and out[9] == -1
+            ok = np.ones(300, bool)
+            ok[[7, 9]] = False
+            assert np.array_equal(out[ok], oracle.rmq_naive(A, l[ok], r[ok]))
+        else:
+            srv.wait(t)
+            assert np.array_equal(out, oracle.rmq_naive(A, l, r))
+    srv.close()
+    # the server's own streams reported the error; the caller's stream is clean
+    assert R.rmq_stream_status() == R.Status.OK
+
+
+def test_admit_wait_gets_memory_freed_by_an_eviction(R):
+    A = torch.from_numpy(W.uniform_array(5_000_000, 83)).to(DEV)
+    B = torch.from_numpy(W.uniform_array(5_000_000, 84)).to(DEV)
+    srv = R.Server(budget_bytes=30_000_000)          # room for one of the two
+    a = srv.admit(A)
+    with pytest.raises(R.RmqError) as ei:
+        srv.admit_wait(B, 0.2)                       # nothing is evicted: times out
+    assert ei.value.status == R.Status.ERR_BUDGET
+    got = []
+    th = threading.Thread(target=lambda: got.append(srv.admit_wait(B, 30.0)))
+    th.start()
+    srv.evict(a)
+    th.join()
+    b = got[0]
+    l, r = W.uniform_queries(5_000_000, 500, 85)
+    out = np.zeros(500, np.int32)
+    srv.wait(srv.submit(b, l, r, out))
+    assert np.array_equal(out, oracle.rmq_naive(B.cpu().numpy(), l, r))
+    srv.close()
