@@ -570,18 +570,59 @@ __device__ __forceinline__ void emit_atomic(uint64_t *H, int64_t s, uint64_t v) 
 // then stored to A_Q in order (coalesced).  Only the first segment (begun in
 // an earlier tile) and the one left open at the end are combined with
 // atomics (those entries were set to KEY_MAX by k_bits_final).
+// A warp's shared memory is 4 KB: the tile, then (once the lanes hold their
+// cells) the slots of at most kSlots segments.  A tile with more marks than
+// that (more than half of its cells are endpoints) stores its segments to A_Q
+// straight from the walk instead.
 __device__ __forceinline__ int swz(int x) { return (x & ~7) | ((x & 7) ^ ((x >> 3) & 7)); }
 
-constexpr int kContractSmem = (kT / 32) * kATile * 8;   // per warp: the tile, then its slots
+constexpr int kSlots = kATile * 4 / 8;                   // 512 slots of 8 bytes in the tile's 4 KB
+constexpr int kContractSmem = (kT / 32) * kATile * 4;    // per warp: the tile, then its slots
+
+// The walk of one lane over its 32 cells (vals), from cell0: the running
+// (value, cell) minimum of the open segment; a marked cell closes the open
+// segment (as its last cell) and opens the next.  Slot k (k from pre) gets
+// the key of the k-th segment the tile closes.  DIRECT: slots are entries
+// s_t + k of H, stored at once, except the lane's first one, returned in
+// `first` (the segmented scan completes it).
+template <bool DIRECT>
+__device__ __forceinline__ void contract_walk(const int32_t (&vals)[32], uint32_t word, uint32_t cell0, uint32_t pre,
+                                              uint64_t *slot, uint64_t *__restrict__ H, int32_t s_t, int32_t m,
+                                              int32_t &cv, uint32_t &cp, uint64_t &first) {
+    cv = INT_MAX;
+    cp = 0;
+    uint32_t k = pre;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        const int32_t vv = vals[c];
+        const bool lt = vv < cv;
+        const int32_t mv = lt ? vv : cv;
+        const uint32_t mp = lt ? (uint32_t)c : cp;
+        const bool b = (word >> c) & 1u;
+        if (DIRECT) {
+            if (b) {
+                const uint64_t key = make_key(mv, cell0 + mp);
+                const int32_t sg = s_t + (int32_t)k;
+                if (k == pre) first = key;
+                else if (sg >= 0 && sg <= m - 2) H[sg] = key;
+            }
+        } else {
+            if (b) slot[k] = make_key(mv, cell0 + mp);
+        }
+        k += b ? 1u : 0u;
+        cv = b ? vv : mv;
+        cp = b ? (uint32_t)c : mp;
+    }
+}
 
 template <bool VEC>
-__global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const uint32_t *__restrict__ BW,
+__global__ void __launch_bounds__(kT, 4) k_contract(SrcI32 src, int64_t n, const uint32_t *__restrict__ BW,
                                                  const uint32_t *__restrict__ BC,
                                                  const int64_t *m_dev, int64_t ntA, uint64_t *__restrict__ H) {
     pdl_wait();
     extern __shared__ uint64_t csmem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint64_t *slot = csmem + (size_t)w * kATile;                      // 1024 slots per warp
+    uint64_t *slot = csmem + (size_t)w * kSlots;                      // the warp's 4 KB: tile, then slots
     int4 *tile = reinterpret_cast<int4 *>(slot);                      // the same memory, first 4 KB
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -651,26 +692,15 @@ __global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const ui
             vals[4 * x] = q4.x; vals[4 * x + 1] = q4.y; vals[4 * x + 2] = q4.z; vals[4 * x + 3] = q4.w;
         }
         __syncwarp();  // the tile is read; its memory now holds the slots
-        // running minimum of the open segment as (value, cell offset); cells
-        // are met in increasing order, so a strict comparison keeps the
-        // leftmost.  A marked cell is the last cell of the open segment (which
-        // is then written to its slot) and the first of the next one.
         const uint32_t cell0 = (uint32_t)(ts + 32 * lane);
-        int32_t cv = INT_MAX;
-        uint32_t cp = 0;
-        uint32_t k = pre;
-#pragma unroll
-        for (int c = 0; c < 32; ++c) {
-            const int32_t vv = vals[c];
-            const bool lt = vv < cv;
-            const int32_t mv = lt ? vv : cv;
-            const uint32_t mp = lt ? (uint32_t)c : cp;
-            const bool b = (word >> c) & 1u;
-            if (b) slot[k] = make_key(mv, cell0 + mp);
-            k += b ? 1u : 0u;
-            cv = b ? vv : mv;
-            cp = b ? (uint32_t)c : mp;
-        }
+        int32_t cv;
+        uint32_t cp;
+        uint64_t first = KEY_MAX;
+        const bool direct = cnt > kSlots;   // warp-uniform
+        if (!direct) contract_walk<false>(vals, word, cell0, pre, slot, H, s_t, m, cv, cp, first);
+        else contract_walk<true>(vals, word, cell0, pre, slot, H, s_t, m, cv, cp, first);
+        // segmented min-scan over the lanes: the part of each lane's first
+        // segment held by the lanes before it
         bool f = nbits != 0;
         uint64_t val = make_key(cv, cell0 + cp);
 #pragma unroll
@@ -684,14 +714,23 @@ __global__ void __launch_bounds__(kT) k_contract(SrcI32 src, int64_t n, const ui
         }
         uint64_t carry_in = __shfl_up_sync(0xffffffffu, val, 1);
         if (lane == 0) carry_in = KEY_MAX;
-        if (nbits) slot[pre] = kmin(slot[pre], carry_in);
         const uint64_t tail = __shfl_sync(0xffffffffu, val, 31);
-        __syncwarp();
-        for (int32_t b = lane; b < cnt; b += 32) {
-            const int32_t sg = s_t + b;
-            if (sg < 0 || sg > m - 2) continue;
-            if (b == 0) emit_atomic(H, sg, slot[0]);
-            else H[sg] = slot[b];
+        if (!direct) {
+            if (nbits) slot[pre] = kmin(slot[pre], carry_in);
+            __syncwarp();
+            for (int32_t b = lane; b < cnt; b += 32) {
+                const int32_t sg = s_t + b;
+                if (sg < 0 || sg > m - 2) continue;
+                if (b == 0) emit_atomic(H, sg, slot[0]);
+                else H[sg] = slot[b];
+            }
+        } else if (nbits) {
+            const int32_t sg = s_t + (int32_t)pre;
+            const uint64_t v0 = kmin(first, carry_in);
+            if (sg >= 0 && sg <= m - 2) {
+                if (pre == 0) emit_atomic(H, sg, v0);
+                else H[sg] = v0;
+            }
         }
         if (lane == 0 && s_n >= 0 && s_n <= m - 2) emit_atomic(H, s_n, tail);
     }

@@ -312,7 +312,7 @@ cudaError_t run_lary(const int32_t *A, int64_t n, int logk, int logell, const in
                      int64_t q, int32_t *out, uint64_t *T, cudaStream_t s);
 
 // Many arrays in one persistent launch (multi.cu).
-constexpr int kMultiMax = 1024;   // arrays per launch (their descriptors travel as a kernel parameter)
+constexpr int kMultiMax = 512;    // arrays per launch (their descriptors travel as a kernel parameter)
 int multi_logk(int64_t n);
 int multi_max_logk();   // the largest block size the multi-array launch accepts
 size_t multi_workspace_bytes(const int64_t *n, const int64_t *q, const int32_t *logk, int H);

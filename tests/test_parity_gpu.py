@@ -407,3 +407,29 @@ def test_metamorphic_k_and_form_do_not_change_answers(R):
                 ref = got
             assert np.array_equal(got, ref), (v, k)
     assert np.array_equal(ref, oracle.rmq_sparse_table(A, l, r))
+
+
+@pytest.mark.parametrize("offset", [0, 1])
+def test_a6_contract_dense_and_sparse_tiles(R, offset):
+    """Tiles of 1024 cells whose marks exceed the warp's 512 slots (every cell
+    an endpoint; exactly 512 and 513 marks) next to sparse tiles, with ties:
+    A_Q matches the oracle's contraction entry by entry."""
+    n = 300_000
+    A = W.uniform_array(n, 903, 0, 7)
+    parts = [np.arange(100_000, 103_072),                     # three whole tiles, every cell marked
+             np.arange(200_704, 200_704 + 512),               # one tile with exactly 512 marks
+             np.arange(204_800, 204_800 + 513),               # one tile with 513 marks
+             np.arange(0, n, 700)]                            # sparse marks elsewhere
+    P = np.unique(np.concatenate(parts)).astype(np.uint32)
+    m = len(P)
+    want = oracle.contract(A, P)
+    buf = torch.zeros(n + offset, dtype=torch.int32, device=DEV)
+    buf[offset:] = dev(A)
+    AQ = torch.zeros(m - 1, dtype=torch.int64, device=DEV)
+    mdev = torch.tensor([m], dtype=torch.int64, device=DEV)
+    R.rmq_contract(buf[offset:], dev(P.view(np.int32)), mdev, m, AQ)
+    torch.cuda.synchronize()
+    assert np.array_equal(keys_pos(AQ), want)
+    # the same marks as query endpoints through the whole contracted batch
+    l, r = P[:-1].astype(np.int32), P[1:].astype(np.int32)
+    check(R, A, l, r, want=oracle.rmq_sparse_table(A, l, r), variants=(R.Variant.CONTRACTED,), kcons=(32, 256))
