@@ -215,6 +215,14 @@ def coarse_lc(nb, cap=4096):
         lc += 1
 
 
+def plain_workspace(n, k):
+    """Device bytes of a plain batch call (the library's rmq_batch_workspace_bytes):
+    levels 0..lc of the block table and one key per 128 cells for k >= 128."""
+    nb = -(-n // k)
+    m1 = -(-n // 128) if k >= 128 else 0
+    return 8 * (nb * (coarse_lc(nb) + 1) + m1)
+
+
 def profiled_traffic(kernel, kernel_src_rel, want):
     """DRAM bytes per launch of `kernel` from a committed ncu summary under
     profiles/ that names it (a line "kernel: <name>"), if it was taken on the
@@ -287,15 +295,22 @@ def coarse_lc_con(nbq):
     return coarse_lc(nbq, cap=6656)
 
 
-def form_bytes(n, q, k, k_con, m, counts):
+def small_block(k, k1):
+    """Cells per small block of the plain form's two-level layout (None: none)."""
+    if k1 is None or k1 == 0:
+        return 128 if k >= 128 else None
+    return None if k1 < 0 else k1
+
+
+def form_bytes(n, q, k, k_con, m, counts, k1=0):
     """Algorithmic bytes of each stage of each form (per call), the kernels
     that run it, and the whole forms' HBM terms (n cells, q queries, block
     sizes k and k_con, m distinct endpoints, counts from rmq_batch_counted).
 
     Plain (Sec. 3.2): A read once (4n), levels 0..lc of the block table
-    written (8 nb (lc + 1)), the minima of every 128 cells when k >= 128
-    (Sec. 3.3), l, r read and out written (12q), and the edge scans: S cells
-    of A (4S) and the 128-cell minima they read.
+    written (8 nb (lc + 1)), the minima of every small block of k1 cells
+    (Sec. 3.3; by default 128 when k >= 128), l, r read and out written (12q),
+    and the edge scans: S cells of A (4S) and the small-block minima they read.
     Contracted (Sec. 3.1): l, r read by the marking (8q) and W bit words
     written (4W, W = ceil(n/32) + 1); the ranks read the words and write their
     counts (8W); the contraction reads A, the words and counts, and writes
@@ -305,7 +320,8 @@ def form_bytes(n, q, k, k_con, m, counts):
     """
     nb = -(-n // k)
     lc = coarse_lc(nb)
-    m1 = -(-n // 128) if k >= 128 else 0
+    sb1 = small_block(k, k1)
+    m1 = -(-n // sb1) if sb1 else 0
     W = -(-n // 32) + 1
     mq = max(m - 1, 1)
     nbq = -(-mq // k_con)
@@ -354,17 +370,22 @@ def run_main(args, dist, rmq, torch, np):
     # block sizes: measured on this batch over 32..4096 (the autotuner), unless given
     tune_ms = {}
     k, k_con = args.k, args.k_con
+    # the autotuner's other choices per form: lanes per partial-block scan and
+    # (plain form) the small blocks of the two-level layout
+    xo = {"plain": {}, "contracted": {}}
     if not k:
         k = rmq.rmq_tune(n, q)["k"]
         if "plain" in forms:
             best, tune_ms["plain"] = rmq.rmq_autotune(dA, dl, dr, outs["plain"], variant=1, k_min=32, k_max=4096)
             k = best["k"]
+            xo["plain"] = {"threads_per_query": best["threads_per_query"], "k1": best["k1"]}
     if not k_con:
         k_con = rmq.rmq_tune(n, q)["k_con"]
         if "contracted" in forms:
             best, tune_ms["contracted"] = rmq.rmq_autotune(dA, dl, dr, outs["contracted"], variant=2, k_min=32,
                                                            k_max=4096)
             k_con = best["k_con"]
+            xo["contracted"] = {"threads_per_query": best["threads_per_query"]}
     nev = {"plain": 4, "contracted": 6}
     vcode = {"plain": rmq.Variant.PLAIN, "contracted": rmq.Variant.CONTRACTED}
     stream = torch.cuda.current_stream(dev)
@@ -377,7 +398,7 @@ def run_main(args, dist, rmq, torch, np):
             flush_l2(flush, flush_rd, it)
             evs[f] = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
             evs[f][0].record(stream)
-            rmq.rmq_batch_ex(dA, dl, dr, outs[f], variant=vcode[f], k=k, k_con=k_con)
+            rmq.rmq_batch_ex(dA, dl, dr, outs[f], variant=vcode[f], k=k, k_con=k_con, **xo[f])
             evs[f][1].record(stream)
         return evs
 
@@ -386,7 +407,7 @@ def run_main(args, dist, rmq, torch, np):
         for f in forms:
             flush_l2(flush, flush_rd, it)
             evs[f] = [torch.cuda.Event(enable_timing=True) for _ in range(nev[f])]
-            rmq.rmq_batch_timed(dA, dl, dr, outs[f], evs[f], variant=vcode[f], k=k, k_con=k_con)
+            rmq.rmq_batch_timed(dA, dl, dr, outs[f], evs[f], variant=vcode[f], k=k, k_con=k_con, **xo[f])
         return evs
 
     for i in range(args.warmup):
@@ -442,7 +463,7 @@ def run_main(args, dist, rmq, torch, np):
     counts = {}
     for f in forms:
         cnt_out = torch.empty(q, dtype=torch.int32, device=dev)
-        counts[f] = rmq.rmq_batch_counted(dA, dl, dr, cnt_out, variant=vcode[f], k=k, k_con=k_con)
+        counts[f] = rmq.rmq_batch_counted(dA, dl, dr, cnt_out, variant=vcode[f], k=k, k_con=k_con, **xo[f])
         if not torch.equal(cnt_out, outs[f]):
             raise RuntimeError("%s form: the instrumented kernel's answers differ" % f)
     ms_step = sum(form_ms.values())
@@ -453,7 +474,7 @@ def run_main(args, dist, rmq, torch, np):
     # per-kernel roofline of every stage, and the dominant kernel
     peak, peak_kind = measured_peak_hbm()
     m = distinct_endpoints(n, l, r)
-    sb, hbm_b, con_min_b, geo = form_bytes(n, q, k, k_con, m, counts)
+    sb, hbm_b, con_min_b, geo = form_bytes(n, q, k, k_con, m, counts, xo["plain"].get("k1", 0))
     per_kernel = []
     for f in forms:
         for s in stage_names[f]:
@@ -474,13 +495,13 @@ def run_main(args, dist, rmq, torch, np):
                            "time of the step" % (dom["stage"], n_staged),
             "traffic": profiled_traffic(dom["kernel"], dom_src, {"n": n, "q": q, "k": k, "k_con": k_con}),
             "per_kernel": per_kernel}
-    ws_bytes = {f: rmq.rmq_batch_workspace_bytes(n, q, vcode[f], k=k, k_con=k_con) for f in forms}
+    ws_bytes = {f: rmq.rmq_batch_workspace_bytes(n, q, vcode[f], k=k, k_con=k_con, **xo[f]) for f in forms}
     hbm_plain = None
     if "plain" in form_ms:
         gbs = hbm_b / (form_ms["plain"] * 1e-3) / 1e9
         hbm_plain = {"algorithmic_bytes": hbm_b, "S_cells": counts["plain"]["scan_elems"], "gbs": gbs,
                      "frac_of_measured": gbs / peak, "frac_of_8tbs_nominal": gbs / 8000.0,
-                     "terms": "4n + 8 nb (lc+1) + 8 ceil(n/128) + 12q + 4S"}
+                     "terms": "4n + 8 nb (lc+1) + 8 ceil(n/k1) + 12q + 4S (k1: small blocks, 128 by default)"}
     hbm_con = None
     if "contracted" in form_ms:
         gbs = con_min_b / (form_ms["contracted"] * 1e-3) / 1e9
@@ -496,12 +517,12 @@ def run_main(args, dist, rmq, torch, np):
         pout = torch.empty(q, dtype=torch.int32).pin_memory()
         hA, hl, hr, ho = pA.numpy(), pl.numpy(), pr.numpy(), pout.numpy()
         for f in forms:                                          # warm the pool
-            rmq.rmq_batch_host(hA, hl, hr, ho, variant=vcode[f], k=k, k_con=k_con)
+            rmq.rmq_batch_host(hA, hl, hr, ho, variant=vcode[f], k=k, k_con=k_con, **xo[f])
         dist.barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             for f in forms:
-                rmq.rmq_batch_host(hA, hl, hr, ho, variant=vcode[f], k=k, k_con=k_con)
+                rmq.rmq_batch_host(hA, hl, hr, ho, variant=vcode[f], k=k, k_con=k_con, **xo[f])
         dt = dist.max(time.perf_counter() - t0)
         e2e = {"value": dist.world * units * args.e2e_steps / dt, "unit": UNIT,
                "h2d_bytes_per_step": len(forms) * (4 * n + 8 * q),
@@ -518,8 +539,8 @@ def run_main(args, dist, rmq, torch, np):
         "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": workload_name(n, q, args.array), "n": n, "q": q, "seed": args.seed,
-                   "forms": forms, "k": k, "k_con": k_con, "k_autotuned": {"range": [32, 4096],
-                                                                       "best_ms": tune_ms},
+                   "forms": forms, "k": k, "k_con": k_con, "tuned_options": xo,
+                   "k_autotuned": {"range": [32, 4096], "best_ms": tune_ms},
                    "l2": "flushed before each form (outside the timed events) by a 256 MiB write, then a 256 MiB "
                          "read of another buffer (the write's dirty lines leave L2 before the form); "
                          "A alone (%.0f MB) exceeds L2" % (4 * n / 1e6),
@@ -559,7 +580,8 @@ def run_config1(args, rmq, torch, np, dev):
     dl, dr = torch.from_numpy(l).to(dev), torch.from_numpy(r).to(dev)
     out = torch.empty(q, dtype=torch.int32, device=dev)
     best, tune_ms = rmq.rmq_autotune(dA, dl, dr, out, variant=0, k_min=32, k_max=4096)
-    opts = dict(variant=int(best["variant"]), k=best["k"], k_con=best["k_con"])
+    opts = dict(variant=int(best["variant"]), k=best["k"], k_con=best["k_con"],
+                threads_per_query=best["threads_per_query"], k1=best["k1"])
     rmq.rmq_batch_ex(dA, dl, dr, out, **opts)
     torch.cuda.synchronize()
     if rmq.rmq_stream_status() != rmq.Status.OK or not np.array_equal(out.cpu().numpy(), oracle.rmq_naive(A, l, r)):
@@ -607,6 +629,7 @@ def run_config1(args, rmq, torch, np, dev):
         raise RuntimeError("config 1: graph replay answers differ from the oracle")
     return {"workload": "plain RMQ: A int32 n=1e6 uniform in [0,2^31), q=1000 uniform queries (l<=r)",
             "choice": {"variant": best["variant"].name, "k": best["k"], "k_con": best["k_con"],
+                       "threads_per_query": best["threads_per_query"], "k1": best["k1"],
                        "autotune_best_ms": tune_ms},
             "call_ms_median": d_ms, "queries_per_s": q / (d_ms * 1e-3),
             "graph_replay_ms_median": g_ms, "graph_queries_per_s": q / (g_ms * 1e-3),
@@ -639,7 +662,8 @@ def run_config3(args, rmq, torch, np, dev, peak):
     m = distinct_endpoints(n, l, r)
     for form, v in (("plain", 1), ("contracted", 2)):
         best, tms = rmq.rmq_autotune(dA, dl, dr, out, variant=v, k_min=32, k_max=4096)
-        opts = dict(variant=v, k=best["k"], k_con=best["k_con"])
+        opts = dict(variant=v, k=best["k"], k_con=best["k_con"], threads_per_query=best["threads_per_query"],
+                    k1=best["k1"])
         times = []
         for i in range(max(5, min(args.steps, 10))):
             flush_l2(flush, flush_rd, i)
@@ -655,17 +679,19 @@ def run_config3(args, rmq, torch, np, dev, peak):
         cnt = rmq.rmq_batch_counted(dA, dl, dr, out, **opts)
         k = best["k"] if form == "plain" else 1024
         k_con = best["k_con"] if form == "contracted" else 256
-        sb, hbm_b, con_min_b, geo = form_bytes(n, q, k, k_con, m, {form: cnt})
-        b = hbm_b if form == "plain" else con_min_b + 8 * cnt["scan_elems"] + 4 * cnt["rank_reads"]
+        sb, hbm_b, con_min_b, geo = form_bytes(n, q, k, k_con, m, {form: cnt}, best["k1"] if form == "plain" else 0)
+        b = hbm_b + 8 * cnt["m1_reads"] if form == "plain" else con_min_b + 8 * cnt["scan_elems"] + 4 * cnt["rank_reads"]
         gbs = b / (ms * 1e-3) / 1e9
         res[form] = {"k": best["k"] if form == "plain" else best["k_con"], "ms": ms,
+                     "threads_per_query": best["threads_per_query"], "k1": best["k1"] if form == "plain" else None,
                      "queries_per_s": q / (ms * 1e-3), "open_query_work": cnt,
                      "algorithmic_bytes": b, "gbs": gbs, "frac_of_measured": gbs / peak}
     bestf = min(res, key=lambda f: res[f]["ms"])
     return {"workload": "tie-heavy and short ranges: A int32 n=1e8 values uniform in [0,1000), q=1e7 queries "
                         "of width log-uniform in [1,1e4], l uniform",
             "best_form": bestf, "queries_per_s": res[bestf]["queries_per_s"], "forms": res,
-            "bytes": "plain: 4n + 8 nb (lc+1) + 8 ceil(n/128) + 12q + 4S (S cells scanned); contracted: the "
+            "bytes": "plain: 4n + 8 nb (lc+1) + 8 ceil(n/k1) + 12q + 4S + 8 M (S cells scanned, M small-block minima "
+                     "read); contracted: the "
                      "measurement model's B_min + 8S (S keys of A_Q scanned) + the rank reads of open queries",
             "l2": "flushed before every timed call", "oracle": "naive oracle on 4000 sampled queries: identical"}
 

@@ -85,6 +85,14 @@ typedef struct {
     int32_t k;         /* block size over A (plain form): 0 = tuned, else a power of 2 in [32, 65536] */
     int32_t k_con;     /* block size over A_Q (contracted form): 0 = tuned, else a power of 2 in [32, 65536] */
     int32_t flags;     /* 0, or RMQ_FLAG_* bits where an entry point allows them */
+    int32_t threads_per_query;  /* lanes that scan one partial block of an open query (Sec. 3.1 step 4):
+                                   0 = tuned (default: teams of 8, 16 or 32 lanes by scan length),
+                                   8, 16 or 32 = teams of at least that many lanes */
+    int32_t k1;        /* small blocks of the two-level layout (Sec. 3.3), plain form: 0 = tuned
+                          (default: 128 cells when k >= 128, none below), -1 = none, else a power
+                          of 2 in [32, k]: the minima of every k1 cells are kept beside the block
+                          table, and a partial block is resolved from them plus at most two
+                          parts of k1 cells */
 } rmq_opts;
 
 /* One array of a multi-array batch: A is a device pointer to n int32 cells;
@@ -352,25 +360,46 @@ rmq_status rmq_batch_lary(const int32_t *A, int64_t n, const int32_t *l, const i
  * arguments (those rmq_batch_ex rejects). */
 int64_t rmq_batch_workspace_bytes(int64_t n, int64_t q, const rmq_opts *opts);
 
-/* The tuner's choice of form and block sizes for (n, q); host only. */
+/* The tuner's choice of options for (n, q); host only.  When rmq_autotune
+ * has remembered choices for several width classes of this shape, this
+ * returns the one of the lowest width class (rmq_tune_batch chooses by a
+ * batch's widths).  Without a remembered choice: the plain form with k near
+ * sqrt(n)/8 (and k_con near sqrt(2q), at most 512), threads_per_query and k1
+ * at their defaults (0). */
 rmq_status rmq_tune(int64_t n, int64_t q, rmq_opts *out);
+
+/* The options an AUTO call (rmq_batch, or rmq_batch_ex with zero fields)
+ * uses for this batch: the remembered choice for its shape and, when the
+ * shape holds choices for several width classes, for the width class of the
+ * batch, which is found from 256 of its queries read back to the host (the
+ * call then waits for `stream`; calls during stream capture skip the read
+ * and take the lowest class).  l, r: device int32[q]. */
+rmq_status rmq_tune_batch(const int32_t *l, const int32_t *r, int64_t q, int64_t n, void *stream, rmq_opts *out);
 
 /* Autotuner (the paper leaves automated selection of k open, Sec. 5):
  * times rmq_batch_ex on this batch for every power-of-two block size in
  * [k_min, k_max] (0, 0 = [32, 4096]) and for the form(s) allowed by
- * `variant` (AUTO = both), and returns the fastest options in *best (and its
+ * `variant` (AUTO = both); then, for the fastest, the lanes per partial-block
+ * scan (threads_per_query 16 and 32 against the default) and, for the plain
+ * form, the small blocks of the two-level layout (k1 none, 32 .. 512, at most
+ * k/2, against the default).  Returns the fastest options in *best (and its
  * time in ms in *best_ms, may be NULL).  Each candidate runs once untimed,
  * then three times, each after a read of twice the L2 size has evicted the
- * batch from L2; its time is the best of the three.  `out` receives answers while it
- * measures.  Waits for the device.  With variant == AUTO the choice is
- * remembered for the (n, q) shape (log2 rounded) and used by rmq_tune,
- * rmq_batch and rmq_build from then on. */
+ * batch from L2; its time is the best of the three.  `out` receives answers
+ * while it measures.  Waits for the device.  With variant == AUTO the choice
+ * is remembered for the batch's shape: (round(log2 n), round(log2 q), width
+ * class = round(log2 of the median width r - l + 1 of 256 sampled queries)),
+ * so that batches of the same n and q but different widths keep separate
+ * choices; rmq_tune, rmq_tune_batch, rmq_batch and rmq_build use them from
+ * then on. */
 rmq_status rmq_autotune(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q,
                         int32_t *out, int32_t variant, int32_t k_min, int32_t k_max, void *stream,
                         rmq_opts *best, float *best_ms);
 
-/* Write / read the remembered choices (text: "log2n log2q variant k k_con"
- * per line).  Loading merges into the current choices. */
+/* Write / read the remembered choices (text, one per line:
+ * "log2n log2q wclass variant k k_con threads_per_query k1"; lines of the
+ * older form "log2n log2q variant k k_con" load as choices that serve every
+ * width class of their shape).  Loading merges into the current choices. */
 rmq_status rmq_tune_save(const char *path);
 rmq_status rmq_tune_load(const char *path);
 

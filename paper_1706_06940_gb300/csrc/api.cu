@@ -162,6 +162,10 @@ rmq_status check_batch_args(const int32_t *A, int64_t n, const int32_t *l, const
         if (opts->k != 0 && !pow2_in_range(opts->k)) return RMQ_ERR_INVALID_ARG;
         if (opts->k_con != 0 && !pow2_in_range(opts->k_con)) return RMQ_ERR_INVALID_ARG;
         if (opts->flags != 0) return RMQ_ERR_INVALID_ARG;
+        const int32_t t = opts->threads_per_query;
+        if (t != 0 && t != 8 && t != 16 && t != 32) return RMQ_ERR_INVALID_ARG;
+        if (opts->k1 != 0 && opts->k1 != -1 && !pow2_in_range(opts->k1)) return RMQ_ERR_INVALID_ARG;
+        if (opts->k1 > 0 && opts->k != 0 && opts->k1 > opts->k) return RMQ_ERR_INVALID_ARG;
     }
     return RMQ_OK;
 }
@@ -172,50 +176,104 @@ rmq_status cuda_status(cudaError_t e) {
     return RMQ_ERR_CUDA;
 }
 
-// Fill zero fields of opts with the tuner's choice.
-rmq_opts resolve_opts(int64_t n, int64_t q, const rmq_opts *opts) {
+bool stream_capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return true;   // unknown: do not read the batch back
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+// The tuner's choice for a batch: the remembered one for its shape, and when
+// the shape holds choices for several width classes and l, r are given (an
+// AUTO call), the one for the batch's width class, from a sample of its
+// queries (not while the stream is being captured: then the lowest class).
+rmq_opts tuned_for(int64_t n, int64_t q, const int32_t *l, const int32_t *r, cudaStream_t s) {
     rmq_opts t;
     rmq_tune(n, q, &t);
-    if (opts) {
-        if (opts->variant != RMQ_VARIANT_AUTO) t.variant = opts->variant;
-        if (opts->k) t.k = opts->k;
-        if (opts->k_con) t.k_con = opts->k_con;
+    rmq_opts m;
+    if (q > 0 && l && r && tuned_lookup(n, q, -1, &m) == TUNE_AMBIGUOUS && !stream_capturing(s)) {
+        const int w = sample_width_class(l, r, q, n, s);
+        if (w >= 0 && tuned_lookup(n, q, w, &m) == TUNE_FOUND) t = m;
     }
     return t;
 }
 
+// Fill zero fields of opts with the tuner's choice.  The batch is sampled
+// only for an AUTO form (l, r may be null).  A choice's threads_per_query and
+// k1 were measured with its form and block size, so they are taken only with
+// those.
+rmq_opts resolve_opts(int64_t n, int64_t q, const rmq_opts *opts, const int32_t *l = nullptr,
+                      const int32_t *r = nullptr, cudaStream_t s = nullptr) {
+    const bool auto_form = !opts || opts->variant == RMQ_VARIANT_AUTO;
+    rmq_opts t = tuned_for(n, q, auto_form ? l : nullptr, auto_form ? r : nullptr, s);
+    if (opts) {
+        if (opts->variant != RMQ_VARIANT_AUTO && opts->variant != t.variant) {
+            t.variant = opts->variant;
+            t.threads_per_query = 0;
+            t.k1 = 0;
+        }
+        if (opts->k) {
+            if (opts->k != t.k) t.k1 = 0;
+            t.k = opts->k;
+        }
+        if (opts->k_con) t.k_con = opts->k_con;
+        if (opts->threads_per_query) t.threads_per_query = opts->threads_per_query;
+        if (opts->k1) t.k1 = opts->k1;
+    }
+    return t;
+}
+
+// Teams of partial-block scans (1, 2 or 4 per warp) for threads_per_query.
+int max_teams_of(int32_t tpq) { return tpq == 32 ? 1 : (tpq == 16 ? 2 : 4); }
+
+// log2 of the small blocks of the two-level layout for k1 and k = 2^logk
+// (-1: none): k1 = 0 is 128 cells when k >= 128.
+int logk1_of(int32_t k1, int logk) {
+    if (k1 < 0) return -1;
+    if (k1 == 0) return logk >= 7 ? 7 : -1;
+    return ilog2_host((uint64_t)k1);
+}
+
 // Keys of a plain batch call's workspace: levels 0..lc of the block table,
-// then, when k >= 128, the 128-cell minima of the two-level layout (Sec. 3.3).
+// then the small-block minima of the two-level layout (Sec. 3.3), one per
+// 2^logk1 cells (none for logk1 < 0).
 int64_t plain_table_keys(int64_t n, int logk) { return two_level_entries(cdiv(n, 1ll << logk)); }
-int64_t plain_m1_keys(int64_t n, int logk) { return logk >= 7 ? cdiv(n, 128) : 0; }
+int64_t plain_m1_keys(int64_t n, int logk1) { return logk1 >= 0 ? cdiv(n, 1ll << logk1) : 0; }
+int64_t plain_workspace_bytes(int64_t n, int logk, int logk1) {
+    return (plain_table_keys(n, logk) + plain_m1_keys(n, logk1)) * 8;
+}
 
 rmq_status batch_plain(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
-                       int logk, cudaStream_t s, Stages *sg, unsigned long long *counts = nullptr) {
+                       int logk, int logk1, int max_teams, cudaStream_t s, Stages *sg,
+                       unsigned long long *counts = nullptr) {
     const int64_t nb = cdiv(n, 1ll << logk);
     Workspace ws;
     const int64_t te = plain_table_keys(n, logk);
-    const int64_t m1 = plain_m1_keys(n, logk);
-    rmq_status st = ws.alloc((size_t)(te + m1) * 8, s);
+    const int64_t m1 = plain_m1_keys(n, logk1);
+    rmq_status st = ws.alloc((size_t)plain_workspace_bytes(n, logk, logk1), s);
     if (st != RMQ_OK) return st;
     uint64_t *T = static_cast<uint64_t *>(ws.p);
     uint64_t *M1 = m1 ? T + te : nullptr;
     cudaError_t e;
     sg->mark(s);
-    if ((e = launch_block_minima_i32(A, n, logk, T, s, M1)) != cudaSuccess) return cuda_status(e);
+    if ((e = launch_block_minima_i32(A, n, logk, T, s, M1, logk1)) != cudaSuccess) return cuda_status(e);
     sg->mark(s);
     if ((e = launch_sparse_table(T, Len{n, nullptr}, logk, nb, s, true)) != cudaSuccess) return cuda_status(e);
     sg->mark(s);
-    e = launch_query_plain(A, n, logk, T, nullptr, l, r, q, out, s, M1, kCoarseCap, counts);
+    e = launch_query_plain(A, n, logk, T, nullptr, l, r, q, out, s, M1, kCoarseCap, counts, logk1, max_teams);
     sg->mark(s);
     return cuda_status(e);
 }
 
 rmq_status batch_contracted(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
-                            int logk_con, cudaStream_t s, Stages *sg, unsigned long long *counts = nullptr) {
+                            int logk_con, int max_teams, cudaStream_t s, Stages *sg,
+                            unsigned long long *counts = nullptr) {
     Workspace ws;
     rmq_status st = ws.alloc(con_workspace_bytes(n, q, logk_con), s);
     if (st != RMQ_OK) return st;
-    return cuda_status(run_contracted(A, n, l, r, q, out, logk_con, ws.p, s, sg, counts));
+    return cuda_status(run_contracted(A, n, l, r, q, out, logk_con, ws.p, s, sg, counts, max_teams));
 }
 
 rmq_status batch_dispatch(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
@@ -223,10 +281,13 @@ rmq_status batch_dispatch(const int32_t *A, int64_t n, const int32_t *l, const i
     rmq_status st = check_batch_args(A, n, l, r, q, out, opts);
     if (st != RMQ_OK) return st;
     if (q == 0) return RMQ_OK;
-    const rmq_opts o = resolve_opts(n, q, opts);
+    const rmq_opts o = resolve_opts(n, q, opts, l, r, s);
+    const int teams = max_teams_of(o.threads_per_query);
     if (o.variant == RMQ_VARIANT_CONTRACTED)
-        return batch_contracted(A, n, l, r, q, out, ilog2_host((uint64_t)o.k_con), s, sg, counts);
-    return batch_plain(A, n, l, r, q, out, ilog2_host((uint64_t)o.k), s, sg, counts);
+        return batch_contracted(A, n, l, r, q, out, ilog2_host((uint64_t)o.k_con), teams, s, sg, counts);
+    if (o.k1 > o.k) return RMQ_ERR_INVALID_ARG;   // small blocks larger than the blocks
+    const int logk = ilog2_host((uint64_t)o.k);
+    return batch_plain(A, n, l, r, q, out, logk, logk1_of(o.k1, logk), teams, s, sg, counts);
 }
 
 }  // namespace
@@ -546,8 +607,9 @@ int64_t rmq_batch_workspace_bytes(int64_t n, int64_t q, const rmq_opts *opts) {
     if (q == 0) return 0;
     const rmq_opts o = resolve_opts(n, q, opts);
     if (o.variant == RMQ_VARIANT_CONTRACTED) return (int64_t)con_workspace_bytes(n, q, ilog2_host((uint64_t)o.k_con));
+    if (o.k1 > o.k) return -1;
     const int logk = ilog2_host((uint64_t)o.k);
-    return (plain_table_keys(n, logk) + plain_m1_keys(n, logk)) * 8;
+    return plain_workspace_bytes(n, logk, logk1_of(o.k1, logk));
 }
 
 // The tuner: a choice measured by rmq_autotune for this (n, q) shape when
@@ -557,11 +619,22 @@ int64_t rmq_batch_workspace_bytes(int64_t n, int64_t q, const rmq_opts *opts) {
 // 512.
 rmq_status rmq_tune(int64_t n, int64_t q, rmq_opts *out) {
     if (!out || n <= 0) return RMQ_ERR_INVALID_ARG;
-    if (q > 0 && tuned_lookup(n, q, out)) return RMQ_OK;   // a measured choice for this shape
+    if (q > 0) {   // a measured choice for this shape (the lowest width class if several)
+        const int st = tuned_lookup(n, q, -1, out);
+        if (st == TUNE_FOUND || (st == TUNE_AMBIGUOUS && tuned_lookup(n, q, 0, out) == TUNE_FOUND)) return RMQ_OK;
+    }
     out->variant = RMQ_VARIANT_PLAIN;
     out->k = 1 << pow2_log_near(std::sqrt((double)n) / 8.0, MIN_LOGK, 12);
     out->k_con = 1 << pow2_log_near(std::sqrt(2.0 * (double)std::max<int64_t>(q, 1)), MIN_LOGK, 9);
     out->flags = 0;
+    out->threads_per_query = 0;
+    out->k1 = 0;
+    return RMQ_OK;
+}
+
+rmq_status rmq_tune_batch(const int32_t *l, const int32_t *r, int64_t q, int64_t n, void *stream, rmq_opts *out) {
+    if (!out || n <= 0 || n > kMaxN || q < 0 || q > kMaxQ || (q > 0 && (!l || !r))) return RMQ_ERR_INVALID_ARG;
+    *out = resolve_opts(n, q, nullptr, l, r, as_stream(stream));
     return RMQ_OK;
 }
 

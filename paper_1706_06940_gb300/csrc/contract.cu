@@ -927,7 +927,8 @@ size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con) {
 
 cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q,
                            int32_t *out, int logk_con, void *ws, cudaStream_t s, Stages *st,
-                           unsigned long long *counts) {
+                           unsigned long long *counts, int max_teams) {
+    if (max_teams != 1 && max_teams != 2 && max_teams != 4) return cudaErrorInvalidValue;
     const int64_t mq_max = std::max<int64_t>(std::min<int64_t>(2 * q, n) - 1, 1);
     const int64_t nbq = cdiv(mq_max, 1ll << logk_con);
     const int64_t lv = coarse_geom(nbq, kCoarseCapCon).lc + 1;
@@ -967,16 +968,16 @@ cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const 
         e = launch_query_two<SrcU64, true, true, true, Count>(di.device, (unsigned)qctas,
                                                               smem + query_ring_bytes<true, true>(), s, src, lenq,
                                                               logk_con, kCoarseCapCon, T, nullptr, l, r, BW, BC, CP, CB,
-                                                              nullptr, n, out, q, nullptr, counts);
+                                                              nullptr, 7, max_teams, n, out, q, nullptr, counts);
     } else if (vecq)
         e = launch_query_two<SrcU64, true, true, true>(di.device, (unsigned)qctas,
                                                        smem + query_ring_bytes<true, true>(), s, src, lenq, logk_con,
-                                                       kCoarseCapCon, T, nullptr, l, r, BW, BC, CP, CB, nullptr, n,
-                                                       out, q, nullptr, no_counts);
+                                                       kCoarseCapCon, T, nullptr, l, r, BW, BC, CP, CB, nullptr, 7,
+                                                       max_teams, n, out, q, nullptr, no_counts);
     else
         e = launch_query_two<SrcU64, true, false, true>(di.device, (unsigned)qctas, smem, s, src, lenq, logk_con,
-                                                        kCoarseCapCon, T, nullptr, l, r, BW, BC, CP, CB, nullptr, n,
-                                                        out, q, nullptr, no_counts);
+                                                        kCoarseCapCon, T, nullptr, l, r, BW, BC, CP, CB, nullptr, 7,
+                                                        max_teams, n, out, q, nullptr, no_counts);
     if (e != cudaSuccess) return e;
     note_launches(1);
     e = cudaGetLastError();

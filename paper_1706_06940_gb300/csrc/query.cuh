@@ -202,18 +202,19 @@ __device__ __forceinline__ uint64_t lane_part_min(const SrcI32 &src, int64_t n, 
     return m;
 }
 
-// Minimum key over A[lo .. hi], a part of one block of k >= 128 cells, with
-// the 128-cell minima M1 of the two-level layout (Sec. 3.3, k1 = 128): the
-// small blocks strictly inside come from M1; an end small block's minimum is
-// taken when it lies in the range, else (and only when it could matter) its
-// part of at most 128 cells is scanned.  Two rounds of loads at most: M1,
-// then the end parts.  The whole warp calls it with the same arguments.
+// Minimum key over A[lo .. hi], a part of one block, with the minima M1 of
+// the small blocks of k1 = 2^logk1 cells of the two-level layout (Sec. 3.3):
+// the small blocks strictly inside come from M1; an end small block's
+// minimum is taken when it lies in the range, else (and only when it could
+// matter) its part of at most k1 cells is scanned.  Two rounds of loads for
+// k1 <= 128 and k / k1 <= 32: M1, then the end parts.  The whole warp calls
+// it with the same arguments.
 template <bool VEC, class Ctr = NoCount>
-__device__ __forceinline__ uint64_t warp_range_min_m1(const SrcI32 &src, const uint64_t *__restrict__ M1,
+__device__ __forceinline__ uint64_t warp_range_min_m1(const SrcI32 &src, const uint64_t *__restrict__ M1, int logk1,
                                                       int64_t n, int64_t lo, int64_t hi, const Ctr &ctr = Ctr{}) {
     const int lane = threadIdx.x & 31;
     const unsigned long long *Mu = reinterpret_cast<const unsigned long long *>(M1);
-    const int64_t ml = lo >> 7, mh = hi >> 7;
+    const int64_t ml = lo >> logk1, mh = hi >> logk1;
     uint64_t best = KEY_MAX;
     bool scan_l = false, scan_r = false;
     int64_t l_end = hi, r_beg = lo;
@@ -222,7 +223,7 @@ __device__ __forceinline__ uint64_t warp_range_min_m1(const SrcI32 &src, const u
         const uint64_t e0 = __ldg(Mu + ml);
         const uint32_t p = key_pos(e0);
         if (p >= lo && p <= hi) return e0;
-        scan_l = true;                              // the whole range, at most 128 cells
+        scan_l = true;                              // the whole range, at most k1 cells
     } else {
         uint64_t inner = KEY_MAX;
         for (int64_t j = ml + 1 + lane; j < mh; j += 32) inner = kmin(inner, __ldg(Mu + j));
@@ -236,8 +237,8 @@ __device__ __forceinline__ uint64_t warp_range_min_m1(const SrcI32 &src, const u
             if (key_pos(er) <= hi) best = er;
             else scan_r = true;
         }
-        l_end = ((ml + 1) << 7) - 1;
-        r_beg = mh << 7;
+        l_end = ((ml + 1) << logk1) - 1;
+        r_beg = mh << logk1;
     }
     uint64_t sc = KEY_MAX;
     if (scan_l) sc = lane_part_min<VEC>(src, n, lo, l_end, ctr);
@@ -254,8 +255,8 @@ __device__ __forceinline__ uint64_t warp_range_min_m1(const SrcI32 &src, const u
 // warp_range_min_m1 instead.
 template <class Src, bool VEC, class Ctr = NoCount>
 __device__ __forceinline__ void warp_drain_scans(const Src &src, int64_t n, bool has, const Pending &p,
-                                                 uint64_t &best, const uint64_t *M1 = nullptr,
-                                                 const Ctr &ctr = Ctr{}) {
+                                                 uint64_t &best, const uint64_t *M1 = nullptr, int logk1 = 7,
+                                                 int max_teams = 4, const Ctr &ctr = Ctr{}) {
     constexpr int EPV = Src::EPV;
     const int lane = threadIdx.x & 31;
     unsigned pend = __ballot_sync(0xffffffffu, has);
@@ -267,6 +268,7 @@ __device__ __forceinline__ void warp_drain_scans(const Src &src, int64_t n, bool
         const uint32_t len = has ? (uint32_t)(p.hi / EPV - p.lo / EPV + 1) : 0u;
         const uint32_t maxlen = __reduce_max_sync(0xffffffffu, len);
         fit = maxlen <= 16u ? 4 : (maxlen <= 32u ? 2 : 1);   // teams whose one round covers it
+        fit = min(fit, max_teams);                           // lanes per scan at least 32 / max_teams
     }
     while (pend) {
         const int cnt = __popc(pend);
@@ -278,14 +280,14 @@ __device__ __forceinline__ void warp_drain_scans(const Src &src, int64_t n, bool
             const uint32_t lb = __shfl_sync(0xffffffffu, p.lb, s);
             uint64_t v;
             if constexpr (EPV == 4) {
-                v = M1 ? warp_range_min_m1<VEC>(src, M1, n, lo, hi, ctr) : warp_scan_min<Src, VEC>(src, n, lo, hi, lb, ctr);
+                v = M1 ? warp_range_min_m1<VEC>(src, M1, logk1, n, lo, hi, ctr) : warp_scan_min<Src, VEC>(src, n, lo, hi, lb, ctr);
             } else {
                 v = warp_scan_min<Src, VEC>(src, n, lo, hi, lb, ctr);
             }
             if (lane == s) best = kmin(best, v);
             continue;
         }
-        const int nteams = cnt >= 4 ? fit : 2;
+        const int nteams = cnt >= 4 ? fit : min(2, fit);
         const int ts = 32 / nteams;                  // lanes per team
         const int team = lane / ts, tl = lane % ts;
         // the scans taken now: the nteams lowest pending lanes
@@ -445,7 +447,7 @@ __device__ __forceinline__ void resolve_queued(const Src src, int64_t n, int log
                                             const uint32_t *__restrict__ BW, const uint32_t *__restrict__ BC,
                                             int32_t *__restrict__ out,
                                             const uint32_t *q_ids, int take, const uint64_t *M1,
-                                            PartPool *pool, const Ctr &ctr) {
+                                            int logk1, int max_teams, PartPool *pool, const Ctr &ctr) {
     const int lane = threadIdx.x & 31;
     const int sh = logk + g.lc;
     const bool has = lane < take;
@@ -510,8 +512,8 @@ __device__ __forceinline__ void resolve_queued(const Src src, int64_t n, int log
             ++w;
         }
     }
-    warp_drain_scans<Src, VEC>(src, n, hl && !defer, pl, best, M1, ctr);
-    warp_drain_scans<Src, VEC>(src, n, hr && !defer, pr, best, M1, ctr);
+    warp_drain_scans<Src, VEC>(src, n, hl && !defer, pl, best, M1, logk1, max_teams, ctr);
+    warp_drain_scans<Src, VEC>(src, n, hr && !defer, pr, best, M1, logk1, max_teams, ctr);
     if (has && !defer) out[qid] = (int32_t)key_pos(best);
     __syncwarp();
 }
@@ -520,7 +522,7 @@ __device__ __forceinline__ void resolve_queued(const Src src, int64_t n, int log
 // ...), then write the pooled queries' answers.  Called by all threads of
 // the CTA, after every warp has finished its queries.
 template <class Src, bool VEC, class Ctr>
-__device__ __forceinline__ void drain_pool(const Src src, int64_t n, const uint64_t *M1, PartPool *pool,
+__device__ __forceinline__ void drain_pool(const Src src, int64_t n, const uint64_t *M1, int logk1, PartPool *pool,
                                            int32_t *__restrict__ out, const Ctr &ctr) {
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -530,7 +532,7 @@ __device__ __forceinline__ void drain_pool(const Src src, int64_t n, const uint6
         if (lo > hi) continue;   // reserved, unused
         uint64_t v;
         if constexpr (Src::EPV == 4) {
-            v = M1 ? warp_range_min_m1<VEC>(src, M1, n, lo, hi, ctr)
+            v = M1 ? warp_range_min_m1<VEC>(src, M1, logk1, n, lo, hi, ctr)
                    : warp_scan_min<Src, VEC>(src, n, lo, hi, pool->lb[p], ctr);
         } else {
             v = warp_scan_min<Src, VEC>(src, n, lo, hi, pool->lb[p], ctr);
@@ -574,9 +576,9 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
                                                     const uint32_t *__restrict__ BW, const uint32_t *__restrict__ BC,
                                                     const uint32_t *__restrict__ CP,
                                                     const uint16_t *__restrict__ CB, const uint64_t *__restrict__ M1,
+                                                    int logk1, int max_teams,
                                                     int64_t n_a, int32_t *__restrict__ out, int64_t q,
                                                     unsigned *err, unsigned long long *counts) {
-    pdl_wait();
     const Ctr ctr{};
     // Phase A answers the queries the coarse table settles.  Each warp queues
     // the others (their indices) in its own shared-memory queue, and as soon
@@ -625,6 +627,10 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
     } else {
         fetch(warp * 128 + lane * 4);
     }
+    // l and r are the caller's: they are requested above, before the wait
+    // for the kernels of this call that build the table (and, for the
+    // contracted form, write the length of A_Q)
+    pdl_wait();
     const int64_t n = len.get();
     const int64_t nb = (n + (1ll << logk) - 1) >> logk;
     const Coarse g = coarse_geom(nb, cap);
@@ -646,7 +652,7 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
     const int sh = logk + g.lc;
     auto resolve = [&](int take) {
         resolve_queued<Src, CON, VEC>(src, n, logk, T, nb, cs, g, L, R, BW, BC, out, my + nq - take, take, M1,
-                                      &pool, ctr);
+                                      logk1, max_teams, &pool, ctr);
         nq -= take;
     };
     int slot = 0;
@@ -728,7 +734,7 @@ k_query_two(Src src, Len len, int logk, int cap, const uint64_t *__restrict__ T,
     }
     if (nq > 0) resolve(nq);
     if (RING) cp_async_wait<0>();   // no copy is left in flight (all were empty)
-    drain_pool<Src, VEC>(src, n, M1, &pool, out, ctr);
+    drain_pool<Src, VEC>(src, n, M1, logk1, &pool, out, ctr);
     if constexpr (Ctr::on) {   // the instrumented kernel: one atomic per warp and counter
 #pragma unroll
         for (int i = 0; i < CNT_N; ++i) {

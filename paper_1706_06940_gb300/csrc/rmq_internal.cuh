@@ -97,6 +97,7 @@ __host__ __device__ __forceinline__ Coarse coarse_geom(int64_t nb, int cap = kCo
 // is a no-op.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+
 template <class... KArgs, class... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
                               Args... args) {
@@ -238,9 +239,10 @@ inline int ilog2_host(uint64_t x) { int t = -1; while (x) { x >>= 1; ++t; } retu
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // Launchers (plain.cu).  All enqueue on `s` and return the launch status.
-// M1 (optional, k >= 128): minima of every 128 cells, ceil(n / 128) entries.
+// M1 (optional): minima of every small block of 2^logk1 cells (5 <= logk1 <=
+// logk), ceil(n / 2^logk1) entries.
 cudaError_t launch_block_minima_i32(const int32_t *A, int64_t n, int logk, uint64_t *T0, cudaStream_t s,
-                                    uint64_t *M1 = nullptr);
+                                    uint64_t *M1 = nullptr, int logk1 = 7);
 cudaError_t launch_block_minima_u64(const uint64_t *AQ, Len len, int64_t n_max, int logk, uint64_t *T0,
                                     cudaStream_t s);
 // The table's block count is nb = ceil(len / 2^logk), read on the device from
@@ -300,10 +302,12 @@ __host__ __device__ inline int64_t bucket_count(int64_t n) { return ((n - 1) >> 
 // counts (optional): 5 device counters; when given, the instrumented kernel
 // runs and adds its work counts there (rmq_scan_stats order; aligned
 // buffers only, else cudaErrorInvalidValue).
+// logk1: the small blocks of M1; max_teams: partial-block scans run by
+// teams of at least 32 / max_teams lanes (1, 2 or 4).
 cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint64_t *T, const uint64_t *Cs,
                                const int32_t *l, const int32_t *r, int64_t q, int32_t *out, cudaStream_t s,
                                const uint64_t *M1 = nullptr, int cap = kCoarseCap,
-                               unsigned long long *counts = nullptr);
+                               unsigned long long *counts = nullptr, int logk1 = 7, int max_teams = 4);
 
 // The l-ary block sparse table (lary.cu): levels of the table for nb blocks
 // and l = 2^logell; the whole batch with the table T (lary_levels * nb keys).
@@ -332,8 +336,17 @@ struct QueryReq {
 cudaError_t launch_query_handles(const QueryReq *reqs, int H, const int32_t *l, const int32_t *r, int32_t *out,
                                  cudaStream_t s);
 
-// Measured choices of the autotuner (tune.cu).
-bool tuned_lookup(int64_t n, int64_t q, rmq_opts *out);
+// Measured choices of the autotuner (tune.cu), remembered per shape
+// (round(log2 n), round(log2 q), width class = round(log2 of the median query
+// width)).  tuned_lookup with wclass < 0: TUNE_AMBIGUOUS when the shape holds
+// choices for several width classes (the batch must be sampled).
+enum : int { TUNE_NONE = 0, TUNE_FOUND = 1, TUNE_AMBIGUOUS = 2 };
+constexpr int kWidthSample = 256;   // queries read back to find a batch's width class
+int tuned_lookup(int64_t n, int64_t q, int wclass, rmq_opts *out);
+int width_class_of(const int32_t *l, const int32_t *r, int64_t count, int64_t n);
+// Width class of a device batch from kWidthSample of its queries (waits for
+// the stream); -1 if they cannot be read.
+int sample_width_class(const int32_t *l, const int32_t *r, int64_t q, int64_t n, cudaStream_t s);
 
 // Device bytes rmq_build allocates for an array of n cells with blocks of
 // 2^logk cells (levels 0 .. lc of the block table and the coarse summary).
@@ -349,7 +362,7 @@ int32_t h_logk(rmq_handle h);
 size_t con_workspace_bytes(int64_t n, int64_t q, int logk_con);
 cudaError_t run_contracted(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q,
                            int32_t *out, int logk_con, void *ws, cudaStream_t s, Stages *st,
-                           unsigned long long *counts = nullptr);
+                           unsigned long long *counts = nullptr, int max_teams = 4);
 cudaError_t sort_endpoints(const int32_t *l, const int32_t *r, int64_t q, int64_t n, uint32_t *pos_out,
                            uint32_t *tag_out, void *ws, size_t ws_bytes, cudaStream_t s);
 size_t sort_workspace_bytes(int64_t q);

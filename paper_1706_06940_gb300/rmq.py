@@ -68,7 +68,8 @@ class rmq_scan_stats(ctypes.Structure):
 
 class rmq_opts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("k", ctypes.c_int32),
-                ("k_con", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("k_con", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("threads_per_query", ctypes.c_int32), ("k1", ctypes.c_int32)]
 
 
 _vp = ctypes.c_void_p
@@ -111,6 +112,7 @@ _SIGS = {
     "rmq_batch_workspace_bytes": (_i64, [_i64, _i64, ctypes.POINTER(rmq_opts)]),
     "rmq_batch_lary": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, _i32, _i32, _vp]),
     "rmq_tune": (_i32, [_i64, _i64, ctypes.POINTER(rmq_opts)]),
+    "rmq_tune_batch": (_i32, [_vp, _vp, _i64, _i64, _vp, ctypes.POINTER(rmq_opts)]),
     "rmq_block_minima": (_i32, [_vp, _i64, _i32, _vp, _vp]),
     "rmq_sparse_table_build": (_i32, [_vp, _i64, _vp]),
     "rmq_sort_endpoints": (_i32, [_vp, _vp, _i64, _i64, _vp, _vp, _vp]),
@@ -152,8 +154,13 @@ def _check(st):
         raise RmqError(st)
 
 
-def _opts(variant=0, k=0, k_con=0, flags=0):
-    return rmq_opts(int(variant), int(k), int(k_con), int(flags))
+def _opts(variant=0, k=0, k_con=0, flags=0, threads_per_query=0, k1=0):
+    return rmq_opts(int(variant), int(k), int(k_con), int(flags), int(threads_per_query), int(k1))
+
+
+def _opts_dict(o) -> dict:
+    return {"variant": Variant(o.variant), "k": o.k, "k_con": o.k_con,
+            "threads_per_query": o.threads_per_query, "k1": o.k1}
 
 
 def _stream(stream, t=None):
@@ -190,14 +197,14 @@ def rmq_batch(A, l, r, out, stream=None):
                             _stream(stream, A)))
 
 
-def rmq_batch_ex(A, l, r, out, variant=0, k=0, k_con=0, stream=None, flags=0):
-    o = _opts(variant, k, k_con, flags)
+def rmq_batch_ex(A, l, r, out, variant=0, k=0, k_con=0, stream=None, flags=0, threads_per_query=0, k1=0):
+    o = _opts(variant, k, k_con, flags, threads_per_query, k1)
     _check(load().rmq_batch_ex(_dptr(A, _i32t(), "A"), A.numel(), _dptr(l, _i32t(), "l"),
                                _dptr(r, _i32t(), "r"), l.numel(), _dptr(out, _i32t(), "out"),
                                ctypes.byref(o), _stream(stream, A)))
 
 
-def rmq_batch_timed(A, l, r, out, events, variant=0, k=0, k_con=0, stream=None):
+def rmq_batch_timed(A, l, r, out, events, variant=0, k=0, k_con=0, stream=None, threads_per_query=0, k1=0):
     """rmq_batch_ex recording torch.cuda.Event objects at the stage boundaries
     (4 for the plain form, 6 for the contracted form)."""
     handles = []
@@ -206,16 +213,16 @@ def rmq_batch_timed(A, l, r, out, events, variant=0, k=0, k_con=0, stream=None):
             ev.record()
         handles.append(ev.cuda_event)
     arr = (ctypes.c_void_p * max(len(handles), 1))(*handles)
-    o = _opts(variant, k, k_con)
+    o = _opts(variant, k, k_con, 0, threads_per_query, k1)
     _check(load().rmq_batch_timed(_dptr(A, _i32t(), "A"), A.numel(), _dptr(l, _i32t(), "l"),
                                   _dptr(r, _i32t(), "r"), l.numel(), _dptr(out, _i32t(), "out"),
                                   ctypes.byref(o), _stream(stream, A), arr, len(handles)))
 
 
-def rmq_batch_counted(A, l, r, out, variant=0, k=0, k_con=0, stream=None) -> dict:
+def rmq_batch_counted(A, l, r, out, variant=0, k=0, k_con=0, stream=None, threads_per_query=0, k1=0) -> dict:
     """rmq_batch_ex through the instrumented query kernel; returns the work
     counts of the open queries (rmq_scan_stats as a dict).  Waits."""
-    o = _opts(variant, k, k_con)
+    o = _opts(variant, k, k_con, 0, threads_per_query, k1)
     st = rmq_scan_stats()
     _check(load().rmq_batch_counted(_dptr(A, _i32t(), "A"), A.numel(), _dptr(l, _i32t(), "l"),
                                     _dptr(r, _i32t(), "r"), l.numel(), _dptr(out, _i32t(), "out"),
@@ -249,12 +256,12 @@ def rmq_launch_count() -> int:
     return int(load().rmq_launch_count())
 
 
-def rmq_batch_host(A, l, r, out, variant=0, k=0, k_con=0, stream=None):
+def rmq_batch_host(A, l, r, out, variant=0, k=0, k_con=0, stream=None, threads_per_query=0, k1=0):
     """Host-buffer batch (numpy int32 arrays, out written in place); waits."""
     for name, a in (("A", A), ("l", l), ("r", r), ("out", out)):
         if not (isinstance(a, np.ndarray) and a.dtype == np.int32 and a.flags.c_contiguous):
             raise ValueError("%s must be a C-contiguous numpy int32 array" % name)
-    o = _opts(variant, k, k_con)
+    o = _opts(variant, k, k_con, 0, threads_per_query, k1)
     st = load().rmq_batch_host(A.ctypes.data, len(A), l.ctypes.data, r.ctypes.data, len(l),
                                out.ctypes.data, ctypes.byref(o), _stream(stream))
     _check(st)
@@ -414,16 +421,24 @@ def rmq_batch_lary(A, l, r, out, k: int, ell: int, stream=None):
                                  int(k), int(ell), _stream(stream, A)))
 
 
-def rmq_batch_workspace_bytes(n: int, q: int, variant=0, k=0, k_con=0) -> int:
+def rmq_batch_workspace_bytes(n: int, q: int, variant=0, k=0, k_con=0, threads_per_query=0, k1=0) -> int:
     """Device workspace of one rmq_batch_ex call (-1 on bad arguments)."""
-    o = _opts(variant, k, k_con)
+    o = _opts(variant, k, k_con, 0, threads_per_query, k1)
     return int(load().rmq_batch_workspace_bytes(int(n), int(q), ctypes.byref(o)))
 
 
 def rmq_tune(n: int, q: int) -> dict:
     o = rmq_opts()
     _check(load().rmq_tune(int(n), int(q), ctypes.byref(o)))
-    return {"variant": Variant(o.variant), "k": o.k, "k_con": o.k_con}
+    return _opts_dict(o)
+
+
+def rmq_tune_batch(l, r, n: int, stream=None) -> dict:
+    """The options an AUTO call uses for this batch (may read 256 of its queries back)."""
+    o = rmq_opts()
+    _check(load().rmq_tune_batch(_dptr(l, _i32t(), "l"), _dptr(r, _i32t(), "r"), l.numel(), int(n),
+                                 _stream(stream, l), ctypes.byref(o)))
+    return _opts_dict(o)
 
 
 def rmq_autotune(A, l, r, out, variant=0, k_min=0, k_max=0, stream=None):
@@ -433,7 +448,7 @@ def rmq_autotune(A, l, r, out, variant=0, k_min=0, k_max=0, stream=None):
     _check(load().rmq_autotune(_dptr(A, _i32t(), "A"), A.numel(), _dptr(l, _i32t(), "l"), _dptr(r, _i32t(), "r"),
                                l.numel(), _dptr(out, _i32t(), "out"), int(variant), int(k_min), int(k_max),
                                _stream(stream, A), ctypes.byref(o), ctypes.byref(ms)))
-    return {"variant": Variant(o.variant), "k": o.k, "k_con": o.k_con}, ms.value
+    return _opts_dict(o), ms.value
 
 
 def rmq_tune_save(path):

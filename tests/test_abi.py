@@ -68,15 +68,14 @@ def test_plain_workspace_between_level_zero_and_the_full_table(lib, n, k):
 
 
 @pytest.mark.parametrize("n,k", [(10**8, 1024), (10**8, 512), (10**9, 2048), (5000, 32), (1, 64),
-                                 (510 * 32, 32), (511 * 32, 32)])
+                                 (510 * 32, 32), (511 * 32, 32), (1000, 128), (1024, 128), (2**20, 128),
+                                 (2**31 - 1, 65536), (3 * 10**6, 256)])
 def test_bench_table_geometry_matches_the_library(lib, n, k):
     """bench.py counts the plain form's bytes with its own copy of the coarse
     geometry; it must give the library's workspace exactly."""
     import bench
-    nb = -(-n // k)
-    m1 = -(-n // 128) if k >= 128 else 0
     want = rmq.rmq_batch_workspace_bytes(n, 1000, rmq.Variant.PLAIN, k=k)
-    assert 8 * (nb * (bench.coarse_lc(nb) + 1) + m1) == want
+    assert bench.plain_workspace(n, k) == want
 
 
 def test_contracted_workspace_holds_the_bitmap_and_a_q(lib):
@@ -142,20 +141,55 @@ def test_host_checks_reject_bad_arguments_before_any_device_work(lib):
 def test_tune_table_load_save_roundtrip(lib, tmp_path):
     rmq.rmq_tune_clear()
     base = rmq.rmq_tune(10**8, 10**7)
+    assert base["threads_per_query"] == 0 and base["k1"] == 0
     p = tmp_path / "tune.txt"
+    # the older five-field line: a choice that serves every width class of its shape
     p.write_text("# log2n log2q variant k k_con\n27 23 2 2048 256\n")
     rmq.rmq_tune_load(p)
     t = rmq.rmq_tune(10**8, 10**7)                   # log2 1e8 ~ 26.6 -> 27, log2 1e7 ~ 23.3 -> 23
-    assert t == {"variant": rmq.Variant.CONTRACTED, "k": 2048, "k_con": 256}
+    assert t == {"variant": rmq.Variant.CONTRACTED, "k": 2048, "k_con": 256, "threads_per_query": 0, "k1": 0}
+    rmq.rmq_tune_clear()
+    # two width classes of one shape; rmq_tune gives the lowest class
+    p.write_text("# log2n log2q wclass variant k k_con threads_per_query k1\n"
+                 "27 23 25 1 1024 256 8 -1\n27 23 7 2 1024 32 16 0\n")
+    rmq.rmq_tune_load(p)
+    assert rmq.rmq_tune(10**8, 10**7) == {"variant": rmq.Variant.CONTRACTED, "k": 1024, "k_con": 32,
+                                          "threads_per_query": 16, "k1": 0}
     assert rmq.rmq_tune(10**6, 10**3) == rmq.rmq_tune(10**6, 10**3)
     out = tmp_path / "saved.txt"
     rmq.rmq_tune_save(out)
-    assert "27 23 2 2048 256" in out.read_text()
+    text = out.read_text()
+    assert "27 23 25 1 1024 256 8 -1" in text and "27 23 7 2 1024 32 16 0" in text
     rmq.rmq_tune_clear()
     assert rmq.rmq_tune(10**8, 10**7) == base
-    bad = tmp_path / "bad.txt"
-    bad.write_text("27 23 2 2047 256\n")
-    with pytest.raises(rmq.RmqError):
-        rmq.rmq_tune_load(bad)
+    rmq.rmq_tune_load(out)                            # what was saved loads back
+    assert rmq.rmq_tune(10**8, 10**7)["k_con"] == 32
+    rmq.rmq_tune_clear()
+    for bad_line in ("27 23 2 2047 256\n",           # k not a power of two
+                     "27 23 7 1 1024 256 12 0\n",     # threads_per_query not 8, 16 or 32
+                     "27 23 7 1 256 256 0 512\n",     # k1 > k
+                     "27 23\n"):
+        bad = tmp_path / "bad.txt"
+        bad.write_text(bad_line)
+        with pytest.raises(rmq.RmqError):
+            rmq.rmq_tune_load(bad)
     with pytest.raises(rmq.RmqError):
         rmq.rmq_tune_load(tmp_path / "missing.txt")
+
+
+def test_new_option_fields_are_checked_before_device_work(lib):
+    p = ctypes.c_void_p(16)  # never dereferenced: the checks fail first
+    E = rmq.Status.ERR_INVALID_ARG
+    for o in (rmq.rmq_opts(0, 0, 0, 0, 12, 0),      # threads_per_query not 8, 16 or 32
+              rmq.rmq_opts(0, 0, 0, 0, 0, 48),      # k1 not a power of two
+              rmq.rmq_opts(0, 0, 0, 0, 0, 16),      # k1 below 32
+              rmq.rmq_opts(1, 256, 0, 0, 0, 512),   # k1 > k
+              rmq.rmq_opts(0, 0, 0, 0, 0, -2)):
+        assert lib.rmq_batch_ex(p, 10, p, p, 5, p, ctypes.byref(o), None) == E
+    assert rmq.rmq_batch_workspace_bytes(10**6, 100, variant=1, k=256, k1=512) == -1
+    # k1 sizes the small-block minima of the plain form
+    base = rmq.rmq_batch_workspace_bytes(10**6, 100, variant=1, k=1024, k1=-1)
+    assert rmq.rmq_batch_workspace_bytes(10**6, 100, variant=1, k=1024, k1=32) == base + 8 * (10**6 // 32)
+    assert rmq.rmq_batch_workspace_bytes(10**6, 100, variant=1, k=1024) == base + 8 * (-(-10**6 // 128))
+    assert rmq.rmq_batch_workspace_bytes(10**6, 100, variant=1, k=64) == \
+        rmq.rmq_batch_workspace_bytes(10**6, 100, variant=1, k=64, k1=-1)

@@ -433,3 +433,54 @@ def test_a6_contract_dense_and_sparse_tiles(R, offset):
     # the same marks as query endpoints through the whole contracted batch
     l, r = P[:-1].astype(np.int32), P[1:].astype(np.int32)
     check(R, A, l, r, want=oracle.rmq_sparse_table(A, l, r), variants=(R.Variant.CONTRACTED,), kcons=(32, 256))
+
+
+@pytest.mark.parametrize("nb,k", [(3001, 128), (6007, 256), (12001, 128), (25013, 512), (50021, 128),
+                                  (100003, 128), (2041, 1024), (130_000, 256)])
+def test_coarse_shifts_three_to_eight(R, nb, k):
+    """Plain batches whose coarse blocks hold 2^3 .. 2^8 blocks (up to 508
+    coarse blocks), with a short last block, ties, uniform and short queries,
+    aligned and unaligned arrays: answers match the oracle."""
+    n = (nb - 1) * k + 1 + (nb * 7) % (k - 1)
+    A = W.uniform_array(n, nb + k, 0, 50)
+    l, r = W.uniform_queries(n, 20_000, nb + 1)
+    l[:5000], r[:5000] = W.log_width_queries(n, 5000, nb + 2, 1, 4 * k)
+    l[5000], r[5000] = 0, n - 1
+    l[5001], r[5001] = n - 1, n - 1
+    check(R, A, l, r, want=oracle.rmq_sparse_table(A, l, r), variants=(R.Variant.PLAIN,), ks=(k,), offsets=(0, 1))
+
+
+@pytest.mark.parametrize("k,k1", [(64, 32), (128, 32), (128, 64), (256, 32), (256, 128), (1024, 32), (1024, 64),
+                                  (1024, 256), (1024, 512), (4096, 256), (4096, 4096), (64, 64), (1024, -1)])
+@pytest.mark.parametrize("hi", [1000, 2**31])
+def test_small_blocks_k1(R, k, k1, hi):
+    """The two-level layout with small blocks of k1 cells (Sec. 3.3), from
+    k1 = 32 to k1 = k and without small blocks: tie-heavy short ranges,
+    uniform ranges, a short last block and unaligned arrays; answers match the
+    oracle, and the instrumented kernel reads small-block minima exactly when
+    k1 is in use."""
+    n = 777_777 + k // 3
+    A = W.uniform_array(n, k + k1 + hi % 7, 0, hi)
+    l, r = W.log_width_queries(n, 40_000, k + 1, 1, 4 * k)
+    l[:8000], r[:8000] = W.uniform_queries(n, 8000, k + 2)
+    l[8000], r[8000] = 0, n - 1
+    for off in (0, 1):
+        got, st = run_batch_k1(R, A, l, r, k, k1, off)
+        assert st == R.Status.OK
+        assert np.array_equal(got, oracle.rmq_sparse_table(A, l, r)), (k, k1, off)
+    dA, dl, dr = dev(A), dev(l), dev(r)
+    out = torch.empty(len(l), dtype=torch.int32, device=DEV)
+    cnt = R.rmq_batch_counted(dA, dl, dr, out, variant=1, k=k, k1=k1)
+    assert (cnt["m1_reads"] > 0) == (k1 > 0), cnt
+
+
+def run_batch_k1(R, A, l, r, k, k1, offset):
+    n, q = len(A), len(l)
+    bufA = torch.zeros(n + offset, dtype=torch.int32, device=DEV)
+    bufA[offset:] = dev(A)
+    bl = torch.zeros(q + offset, dtype=torch.int32, device=DEV)
+    br = torch.zeros(q + offset, dtype=torch.int32, device=DEV)
+    bo = torch.full((q + offset,), -7, dtype=torch.int32, device=DEV)
+    bl[offset:], br[offset:] = dev(l), dev(r)
+    R.rmq_batch_ex(bufA[offset:], bl[offset:], br[offset:], bo[offset:], variant=1, k=k, k1=k1)
+    return bo[offset:].cpu().numpy(), R.rmq_stream_status()
