@@ -72,6 +72,11 @@ def _load():
     lib.oracle_lary_block_table.argtypes = [_i32p, _i64, _i64, _i64, _i32p]
     lib.oracle_lary_query.restype = None
     lib.oracle_lary_query.argtypes = [_i32p, _i64, _i64, _i64, _i32p, _i32p, _i32p, _i64, _i32p, _i32p]
+    _i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+    lib.oracle_hlevel_space.restype = ctypes.c_int64
+    lib.oracle_hlevel_space.argtypes = [_i64, _i64p, ctypes.c_int]
+    lib.oracle_hlevel_query.restype = ctypes.c_int
+    lib.oracle_hlevel_query.argtypes = [_i32p, _i64, _i64p, ctypes.c_int, _i32p, _i32p, _i64, _i32p, _i64p]
     _lib = lib
     return lib
 
@@ -207,3 +212,22 @@ def lary_query(A, k: int, ell: int, l, r):
     used = np.empty(len(l), dtype=np.int32)
     _load().oracle_lary_query(A, len(A), int(k), int(ell), T, l, r, len(l), out, used)
     return out, used
+
+
+def hlevel_space(n: int, ks) -> int:
+    """Entries kept by the multi-level structure of Sec. 3.3 with block sizes
+    ks = (k_1, ..., k_h) (-1 on bad parameters)."""
+    ks = np.ascontiguousarray(ks, dtype=np.int64)
+    return int(_load().oracle_hlevel_space(int(n), ks, len(ks)))
+
+
+def hlevel_query(A, ks, l, r):
+    """Answers through the multi-level structure of Sec. 3.3 (block sizes ks),
+    and the work of each query (cells scanned, minima and table values read)."""
+    A, l, r = _i32(A), _i32(l), _i32(r)
+    ks = np.ascontiguousarray(ks, dtype=np.int64)
+    out = np.empty(len(l), dtype=np.int32)
+    work = np.empty(len(l), dtype=np.int64)
+    if _load().oracle_hlevel_query(A, len(A), ks, len(ks), l, r, len(l), out, work) != 0:
+        raise ValueError("bad block sizes for the multi-level structure")
+    return out, work

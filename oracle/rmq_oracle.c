@@ -403,3 +403,121 @@ ORACLE_API void oracle_lary_query(const int32_t *A, int64_t n, int64_t k, int64_
         if (lookups) lookups[i] = used;
     }
 }
+
+/*
+ * The multi-level block-based sparse table of Sec. 3.3: block sizes
+ * k_1 < k_2 < ... < k_h, each dividing the next.  The minima of the
+ * non-overlapping blocks of size k_i are kept for 1 <= i < h, and for
+ * blocks of size k_h their minima, doubles, quadruples and so on (the
+ * sparse table of Sec. 3.1 step 3 over blocks of k_h).  Space in entries:
+ * n/k_1 + ... + n/k_{h-1} + (n/k_h)(floor(log2(n/k_h)) + 1), block counts
+ * rounded up.  ks[0 .. h-1] = k_1 .. k_h.  Returns -1 on bad parameters
+ * (h < 1, k_1 < 1, or some k_i not dividing k_{i+1}).
+ */
+ORACLE_API int64_t oracle_hlevel_space(int64_t n, const int64_t *ks, int h)
+{
+    if (n <= 0 || h < 1 || ks[0] < 1) return -1;
+    for (int i = 0; i + 1 < h; ++i)
+        if (ks[i + 1] <= ks[i] || ks[i + 1] % ks[i] != 0) return -1;
+    int64_t words = 0;
+    for (int i = 0; i + 1 < h; ++i) words += (n + ks[i] - 1) / ks[i];
+    int64_t nb = (n + ks[h - 1] - 1) / ks[h - 1];
+    return words + nb * oracle_sparse_levels(nb);
+}
+
+/*
+ * Leftmost minimum position of A[a .. b], a part lying inside one block of
+ * level lev (blocks of ks[lev - 1] cells; M[i - 1] holds the minima of the
+ * blocks of level i, i < h).  At level 1 the part is scanned.  Otherwise the
+ * blocks of level lev - 1 lying wholly inside the part give their minima, and
+ * the cells before the first and after the last of them form at most two
+ * parts of level lev - 1, resolved one level down: the "checking of up to
+ * two blocks" of Sec. 3.3, at cost k_lev / k_{lev-1} per level and k_1 at the
+ * bottom.  *work counts the cells scanned and the minima read.
+ */
+static int32_t hlevel_part(const int32_t *A, int32_t *const *M, const int64_t *ks, int lev, int64_t a, int64_t b,
+                           int64_t *work)
+{
+    if (lev == 1) {
+        *work += b - a + 1;
+        return scan_min(A, a, b);
+    }
+    int64_t s = ks[lev - 2];           /* block size of level lev - 1 */
+    int64_t first = (a + s - 1) / s;   /* first block of level lev - 1 starting at or after a */
+    int64_t last = (b + 1) / s;        /* blocks first .. last - 1 end at or before b */
+    if (first >= last) {               /* no whole block inside: one or two parts one level down */
+        if (a / s == b / s) return hlevel_part(A, M, ks, lev - 1, a, b, work);
+        int32_t x = hlevel_part(A, M, ks, lev - 1, a, (a / s + 1) * s - 1, work);
+        return lex_min(A, x, hlevel_part(A, M, ks, lev - 1, (b / s) * s, b, work));
+    }
+    int32_t best = -1;
+    if (a < first * s) best = hlevel_part(A, M, ks, lev - 1, a, first * s - 1, work);
+    for (int64_t j = first; j < last; ++j) {
+        int32_t p = M[lev - 2][j];
+        best = best < 0 ? p : lex_min(A, best, p);
+        ++*work;
+    }
+    if (last * s <= b) best = lex_min(A, best, hlevel_part(A, M, ks, lev - 1, last * s, b, work));
+    return best;
+}
+
+/*
+ * Queries over the multi-level structure (Sec. 3.3), in the paper's order:
+ * the block minima of every level i < h, written as their definition (a scan
+ * of each block); the sparse table over blocks of k_h (a scan of each span);
+ * then each query: with bl = l / k_h and br = r / k_h, the inner span of
+ * blocks bl+1 .. br-1 from two overlapping table lookups at level
+ * t = floor(log2(br - bl - 1)) (Sec. 3.1 step 4), and the two end parts, each
+ * inside one block of k_h, resolved down the levels (hlevel_part); a query
+ * inside one block of k_h is one such part.  work (may be NULL) receives per
+ * query the cells scanned, minima read and table values used.  Returns -1 on
+ * bad parameters or when memory cannot be had.  Invalid queries answer -1.
+ */
+ORACLE_API int oracle_hlevel_query(const int32_t *A, int64_t n, const int64_t *ks, int h,
+                                   const int32_t *l, const int32_t *r, int64_t q, int32_t *out, int64_t *work)
+{
+    if (oracle_hlevel_space(n, ks, h) < 0 || h > 16) return -1;
+    int32_t *M[16] = {0};
+    int rc = 0;
+    for (int i = 0; i + 1 < h && rc == 0; ++i) {
+        int64_t nbi = (n + ks[i] - 1) / ks[i];
+        M[i] = (int32_t *)malloc((size_t)nbi * sizeof(int32_t));
+        if (!M[i]) { rc = -1; break; }
+        oracle_block_minima(A, n, ks[i], M[i]);
+    }
+    int64_t kh = ks[h - 1];
+    int64_t nb = (n + kh - 1) / kh;
+    int levels = oracle_sparse_levels(nb);
+    int32_t *T = rc == 0 ? (int32_t *)malloc((size_t)(nb * levels) * sizeof(int32_t)) : NULL;
+    if (!T) rc = -1;
+    if (rc == 0) {
+        oracle_block_sparse_table(A, n, kh, T);
+        for (int64_t i = 0; i < q; ++i) {
+            int64_t wk = 0;
+            if (!valid_query(n, l[i], r[i])) {
+                out[i] = -1;
+                if (work) work[i] = 0;
+                continue;
+            }
+            int64_t bl = l[i] / kh, br = r[i] / kh;
+            int32_t best;
+            if (bl == br) {
+                best = hlevel_part(A, M, ks, h, l[i], r[i], &wk);
+            } else {
+                best = hlevel_part(A, M, ks, h, l[i], (bl + 1) * kh - 1, &wk);
+                if (br - bl >= 2) {
+                    int t = ilog2_u64((uint64_t)(br - bl - 1));
+                    best = lex_min(A, best, T[(int64_t)t * nb + bl + 1]);
+                    best = lex_min(A, best, T[(int64_t)t * nb + br - ((int64_t)1 << t)]);
+                    wk += 2;
+                }
+                best = lex_min(A, best, hlevel_part(A, M, ks, h, br * kh, r[i], &wk));
+            }
+            out[i] = best;
+            if (work) work[i] = wk;
+        }
+    }
+    for (int i = 0; i < 16; ++i) free(M[i]);
+    free(T);
+    return rc;
+}

@@ -384,3 +384,148 @@ def test_pins_reject_planted_mutants(mutant):
         if caught:
             break
     assert caught, mutant.__name__
+
+
+# ---------------------------------------------------------------- multi-level BbST (Sec. 3.3)
+
+HLEVEL_KS = [(1,), (2,), (1, 2), (1, 3), (2, 4), (1, 2, 4), (1, 3, 6), (2, 4, 8), (1, 2, 4, 8)]
+
+
+@pytest.mark.parametrize("n", range(1, 9))
+def test_hlevel_query_exhaustive(n):
+    """Every array of length <= 8 over {0, 1, 2}, every range, block sizes of
+    one to four levels (ks with k_1 = 1 scan nothing at the bottom): the same
+    answers as the brute force."""
+    l, r = all_ranges(n)
+    arrays = itertools.product((0, 1, 2), repeat=n)
+    if n == 8:                      # 3^8 arrays: take every fifth
+        arrays = itertools.islice(arrays, 0, None, 5)
+    for A in arrays:
+        A = np.array(A, dtype=np.int32)
+        want = brute(A, l, r)
+        for ks in HLEVEL_KS:
+            got, _ = oracle.hlevel_query(A, ks, l, r)
+            assert np.array_equal(got, want), (A, ks)
+
+
+@pytest.mark.parametrize("n,ks,hi", [(50_000, (8, 64), 100), (50_000, (4, 32, 256), 3),
+                                     (65_536, (16, 256, 4096), 2**31 - 1), (99_991, (32, 96, 192, 1536), 50),
+                                     (7_000, (64, 128, 8192), 9), (123_457, (128, 1024), 1000)])
+def test_hlevel_query_random_and_work_bound(n, ks, hi):
+    """Uniform and short ranges against the (pinned) naive scan; every query
+    reads at most two end parts of k_h / k_{h-1} + ... + k_2 / k_1 + k_1
+    values each, plus two table values (the Sec. 3.3 cost of checking up to
+    two blocks)."""
+    A = W.uniform_array(n, 91 + len(ks), 0, hi)
+    l, r = W.uniform_queries(n, 4_000, 92)
+    ls, rs = W.log_width_queries(n, 4_000, 93, 1, 5 * ks[-1])
+    l, r = np.concatenate([l, ls]), np.concatenate([r, rs])
+    got, work = oracle.hlevel_query(A, ks, l, r)
+    assert np.array_equal(got, oracle.rmq_naive(A, l, r))
+    chain = ks[0] + sum(ks[i] // ks[i - 1] for i in range(1, len(ks)))
+    assert work.max() <= 2 * chain + 2
+    assert work.min() >= 1
+
+
+def test_hlevel_work_on_aligned_spans():
+    """A query covering whole blocks of k_h reads exactly k_h / k_{h-1}
+    minima in each end block plus two table values; one covering a single
+    whole block of k_1 reads its one minimum, and one inside a block of k_1
+    that covers no whole block scans exactly its cells."""
+    n = 1 << 15
+    A = W.uniform_array(n, 97, 0, 1 << 20)
+    for ks in ((4, 64), (8, 32, 512), (16, 64, 256, 2048)):
+        kh, kp = ks[-1], ks[-2]
+        for bl, br in ((0, 5), (3, 4), (7, n // kh - 1)):
+            l = np.array([bl * kh], np.int32)
+            r = np.array([(br + 1) * kh - 1], np.int32)
+            got, work = oracle.hlevel_query(A, ks, l, r)
+            assert got[0] == oracle.rmq_naive(A, l, r)[0]
+            assert work[0] == 2 * (kh // kp) + (2 if br - bl >= 2 else 0), (ks, bl, br)
+        l = np.array([3 * ks[0]], np.int32)
+        got, work = oracle.hlevel_query(A, ks, l, l + ks[0] - 1)
+        assert work[0] == 1 and got[0] == 3 * ks[0] + int(np.argmin(A[3 * ks[0]:4 * ks[0]]))
+        got, work = oracle.hlevel_query(A, ks, l + 1, l + ks[0] - 1)
+        assert work[0] == ks[0] - 1 and got[0] == 3 * ks[0] + 1 + int(np.argmin(A[3 * ks[0] + 1:4 * ks[0]]))
+
+
+def test_hlevel_space_closed_form_and_bad_parameters():
+    """n/k_1 + ... + n/k_{h-1} + (n/k_h)(floor(log2(n/k_h)) + 1), block counts
+    rounded up; -1 when some k_i does not divide k_{i+1} or the sizes do not grow."""
+    for n in (1, 1000, 10**8, 10**9):
+        for ks in ((1,), (64,), (32, 1024), (512, 4096, 65536), (2, 6, 12, 48)):
+            nb = -(-n // ks[-1])
+            want = sum(-(-n // k) for k in ks[:-1]) + nb * (nb.bit_length())
+            assert oracle.hlevel_space(n, ks) == want, (n, ks)
+    # one level is the block sparse table of Sec. 3.2 (Table 2's count)
+    assert oracle.hlevel_space(10**8, (4096,)) == 24415 * 15
+    for bad in ((4, 6), (8, 4), (4, 4), (0, 4), ()):
+        assert oracle.hlevel_space(100, bad) == -1
+    with pytest.raises(ValueError):
+        oracle.hlevel_query(np.zeros(10, np.int32), (3, 4), [0], [1])
+
+
+def _hlevel_py(A, ks, l, r, slip):
+    """The multi-level query of Sec. 3.3 in Python with one planted slip, used
+    only to show that the exhaustive pin rejects each slip."""
+    A = [int(x) for x in A]
+    n, h = len(A), len(ks)
+    M = [[b * k + min(range(min(k, n - b * k)), key=lambda t: (A[b * k + t], t))
+          for b in range(-(-n // k))] for k in ks]
+
+    def better(x, y):
+        if slip == "ties_right":
+            return x if A[x] < A[y] else y
+        return x if (A[x], x) <= (A[y], y) else y
+
+    def part(lev, a, b):
+        if lev == 1:
+            return min(range(a, b + 1), key=lambda t: (A[t], t))
+        s = ks[lev - 2]
+        first, last = -(-a // s), (b + 1) // s
+        if slip == "last_floor":
+            last = b // s + 1
+        if first >= last:
+            if a // s == b // s:
+                return part(lev - 1, a, b)
+            x = part(lev - 1, a, (a // s + 1) * s - 1)
+            return x if slip == "drop_split" else better(x, part(lev - 1, (b // s) * s, b))
+        best = part(lev - 1, a, first * s - 1) if a < first * s else None
+        for j in range(first, last):
+            best = M[lev - 2][j] if best is None else better(best, M[lev - 2][j])
+        if last * s <= b and slip != "drop_tail":
+            best = better(best, part(lev - 1, last * s, b))
+        return best
+
+    kh = ks[-1]
+    out = []
+    for lo, hi in zip(l, r):
+        bl, br = lo // kh, hi // kh
+        if bl == br:
+            out.append(part(h, lo, hi))
+            continue
+        best = part(h, lo, (bl + 1) * kh - 1)
+        for j in range(bl + 1, br + (1 if slip == "inner_past_end" else 0)):
+            best = better(best, M[h - 1][j])
+        out.append(better(best, part(h, br * kh, hi)))
+    return np.array(out, dtype=np.int32)
+
+
+@pytest.mark.parametrize("slip", [None, "ties_right", "last_floor", "drop_split", "drop_tail", "inner_past_end"])
+def test_hlevel_pins_reject_planted_slips(slip):
+    """The Python restatement agrees with the brute force without a slip, and
+    each slip in the level descent fails the exhaustive pin."""
+    caught = False
+    for n in range(1, 9):
+        l, r = all_ranges(n)
+        for A in itertools.product((0, 1, 2), repeat=n):
+            A = np.array(A, dtype=np.int32)
+            for ks in ((1, 2), (1, 2, 4), (2, 4)):
+                if not np.array_equal(_hlevel_py(A, ks, l, r, slip), brute(A, l, r)):
+                    caught = True
+                    break
+            if caught:
+                break
+        if caught or (slip is None and n == 6):
+            break
+    assert caught == (slip is not None), slip
