@@ -60,9 +60,10 @@ def parse_args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["all", "single", "c1", "c3", "multi", "served"], default="all",
-                   help="all: the headline workload plus configs 1, 3, 4 and 5 in one line (default); "
-                        "single: the headline workload only; c1, c3, multi, served: one other workload")
+    p.add_argument("--workload", choices=["all", "single", "c1", "c3", "multi", "served", "hlevel"], default="all",
+                   help="all: the headline workload plus configs 1, 3, 4 and 5 and the multi-level leg in one line (default); "
+                        "single: the headline workload only; c1, c3, multi, served: one other workload; "
+                        "hlevel: the multi-level layout of Sec. 3.3 beside the plain form")
     p.add_argument("--served-requests", type=int, default=8000, help="served: requests in the pool")
     p.add_argument("--served-clients", type=int, default=16, help="served: closed-loop client threads")
     p.add_argument("--served-window", type=float, default=0.8, help="served: seconds of each open-loop arm")
@@ -701,6 +702,82 @@ def W():
     return workloads
 
 
+# ----------------------------------------------------------------- multi-level layout (Sec. 3.3)
+
+def time_calls(torch, s, flush, flush_rd, steps, fn):
+    """Median CUDA-event time (ms) of fn() over steps calls, L2 flushed before each."""
+    times = []
+    for i in range(steps):
+        flush_l2(flush, flush_rd, i)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        fn()
+        e1.record(s)
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in times)
+
+
+def run_hlevel(args, rmq, torch, np, dev, peak):
+    """The multi-level layout of Sec. 3.3 beside the one-level plain form on the
+    n = 1e8, q = 1e7 workloads (uniform ranges over uniform values, and short
+    ranges over tie-heavy values): per call time with L2 flushed, queries/s,
+    the structure's bytes next to the one-level table's, and the fraction of
+    measured HBM of the lower bound 4n + 8E + 12q (A read once, E structure
+    entries written, l, r read and out written; end-part reads not counted).
+    Block sizes: Sec. 3.3's choice for h = 2 and h = 3, and two smaller
+    first levels.  Every answer equals the plain form's, and a sample the
+    naive oracle's."""
+    import oracle
+    n, q = 100_000_000, 10_000_000
+    ks_list = [rmq.rmq_hlevel_paper_ks(n, 2), rmq.rmq_hlevel_paper_ks(n, 3), (128, 1024), (128, 1024, 16384)]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    flush_rd = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    s = torch.cuda.current_stream(dev)
+    steps = max(5, min(args.steps, 10))
+    res = {}
+    for name in ("uniform", "tie_heavy_short"):
+        if name == "uniform":
+            A = W().uniform_array(n, 1005)
+            l, r = W().uniform_queries(n, q, 1006)
+        else:
+            A = W().uniform_array(n, 1007, 0, 1000)
+            l, r = W().log_width_queries(n, q, 1008, 1, 10_000)
+        dA = torch.from_numpy(A).to(dev)
+        dl, dr = torch.from_numpy(l).to(dev), torch.from_numpy(r).to(dev)
+        ref = torch.empty(q, dtype=torch.int32, device=dev)
+        out = torch.empty(q, dtype=torch.int32, device=dev)
+        idx = np.random.default_rng(9).choice(q, size=2000, replace=False)
+        want = oracle.rmq_naive(A, l[idx], r[idx])
+        best, _ = rmq.rmq_autotune(dA, dl, dr, ref, variant=1, k_min=32, k_max=4096)
+        popts = dict(variant=1, k=best["k"], threads_per_query=best["threads_per_query"], k1=best["k1"])
+        ms_p = time_calls(torch, s, flush, flush_rd, steps, lambda: rmq.rmq_batch_ex(dA, dl, dr, ref, **popts))
+        if not np.array_equal(ref.cpu().numpy()[idx], want):
+            raise RuntimeError("multi-level leg, %s: plain answers differ from the oracle" % name)
+        row = {"plain": {"k": best["k"], "k1": best["k1"], "ms": ms_p, "queries_per_s": q / (ms_p * 1e-3),
+                         "one_level_table_bytes": rmq.rmq_table_bytes(n, best["k"]),
+                         "workspace_bytes": rmq.rmq_batch_workspace_bytes(n, q, **popts)}, "hlevel": []}
+        for ks in ks_list:
+            ms = time_calls(torch, s, flush, flush_rd, steps, lambda: rmq.rmq_batch_hlevel(dA, dl, dr, out, ks))
+            if rmq.rmq_stream_status() != rmq.Status.OK or not torch.equal(out, ref):
+                raise RuntimeError("multi-level leg, %s, ks=%s: answers differ from the plain form" % (name, ks))
+            nbytes = rmq.rmq_hlevel_bytes(n, ks)
+            lb = 4 * n + nbytes + 12 * q
+            gbs = lb / (ms * 1e-3) / 1e9
+            row["hlevel"].append({"ks": list(ks), "h": len(ks), "ms": ms, "queries_per_s": q / (ms * 1e-3),
+                                  "structure_bytes": nbytes,
+                                  "structure_vs_one_level_table": nbytes / rmq.rmq_table_bytes(n, best["k"]),
+                                  "lower_bound_bytes": lb, "gbs": gbs, "frac_of_measured": gbs / peak})
+        res[name] = row
+        del dA, dl, dr, ref, out
+        torch.cuda.empty_cache()
+    return {"workload": "n=1e8 int32, q=1e7: uniform values with l,r uniform; and values uniform in [0,1000) with "
+                        "width log-uniform in [1,1e4]",
+            "paper_ks": {"h2": list(ks_list[0]), "h3": list(ks_list[1])}, "cases": res,
+            "l2": "flushed before every timed call",
+            "checks": "every answer equal to the plain form's; 2000 sampled answers equal to the naive oracle's"}
+
+
 # ----------------------------------------------------------------- config 4
 
 def run_config4(args, rmq, torch, np, dev, peak, seed):
@@ -1028,6 +1105,7 @@ def run_ours(args, dist):
                 line["config3"] = guarded("config3", run_config3, args, rmq, torch, np, dev, peak)
                 line["config4"] = guarded("config4", run_config4, args, rmq, torch, np, dev, peak, args.seed + 2)
                 line["config5"] = guarded("config5", run_config5, args, rmq, torch, np, dev, args.seed + 3)
+                line["hlevel"] = guarded("hlevel", run_hlevel, args, rmq, torch, np, dev, peak)
             else:
                 line["other_configs"] = "configs 1, 3, 4 and 5 run at N = 1 only"
         if dist.rank == 0:
@@ -1036,7 +1114,8 @@ def run_ours(args, dist):
     fn = {"c1": lambda: run_config1(args, rmq, torch, np, dev),
           "c3": lambda: run_config3(args, rmq, torch, np, dev, peak),
           "multi": lambda: run_config4(args, rmq, torch, np, dev, peak, args.seed + 2),
-          "served": lambda: run_config5(args, rmq, torch, np, dev, args.seed + 3)}[args.workload]
+          "served": lambda: run_config5(args, rmq, torch, np, dev, args.seed + 3),
+          "hlevel": lambda: run_hlevel(args, rmq, torch, np, dev, peak)}[args.workload]
     res = fn()
     if dist.rank == 0:
         print(json.dumps({"workload_only": args.workload, **res}), flush=True)

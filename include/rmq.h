@@ -360,6 +360,31 @@ rmq_status rmq_batch_lary(const int32_t *A, int64_t n, const int32_t *l, const i
  * arguments (those rmq_batch_ex rejects). */
 int64_t rmq_batch_workspace_bytes(int64_t n, int64_t q, const rmq_opts *opts);
 
+/* The plain form over the multi-level block-based sparse table of Sec. 3.3.
+ * ks[0 .. h-1] = k_1 < k_2 < ... < k_h, host array of powers of two (so each
+ * divides the next), 32 <= k_1 <= 65536, k_h <= 2^30, 1 <= h <= 8.  The
+ * minima of the blocks of k_i are kept for i < h and a sparse table over the
+ * blocks of k_h; a query reads two table values for the whole blocks of k_h
+ * inside it and walks each end part down the levels (at most k_h / k_{h-1} +
+ * ... + k_2 / k_1 + k_1 reads per end).  h == 1 is the one-level table of
+ * Sec. 3.2 with k = k_1.  Same answers, error behaviour and ownership as
+ * rmq_batch_ex; the structure (rmq_hlevel_bytes) comes from the
+ * stream-ordered pool and is freed when the call's work is done.
+ * RMQ_ERR_INVALID_ARG for bad block sizes. */
+rmq_status rmq_batch_hlevel(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r,
+                            int64_t q, int32_t *out, const int32_t *ks, int32_t h, void *stream);
+
+/* Bytes of the structure rmq_batch_hlevel builds: 8 * (ceil(n/k_1) + ... +
+ * ceil(n/k_{h-1}) + nb (floor(log2 nb) + 1)) with nb = ceil(n / k_h), the
+ * space of Sec. 3.3.  Host only; -1 on bad arguments. */
+int64_t rmq_hlevel_bytes(int64_t n, const int32_t *ks, int32_t h);
+
+/* Sec. 3.3's choice of block sizes for n and h (2 <= h <= 8): k_i =
+ * sqrt(n) * log2(n)^((i-1)/(h-1) - 1/(h+1)), each rounded to the nearest
+ * power of two, k_1 kept in [32, 65536] and every k_i made at least twice
+ * k_{i-1}.  Writes h values to ks_out (host).  Host only. */
+rmq_status rmq_hlevel_paper_ks(int64_t n, int32_t h, int32_t *ks_out);
+
 /* The tuner's choice of options for (n, q); host only.  When rmq_autotune
  * has remembered choices for several width classes of this shape, this
  * returns the one of the lowest width class (rmq_tune_batch chooses by a

@@ -601,6 +601,53 @@ rmq_status rmq_batch_lary(const int32_t *A, int64_t n, const int32_t *l, const i
     return cuda_status(run_lary(A, n, logk, logell, l, r, q, out, static_cast<uint64_t *>(ws.p), s));
 }
 
+// Block sizes of the multi-level layout: logk[1 .. h] from ks[0 .. h-1];
+// false when they break the rules of rmq_batch_hlevel.
+static bool hlevel_logks(const int32_t *ks, int32_t h, int *logk) {
+    if (!ks || h < 1 || h > kHLevelMax) return false;
+    for (int i = 0; i < h; ++i) {
+        const int32_t k = ks[i];
+        if (k < 1 || (k & (k - 1))) return false;
+        logk[i + 1] = ilog2_host((uint64_t)k);
+        if (i == 0 ? (logk[1] < MIN_LOGK || logk[1] > MAX_LOGK) : (logk[i + 1] <= logk[i] || logk[i + 1] > kHLevelMaxLogK))
+            return false;
+    }
+    return true;
+}
+
+int64_t rmq_hlevel_bytes(int64_t n, const int32_t *ks, int32_t h) {
+    int logk[kHLevelMax + 1];
+    if (n <= 0 || n > kMaxN || !hlevel_logks(ks, h, logk)) return -1;
+    return hlevel_entries(n, logk, h) * 8;
+}
+
+rmq_status rmq_batch_hlevel(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r, int64_t q, int32_t *out,
+                            const int32_t *ks, int32_t h, void *stream) {
+    if (check_batch_args(A, n, l, r, q, out, nullptr) != RMQ_OK) return RMQ_ERR_INVALID_ARG;
+    int logk[kHLevelMax + 1];
+    if (!hlevel_logks(ks, h, logk)) return RMQ_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    Workspace ws;
+    rmq_status st = ws.alloc((size_t)hlevel_entries(n, logk, h) * 8, s);
+    if (st != RMQ_OK) return st;
+    return cuda_status(run_hlevel(A, n, logk, h, l, r, q, out, static_cast<uint64_t *>(ws.p), s));
+}
+
+rmq_status rmq_hlevel_paper_ks(int64_t n, int32_t h, int32_t *ks_out) {
+    if (!ks_out || n < 2 || n > kMaxN || h < 2 || h > kHLevelMax) return RMQ_ERR_INVALID_ARG;
+    const double lg = std::log2((double)n), sq = std::sqrt((double)n);
+    int prev = 0;
+    for (int i = 1; i <= h; ++i) {
+        const double e = (double)(i - 1) / (h - 1) - 1.0 / (h + 1);
+        int t = pow2_log_near(sq * std::pow(lg, e), i == 1 ? MIN_LOGK : 1, i == 1 ? MAX_LOGK : kHLevelMaxLogK);
+        if (i > 1 && t <= prev) t = prev + 1;
+        if (t > kHLevelMaxLogK) return RMQ_ERR_INVALID_ARG;
+        ks_out[i - 1] = 1 << t;
+        prev = t;
+    }
+    return RMQ_OK;
+}
+
 int64_t rmq_batch_workspace_bytes(int64_t n, int64_t q, const rmq_opts *opts) {
     int32_t dummy = 0;
     if (check_batch_args(&dummy, n, &dummy, &dummy, q, &dummy, opts) != RMQ_OK) return -1;

@@ -309,6 +309,15 @@ cudaError_t launch_query_plain(const int32_t *A, int64_t n, int logk, const uint
                                const uint64_t *M1 = nullptr, int cap = kCoarseCap,
                                unsigned long long *counts = nullptr, int logk1 = 7, int max_teams = 4);
 
+// Multi-level layout (hlevel.cu, Sec. 3.3): logk[1 .. h] the logs of the
+// block sizes, strictly increasing, 5 <= logk[1] <= 16, logk[h] <= kHLevelMaxLogK.
+// W holds the minima of levels 1 .. h-1, then the table over blocks of
+// 2^logk[h]; hlevel_entries gives its size in 8-byte keys (-1 on bad h).
+constexpr int kHLevelMax = 8;
+constexpr int kHLevelMaxLogK = 30;
+int64_t hlevel_entries(int64_t n, const int *logk, int h);
+cudaError_t run_hlevel(const int32_t *A, int64_t n, const int *logk, int h, const int32_t *l, const int32_t *r,
+                       int64_t q, int32_t *out, uint64_t *W, cudaStream_t s);
 // The l-ary block sparse table (lary.cu): levels of the table for nb blocks
 // and l = 2^logell; the whole batch with the table T (lary_levels * nb keys).
 int lary_levels(int64_t nb, int logell);

@@ -111,6 +111,9 @@ _SIGS = {
     "rmq_table_bytes": (_i64, [_i64, _i32]),
     "rmq_batch_workspace_bytes": (_i64, [_i64, _i64, ctypes.POINTER(rmq_opts)]),
     "rmq_batch_lary": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, _i32, _i32, _vp]),
+    "rmq_batch_hlevel": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, _vp, _i32, _vp]),
+    "rmq_hlevel_bytes": (_i64, [_i64, _vp, _i32]),
+    "rmq_hlevel_paper_ks": (_i32, [_i64, _i32, _vp]),
     "rmq_tune": (_i32, [_i64, _i64, ctypes.POINTER(rmq_opts)]),
     "rmq_tune_batch": (_i32, [_vp, _vp, _i64, _i64, _vp, ctypes.POINTER(rmq_opts)]),
     "rmq_block_minima": (_i32, [_vp, _i64, _i32, _vp, _vp]),
@@ -419,6 +422,33 @@ def rmq_batch_lary(A, l, r, out, k: int, ell: int, stream=None):
     _check(load().rmq_batch_lary(_dptr(A, _i32t(), "A"), A.numel(), _dptr(l, _i32t(), "l"),
                                  _dptr(r, _i32t(), "r"), l.numel(), _dptr(out, _i32t(), "out"),
                                  int(k), int(ell), _stream(stream, A)))
+
+
+def _ks_array(ks):
+    ks = [int(k) for k in ks]
+    return (ctypes.c_int32 * max(1, len(ks)))(*ks), len(ks)
+
+
+def rmq_batch_hlevel(A, l, r, out, ks, stream=None):
+    """The plain form over the multi-level block sparse table of Sec. 3.3,
+    block sizes ks = (k_1, ..., k_h) (see include/rmq.h)."""
+    arr, h = _ks_array(ks)
+    _check(load().rmq_batch_hlevel(_dptr(A, _i32t(), "A"), A.numel(), _dptr(l, _i32t(), "l"),
+                                   _dptr(r, _i32t(), "r"), l.numel(), _dptr(out, _i32t(), "out"),
+                                   ctypes.cast(arr, ctypes.c_void_p), h, _stream(stream, A)))
+
+
+def rmq_hlevel_bytes(n: int, ks) -> int:
+    """Bytes of the multi-level structure for n and ks (-1 on bad arguments)."""
+    arr, h = _ks_array(ks)
+    return int(load().rmq_hlevel_bytes(int(n), ctypes.cast(arr, ctypes.c_void_p), h))
+
+
+def rmq_hlevel_paper_ks(n: int, h: int) -> tuple:
+    """Sec. 3.3's block sizes for n and h, rounded to powers of two."""
+    arr = (ctypes.c_int32 * max(1, int(h)))()
+    _check(load().rmq_hlevel_paper_ks(int(n), int(h), ctypes.cast(arr, ctypes.c_void_p)))
+    return tuple(int(x) for x in arr[:int(h)])
 
 
 def rmq_batch_workspace_bytes(n: int, q: int, variant=0, k=0, k_con=0, threads_per_query=0, k1=0) -> int:

@@ -1,6 +1,7 @@
 """The C ABI library builds, loads and exports what include/rmq.h declares;
 host-only entry points behave (no GPU needed, no device work is issued)."""
 import ctypes
+import math
 import os
 import re
 
@@ -193,3 +194,51 @@ def test_new_option_fields_are_checked_before_device_work(lib):
     assert rmq.rmq_batch_workspace_bytes(10**6, 100, variant=1, k=1024) == base + 8 * (-(-10**6 // 128))
     assert rmq.rmq_batch_workspace_bytes(10**6, 100, variant=1, k=64) == \
         rmq.rmq_batch_workspace_bytes(10**6, 100, variant=1, k=64, k1=-1)
+
+
+HLEVEL_CASES = [(10**8, (4096, 65536)), (10**8, (128, 1024, 16384)), (10**9, (64, 512, 4096, 65536)),
+                (1000, (32,)), (12345, (32, 64)), (10**6, (32, 1 << 30)), (2**31 - 1, (65536, 1 << 20))]
+
+
+@pytest.mark.parametrize("n,ks", HLEVEL_CASES)
+def test_hlevel_bytes_is_the_space_of_sec33(lib, n, ks):
+    """Eight bytes per entry of the oracle's space count (minima of levels
+    below h, and the sparse table over blocks of k_h); one level is the
+    one-level table of Table 2."""
+    import oracle
+    assert rmq.rmq_hlevel_bytes(n, ks) == 8 * oracle.hlevel_space(n, ks)
+    if len(ks) == 1:
+        assert rmq.rmq_hlevel_bytes(n, ks) == rmq.rmq_table_bytes(n, ks[0])
+
+
+def test_hlevel_rejects_bad_block_sizes_before_device_work(lib):
+    p = ctypes.c_void_p(16)  # never dereferenced: the checks fail first
+    E = rmq.Status.ERR_INVALID_ARG
+    for ks in ((), (16,), (48, 96), (64, 64), (128, 64), (32, 3 << 29),
+               (1 << 17, 1 << 18), tuple(32 << i for i in range(9))):
+        assert rmq.rmq_hlevel_bytes(1000, ks) == -1, ks
+        arr, h = rmq._ks_array(ks)
+        assert lib.rmq_batch_hlevel(p, 1000, p, p, 5, p, ctypes.cast(arr, ctypes.c_void_p), h, None) == E, ks
+    arr, h = rmq._ks_array((64, 256))
+    assert lib.rmq_batch_hlevel(p, 1000, p, p, 5, p, None, 2, None) == E
+    assert lib.rmq_batch_hlevel(None, 1000, p, p, 5, p, ctypes.cast(arr, ctypes.c_void_p), h, None) == E
+    assert rmq.rmq_hlevel_bytes(0, (64,)) == -1
+
+
+@pytest.mark.parametrize("n", [10**6, 10**8, 10**9, 2**31 - 1])
+def test_hlevel_paper_ks_follow_sec33(lib, n):
+    """h = 2: the two sizes Sec. 3.3 gives first, sqrt(n) / log^(1/3) n and
+    sqrt(n) log^(2/3) n, each rounded to the nearest power of two; every h:
+    powers of two, each at least twice the one before, and the structure
+    smaller than the one-level table of k = k_1."""
+    lg, sq = math.log2(n), math.sqrt(n)
+    want = (1 << round(math.log2(sq / lg ** (1 / 3))), 1 << round(math.log2(sq * lg ** (2 / 3))))
+    assert rmq.rmq_hlevel_paper_ks(n, 2) == want
+    for h in range(2, 6):
+        ks = rmq.rmq_hlevel_paper_ks(n, h)
+        assert len(ks) == h and all(k & (k - 1) == 0 for k in ks)
+        assert all(b >= 2 * a for a, b in zip(ks, ks[1:]))
+        assert 32 <= ks[0] <= 65536
+        assert rmq.rmq_hlevel_bytes(n, ks) < rmq.rmq_table_bytes(n, ks[0])
+    with pytest.raises(rmq.RmqError):
+        rmq.rmq_hlevel_paper_ks(n, 1)
