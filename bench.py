@@ -60,10 +60,10 @@ def parse_args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["all", "single", "c1", "c3", "multi", "served", "hlevel"], default="all",
+    p.add_argument("--workload", choices=["all", "single", "c1", "c3", "multi", "served", "hlevel", "qsweep"], default="all",
                    help="all: the headline workload plus configs 1, 3, 4 and 5 and the multi-level leg in one line (default); "
                         "single: the headline workload only; c1, c3, multi, served: one other workload; "
-                        "hlevel: the multi-level layout of Sec. 3.3 beside the plain form")
+                        "hlevel: the multi-level layout of Sec. 3.3 beside the plain form; qsweep: config 2 at q = 1e2 .. 1e6")
     p.add_argument("--served-requests", type=int, default=8000, help="served: requests in the pool")
     p.add_argument("--served-clients", type=int, default=16, help="served: closed-loop client threads")
     p.add_argument("--served-window", type=float, default=0.8, help="served: seconds of each open-loop arm")
@@ -702,6 +702,54 @@ def W():
     return workloads
 
 
+# ----------------------------------------------------------------- config 2, the other batch sizes
+
+def run_qsweep(args, rmq, torch, np, dev, peak):
+    """Config 2 at the batch sizes below the headline's (n = 1e8 uniform,
+    q = 1e2 .. 1e6, the scan-bound cases): both forms autotuned over
+    32..4096 for each q, each call timed with L2 flushed before it, the plain
+    form's HBM fraction on its algorithmic bytes 4n + 8 nb (lc+1) + 8 ceil(n/k1)
+    + 12q + 4S (S counted by the instrumented query kernel)."""
+    import oracle
+    n = 100_000_000
+    A = W().uniform_array(n, 1009)
+    dA = torch.from_numpy(A).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    flush_rd = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    s = torch.cuda.current_stream(dev)
+    steps = max(5, min(args.steps, 10))
+    rows = []
+    for q in (100, 1_000, 10_000, 100_000, 1_000_000):
+        l, r = W().uniform_queries(n, q, 1010 + q)
+        dl, dr = torch.from_numpy(l).to(dev), torch.from_numpy(r).to(dev)
+        out = torch.empty(q, dtype=torch.int32, device=dev)
+        idx = np.random.default_rng(7).choice(q, size=min(q, 48), replace=False)
+        want = oracle.rmq_naive(A, l[idx], r[idx])
+        row = {"q": q}
+        m = distinct_endpoints(n, l, r)
+        for form, v in (("plain", 1), ("contracted", 2)):
+            best, _ = rmq.rmq_autotune(dA, dl, dr, out, variant=v, k_min=32, k_max=4096)
+            opts = dict(variant=v, k=best["k"], k_con=best["k_con"], threads_per_query=best["threads_per_query"])
+            if form == "plain":
+                opts["k1"] = best["k1"]
+            ms = time_calls(torch, s, flush, flush_rd, steps, lambda: rmq.rmq_batch_ex(dA, dl, dr, out, **opts))
+            if rmq.rmq_stream_status() != rmq.Status.OK or not np.array_equal(out.cpu().numpy()[idx], want):
+                raise RuntimeError("config 2 sweep, q=%d, %s form: answers differ from the oracle" % (q, form))
+            entry = {"ms": ms, "k": best["k"] if form == "plain" else best["k_con"]}
+            if form == "plain":
+                cnt = rmq.rmq_batch_counted(dA, dl, dr, out, **opts)
+                _, hbm_b, _, _ = form_bytes(n, q, best["k"], 256, m, {"plain": cnt}, best["k1"])
+                entry.update({"k1": best["k1"], "algorithmic_bytes": hbm_b, "S_cells": cnt["scan_elems"],
+                              "frac_of_measured": hbm_b / (ms * 1e-3) / 1e9 / peak})
+            row[form] = entry
+        row["queries_per_s_both_forms"] = 2 * q / ((row["plain"]["ms"] + row["contracted"]["ms"]) * 1e-3)
+        rows.append(row)
+        del dl, dr, out
+    return {"workload": "config 2 at q = 1e2 .. 1e6: A int32 n=1e8 uniform in [0,2^31), l,r uniform",
+            "rows": rows, "l2": "flushed before every timed call",
+            "oracle": "naive oracle on 48 sampled queries per q and form: identical"}
+
+
 # ----------------------------------------------------------------- multi-level layout (Sec. 3.3)
 
 def time_calls(torch, s, flush, flush_rd, steps, fn):
@@ -1105,6 +1153,7 @@ def run_ours(args, dist):
                 line["config3"] = guarded("config3", run_config3, args, rmq, torch, np, dev, peak)
                 line["config4"] = guarded("config4", run_config4, args, rmq, torch, np, dev, peak, args.seed + 2)
                 line["config5"] = guarded("config5", run_config5, args, rmq, torch, np, dev, args.seed + 3)
+                line["config2_q_sweep"] = guarded("config2_q_sweep", run_qsweep, args, rmq, torch, np, dev, peak)
                 line["hlevel"] = guarded("hlevel", run_hlevel, args, rmq, torch, np, dev, peak)
             else:
                 line["other_configs"] = "configs 1, 3, 4 and 5 run at N = 1 only"
@@ -1115,7 +1164,8 @@ def run_ours(args, dist):
           "c3": lambda: run_config3(args, rmq, torch, np, dev, peak),
           "multi": lambda: run_config4(args, rmq, torch, np, dev, peak, args.seed + 2),
           "served": lambda: run_config5(args, rmq, torch, np, dev, args.seed + 3),
-          "hlevel": lambda: run_hlevel(args, rmq, torch, np, dev, peak)}[args.workload]
+          "hlevel": lambda: run_hlevel(args, rmq, torch, np, dev, peak),
+          "qsweep": lambda: run_qsweep(args, rmq, torch, np, dev, peak)}[args.workload]
     res = fn()
     if dist.rank == 0:
         print(json.dumps({"workload_only": args.workload, **res}), flush=True)

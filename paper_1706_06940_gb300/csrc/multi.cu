@@ -254,6 +254,36 @@ __device__ __forceinline__ uint64_t gresolve_coarse(const uint64_t *C, const Coa
 //   7 <= s <= 10: by lane 0, after a warp reduction over 2^(s-7) rows;
 //   s > 10: the segment spans rounds: acc keeps the lane's minimum, and the
 //     warp reduces it at the segment's last round or when `last` is set.
+// The minimum key over the warp's lanes in 32-bit steps: the smallest value
+// (the keys' high words order as the values), then the smallest position
+// among the lanes that hold it.  Positions are unique, so this is the key
+// of the leftmost minimum whatever cells the lanes hold (KEY_MAX lanes take
+// part harmlessly: their position is the largest).
+__device__ __forceinline__ uint64_t warp_min_key(uint64_t k) {
+    const uint32_t hv = key_hi(k);
+    const uint32_t mv = __reduce_min_sync(0xffffffffu, hv);
+    const uint32_t mp = __reduce_min_sync(0xffffffffu, hv == mv ? key_pos(k) : 0xffffffffu);
+    return ((uint64_t)mv << 32) | mp;
+}
+
+// The same within aligned groups of G consecutive lanes (G <= 16), by
+// shuffles of the 32-bit value, then of the candidates' positions.
+__device__ __forceinline__ uint64_t group_min_key(uint64_t k, int G) {
+    const uint32_t hv = key_hi(k);
+    uint32_t mv = hv;
+    for (int off = G >> 1; off > 0; off >>= 1) mv = min(mv, __shfl_xor_sync(0xffffffffu, mv, off));
+    uint32_t mp = hv == mv ? key_pos(k) : 0xffffffffu;
+    for (int off = G >> 1; off > 0; off >>= 1) mp = min(mp, __shfl_xor_sync(0xffffffffu, mp, off));
+    return ((uint64_t)mv << 32) | mp;
+}
+
+// Key of the leftmost minimum of 4 consecutive cells starting at position e.
+__device__ __forceinline__ uint64_t min4_key(int4 x, uint32_t e) {
+    const int32_t m = min(min(x.x, x.y), min(x.z, x.w));
+    const uint32_t off = x.x == m ? 0u : (x.y == m ? 1u : (x.z == m ? 2u : 3u));
+    return make_key(m, e + off);
+}
+
 template <class Emit>
 __device__ __forceinline__ void seg_round(const uint64_t (&key4)[8], int64_t r0, int64_t n, int s, bool last,
                                           uint64_t &acc, Emit emit) {
@@ -262,8 +292,7 @@ __device__ __forceinline__ void seg_round(const uint64_t (&key4)[8], int64_t r0,
         const int G = 1 << (s - 2);
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            uint64_t v = key4[u];
-            for (int off = G >> 1; off > 0; off >>= 1) v = kmin(v, __shfl_xor_sync(0xffffffffu, v, off));
+            const uint64_t v = group_min_key(key4[u], G);
             const int64_t c = r0 + 128 * u + 4 * lane;
             if ((lane & (G - 1)) == 0 && c < n) emit(c >> s, v);
         }
@@ -273,7 +302,7 @@ __device__ __forceinline__ void seg_round(const uint64_t (&key4)[8], int64_t r0,
         for (int u = 0; u < 8; ++u) {
             acc = kmin(acc, key4[u]);
             if (((u + 1) & (RB - 1)) == 0) {
-                const uint64_t w = warp_min(acc);
+                const uint64_t w = warp_min_key(acc);
                 acc = KEY_MAX;
                 const int64_t c = r0 + 128 * (u + 1 - RB);
                 if (lane == 0 && c < n) emit(c >> s, w);
@@ -283,7 +312,7 @@ __device__ __forceinline__ void seg_round(const uint64_t (&key4)[8], int64_t r0,
 #pragma unroll
         for (int u = 0; u < 8; ++u) acc = kmin(acc, key4[u]);
         if (last || (((r0 + 1024) >> s) << s) == r0 + 1024) {
-            const uint64_t w = warp_min(acc);
+            const uint64_t w = warp_min_key(acc);
             acc = KEY_MAX;
             if (lane == 0) emit(r0 >> s, w);
         }
@@ -310,11 +339,7 @@ __device__ __forceinline__ void multi_slice(const MultiParams &p, int h, int64_t
             // the next round of this slice is fetched into L2 while this one is reduced
             if (lane == 0 && r0 + 2048 <= c1 && r0 + 2048 <= n) prefetch_l2_bulk(d.A + r0 + 1024, 4096);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const uint32_t e = (uint32_t)(r0 + 128 * u + 4 * lane);
-                key4[u] = kmin(kmin(make_key(x[u].x, e), make_key(x[u].y, e + 1)),
-                               kmin(make_key(x[u].z, e + 2), make_key(x[u].w, e + 3)));
-            }
+            for (int u = 0; u < 8; ++u) key4[u] = min4_key(x[u], (uint32_t)(r0 + 128 * u + 4 * lane));
         } else {
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -334,7 +359,7 @@ __device__ __forceinline__ void multi_slice(const MultiParams &p, int h, int64_t
 #pragma unroll
             for (int u = 0; u < 8; ++u) cacc = kmin(cacc, key4[u]);
             if (last) {
-                const uint64_t w = warp_min(cacc);
+                const uint64_t w = warp_min_key(cacc);
                 if (lane == 0) atomicMin(C0 + (c0 >> cs), (unsigned long long)w);
             }
         }
@@ -430,15 +455,47 @@ __global__ void __launch_bounds__(kMT, 4) k_multi(const __grid_constant__ MultiP
                 o[i] = !ok ? -1 : (int32_t)key_pos(m);
                 open |= (ok && !inside ? 1u : 0u) << i;
             }
-#pragma unroll 1
+            // the settled (and invalid) queries' answers; the open ones follow
+#pragma unroll
             for (int i = 0; i < 4; ++i) {
-                if (!__any_sync(0xffffffffu, (open >> i) & 1u)) continue;
-                const int32_t l = lq[i], r = rq[i];
-                const bool is_open = (open >> i) & 1u;
+                const int64_t qi = lane * 4 + i;
+                if (qi < qn && !((open >> i) & 1u)) p.out[qbase + qi] = o[i];
+            }
+            if (bad && p.err) atomicOr(p.err, ERR_QUERY_RANGE);
+            // the open queries of all four slots, one per lane (slot-major
+            // order), resolved in one round and their edge parts drained
+            // together (more rounds only past 32 open queries)
+            const unsigned m0 = __ballot_sync(0xffffffffu, open & 1u), m1 = __ballot_sync(0xffffffffu, open & 2u);
+            const unsigned m2 = __ballot_sync(0xffffffffu, open & 4u), m3 = __ballot_sync(0xffffffffu, open & 8u);
+            const int n0 = __popc(m0), n1 = __popc(m1), n2 = __popc(m2);
+            const int total = n0 + n1 + n2 + __popc(m3);
+            for (int b = 0; b < total; b += 32) {
+                const int k = b + lane;
+                const bool has = k < total;
+                int slot = 0, owner = 0;
+                if (has) {   // the (kk + 1)-th set bit of the slot's mask is the owner lane
+                    int kk = k;
+                    unsigned mm = m0;
+                    if (kk >= n0) {
+                        kk -= n0; mm = m1; slot = 1;
+                        if (kk >= n1) {
+                            kk -= n1; mm = m2; slot = 2;
+                            if (kk >= n2) { kk -= n2; mm = m3; slot = 3; }
+                        }
+                    }
+                    owner = (int)__fns(mm, 0u, kk + 1);
+                }
+                int32_t l = 0, r = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int32_t li = __shfl_sync(0xffffffffu, lq[i], owner);
+                    const int32_t ri = __shfl_sync(0xffffffffu, rq[i], owner);
+                    if (slot == i) { l = li; r = ri; }
+                }
                 Pending pl, pr;
                 bool hl = false, hr = false;
                 uint64_t best = KEY_MAX;
-                if (is_open) {
+                if (has) {
                     int sub;
                     best = gresolve_coarse(C, g, sh, (uint32_t)l, (uint32_t)r, sub);
                     if (sub == SUB_WHOLE) {
@@ -468,14 +525,8 @@ __global__ void __launch_bounds__(kMT, 4) k_multi(const __grid_constant__ MultiP
                     warp_drain_scans<SrcI32, false>(src, d.n, hl, pl, best);
                     warp_drain_scans<SrcI32, false>(src, d.n, hr, pr, best);
                 }
-                if (is_open) o[i] = (int32_t)key_pos(best);
+                if (has) p.out[qbase + owner * 4 + slot] = (int32_t)key_pos(best);
             }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int64_t qi = lane * 4 + i;
-                if (qi < qn) p.out[qbase + qi] = o[i];
-            }
-            if (bad && p.err) atomicOr(p.err, ERR_QUERY_RANGE);
         }
     }
 }

@@ -327,6 +327,47 @@ def test_a4_endpoint_bitmap_clustered_endpoints(R):
     check(R, A, l, r, want=oracle.rmq_sparse_table(A, l, r), variants=(R.Variant.CONTRACTED,), kcons=(0, 32))
 
 
+@pytest.mark.parametrize("case", ["ragged_unaligned_invalid", "full_span", "many_buckets"])
+def test_a4_endpoint_bitmap_large_batch_edges(R, case):
+    """Larger batches at the edges of the marking: a batch that is no
+    multiple of 4096 queries, l and r not 16-byte aligned, invalid queries
+    (they mark position 0), every query the whole array (all endpoints on
+    two positions), and an array of 2^27 + 3 cells.  P, the ranks and m
+    equal the oracle's, and so do the contracted answers."""
+    if case == "ragged_unaligned_invalid":
+        n, q = 65536 * 5 + 3, 65536 + 4097 + 3
+        l, r = W.uniform_queries(n, q, 501)
+        l[:4], r[:4] = [9, -1, 0, 5], [3, 4, n, n - 1]
+    elif case == "full_span":
+        n, q = 1_000_000, 100_000
+        l, r = np.zeros(q, np.int32), np.full(q, n - 1, np.int32)
+    else:
+        n, q = 2**27 + 3, 70_000
+        l, r = W.uniform_queries(n, q, 502)
+    nbp = -(-n // 32) + 1
+    BP = torch.full((2 * nbp,), -1, dtype=torch.int32, device=DEV)
+    m = torch.zeros(1, dtype=torch.int64, device=DEV)
+    bl = torch.zeros(q + 1, dtype=torch.int32, device=DEV)
+    br = torch.zeros(q + 1, dtype=torch.int32, device=DEV)
+    bl[1:], br[1:] = dev(l), dev(r)                     # offset by one cell: not 16-byte aligned
+    R.rmq_endpoint_bitmap(bl[1:], br[1:], n, BP, m)
+    torch.cuda.synchronize()
+    valid = (l >= 0) & (r >= l) & (r < n)
+    assert R.rmq_stream_status() == (R.Status.OK if valid.all() else R.Status.ERR_QUERY_RANGE)
+    wl, wr = np.where(valid, l, 0).astype(np.int32), np.where(valid, r, 0).astype(np.int32)
+    bp = BP.cpu().numpy()
+    wp, wt = oracle.sort_endpoints(wl, wr)
+    P_want, ra_want, rb_want = oracle.rank_endpoints(wp, wt, q)
+    bits = np.unpackbits(np.ascontiguousarray(bp[:nbp]).view(np.uint8), bitorder="little")
+    assert np.array_equal(np.nonzero(bits)[0].astype(np.uint32), P_want)
+    assert int(m.item()) == len(P_want) and bp[-1] == len(P_want) and bp[nbp - 1] == 0
+    assert np.array_equal(bitmap_ranks_host(bp, wl.astype(np.int64)), ra_want)
+    assert np.array_equal(bitmap_ranks_host(bp, wr.astype(np.int64)), rb_want)
+    if n <= 1_000_000:
+        A = W.uniform_array(n, 503, 0, 50)
+        check(R, A, l, r, variants=(R.Variant.CONTRACTED,), kcons=(0, 64), offsets=(0, 1))
+
+
 def test_a4_endpoint_bitmap_invalid_queries_mark_zero(R):
     n, q = 10_000, 300
     l, r = W.uniform_queries(n, q, 99)
