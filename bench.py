@@ -339,7 +339,7 @@ def form_bytes(n, q, k, k_con, m, counts, k1=0):
                         12 * q + 4 * S_p + 8 * cp.get("m1_reads", 0)),
         },
         "contracted": {
-            "mark": ("memset + k_mark_endpoints", "contract.cu", 8 * q + 4 * W),
+            "mark": ("k_mark_endpoints", "contract.cu", 8 * q + 4 * W),   # after a memset of the W words
             "rank": ("k_bits_partial + k_bits_final", "contract.cu", 8 * W),
             "contract": ("k_contract", "contract.cu", 4 * n + 8 * W + 8 * mq),
             "table_AQ": ("k_block_min_warp<SrcU64> + k_st_round", "block_min.cu", 8 * mq + 8 * nbq * (lcq + 1)),
@@ -496,6 +496,13 @@ def run_main(args, dist, rmq, torch, np):
                            "time of the step" % (dom["stage"], n_staged),
             "traffic": profiled_traffic(dom["kernel"], dom_src, {"n": n, "q": q, "k": k, "k_con": k_con}),
             "per_kernel": per_kernel}
+    if dom["kernel"] == "k_mark_endpoints":
+        # its DRAM traffic is its algorithmic bytes, but its time is set by the
+        # L2's rate of reductions (one red.global.or per endpoint)
+        rate = 2 * q / (dom["ms"] * 1e-3)
+        roof["bound_note"] = ("the stage (a memset of the bit words, then one L2 reduction per endpoint) is bound by "
+                              "the L2 reduction rate, not DRAM: %.3g reductions/s against about 1.9e11/s measured "
+                              "for bare reductions" % rate)
     ws_bytes = {f: rmq.rmq_batch_workspace_bytes(n, q, vcode[f], k=k, k_con=k_con, **xo[f]) for f in forms}
     hbm_plain = None
     if "plain" in form_ms:
