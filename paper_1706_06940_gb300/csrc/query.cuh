@@ -455,6 +455,9 @@ __device__ __forceinline__ void resolve_queued(const Src src, int64_t n, int log
     bool hl = false, hr = false;
     uint64_t best = KEY_MAX;
     uint32_t qid = 0;
+    int sub = SUB_NONE;
+    int64_t r_lo = 0, r_hi = -1, r_start = 0, hi_q = -1;
+    uint32_t r_la = 0, r_ra = 0, r_r = 0;
     if (has) {
         qid = q_ids[lane];
         ctr.add(CNT_OPEN, 1);
@@ -462,28 +465,31 @@ __device__ __forceinline__ void resolve_queued(const Src src, int64_t n, int log
         const int32_t l = L[qid], r = R[qid];
         const int64_t lo = CON ? (int64_t)bitmap_rank(BW, BC, (uint32_t)l) : l;
         const int64_t hi = CON ? (int64_t)bitmap_rank(BW, BC, (uint32_t)r) - 1 : r;
-        int sub;
+        hi_q = hi;
         best = resolve_coarse(cs, g, logk, (uint32_t)lo, (uint32_t)hi, (uint32_t)l, (uint32_t)r, sub);
-        if (sub == SUB_WHOLE) {
-            best = resolve_query(T, nb, logk, lo, hi, (uint32_t)l, (uint32_t)r, pl, pr, hl, hr, ctr);
-        } else if (sub != SUB_NONE) {
-            Pending unused;
-            bool unused_flag = false;
-            if (sub & SUB_LEFT) {
-                const int64_t end_l = (((lo >> sh) + 1) << sh) - 1;
-                best = kmin(best, resolve_query(T, nb, logk, lo, end_l, (uint32_t)l, 0xffffffffu, pl, unused, hl,
-                                                unused_flag, ctr));
-            }
-            if (sub & SUB_RIGHT) {
-                // a part inside one block records its scan in the first slot
-                const int64_t start_r = (hi >> sh) << sh;
-                Pending a, b;
-                bool ha = false, hb = false;
-                best = kmin(best, resolve_query(T, nb, logk, start_r, hi, 0u, (uint32_t)r, a, b, ha, hb, ctr));
-                if (ha) { pr = a; hr = true; }
-                if (hb) { pr = b; hr = true; }
-            }
-        }
+        const int64_t end_l = (((lo >> sh) + 1) << sh) - 1, start_r = (hi >> sh) << sh;
+        // the first (sub)range on the block table: the whole range, else the
+        // left end part, else the right end part; a part ending at a whole
+        // coarse block takes that end as inside (la = 0 or ra = ~0), so it
+        // leaves at most one scan, in the first slot (a part inside one
+        // block) or the second
+        r_lo = sub == SUB_WHOLE || (sub & SUB_LEFT) ? lo : start_r;
+        r_hi = sub == SUB_WHOLE ? hi : ((sub & SUB_LEFT) ? end_l : hi);
+        r_la = sub == SUB_WHOLE || (sub & SUB_LEFT) ? (uint32_t)l : 0u;
+        r_ra = sub == SUB_WHOLE ? (uint32_t)r : ((sub & SUB_LEFT) ? 0xffffffffu : (uint32_t)r);
+        r_start = start_r;
+        r_r = (uint32_t)r;
+    }
+    // one call site for the first resolution of every lane that needs one
+    if (has && sub != SUB_NONE)
+        best = kmin(best, resolve_query(T, nb, logk, r_lo, r_hi, r_la, r_ra, pl, pr, hl, hr, ctr));
+    // both end parts: the right one second; the left one used only the first slot
+    if (has && (sub & SUB_LEFT) && (sub & SUB_RIGHT)) {
+        Pending a, b;
+        bool ha = false, hb = false;
+        best = kmin(best, resolve_query(T, nb, logk, r_start, hi_q, 0u, r_r, a, b, ha, hb, ctr));
+        if (ha) { pr = a; hr = true; }
+        if (hb) { pr = b; hr = true; }
     }
     // a query with edge parts goes to the CTA's pool when both fit; its
     // answer is then written after the pool's drain
@@ -512,8 +518,11 @@ __device__ __forceinline__ void resolve_queued(const Src src, int64_t n, int log
             ++w;
         }
     }
-    warp_drain_scans<Src, VEC>(src, n, hl && !defer, pl, best, M1, logk1, max_teams, ctr);
-    warp_drain_scans<Src, VEC>(src, n, hr && !defer, pr, best, M1, logk1, max_teams, ctr);
+    // the two slots' scans, by one copy of the drain
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side)
+        warp_drain_scans<Src, VEC>(src, n, (side == 0 ? hl : hr) && !defer, side == 0 ? pl : pr, best, M1, logk1,
+                                   max_teams, ctr);
     if (has && !defer) out[qid] = (int32_t)key_pos(best);
     __syncwarp();
 }
