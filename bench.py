@@ -387,7 +387,7 @@ def run_main(args, dist, rmq, torch, np):
                                                            k_max=4096)
             k_con = best["k_con"]
             xo["contracted"] = {"threads_per_query": best["threads_per_query"]}
-    nev = {"plain": 4, "contracted": 6}
+    nev = {"plain": 4, "contracted": 7}   # the contracted form's 7th event: after the bitmap clear
     vcode = {"plain": rmq.Variant.PLAIN, "contracted": rmq.Variant.CONTRACTED}
     stream = torch.cuda.current_stream(dev)
 
@@ -450,6 +450,7 @@ def run_main(args, dist, rmq, torch, np):
                    "contracted": ["mark", "rank", "contract", "table_AQ", "queries"]}
     stages = {f: {s: 0.0 for s in stage_names[f]} for f in forms}
     staged_ms = {f: 0.0 for f in forms}
+    clear_ms = 0.0   # contracted: the memset of the bit words at the start of the mark stage
     n_staged = max(3, min(args.steps, 20))
     staged = [staged_step(i) for i in range(n_staged)]
     torch.cuda.synchronize()
@@ -458,7 +459,9 @@ def run_main(args, dist, rmq, torch, np):
             e = evs[f]
             for j, s in enumerate(stage_names[f]):
                 stages[f][s] += e[j].elapsed_time(e[j + 1]) / n_staged
-            staged_ms[f] += e[0].elapsed_time(e[-1]) / n_staged
+            staged_ms[f] += e[0].elapsed_time(e[len(stage_names[f])]) / n_staged
+            if f == "contracted":
+                clear_ms += e[0].elapsed_time(e[6]) / n_staged
     # the work of the open queries (edge scans S, table gathers), counted by
     # the instrumented query kernel on the same batch
     counts = {}
@@ -481,6 +484,15 @@ def run_main(args, dist, rmq, torch, np):
         for s in stage_names[f]:
             kern, src, b = sb[f][s]
             ms = stages[f][s]
+            if f == "contracted" and s == "mark":
+                # the stage is the clear of the W bit words (a memset), then the
+                # marking kernel: each is listed with its own time
+                W = geo["W"]
+                gbs = 4 * W / (clear_ms * 1e-3) / 1e9 if clear_ms > 0 else None
+                per_kernel.append({"form": f, "stage": "mark (clear)", "kernel": "memset of the bit words",
+                                   "source": "contract.cu", "ms": clear_ms, "algorithmic_bytes": 4 * W, "gbs": gbs,
+                                   "frac": gbs / peak if gbs else None})
+                ms = max(ms - clear_ms, 0.0)
             gbs = b / (ms * 1e-3) / 1e9 if ms > 0 else None
             per_kernel.append({"form": f, "stage": s, "kernel": kern, "source": src, "ms": ms,
                                "algorithmic_bytes": b, "gbs": gbs, "frac": gbs / peak if gbs else None})
@@ -492,17 +504,17 @@ def run_main(args, dist, rmq, torch, np):
                           else "fallback 6.8 TB/s"),
             "algorithmic_bytes_per_launch": dom["algorithmic_bytes"],
             "kernel_time": "CUDA events around the %s stage of %d rmq_batch_timed calls on the same batch, same "
-                           "stream, right after the timed region; the dominant kernel is the stage with the largest "
-                           "time of the step" % (dom["stage"], n_staged),
+                           "stream, right after the timed region; the dominant kernel is the one with the largest "
+                           "time of the step (the contracted mark stage is split at its event after the memset of "
+                           "the bit words)" % (dom["stage"], n_staged),
             "traffic": profiled_traffic(dom["kernel"], dom_src, {"n": n, "q": q, "k": k, "k_con": k_con}),
             "per_kernel": per_kernel}
     if dom["kernel"] == "k_mark_endpoints":
         # its DRAM traffic is its algorithmic bytes, but its time is set by the
         # L2's rate of reductions (one red.global.or per endpoint)
         rate = 2 * q / (dom["ms"] * 1e-3)
-        roof["bound_note"] = ("the stage (a memset of the bit words, then one L2 reduction per endpoint) is bound by "
-                              "the L2 reduction rate, not DRAM: %.3g reductions/s against about 1.9e11/s measured "
-                              "for bare reductions" % rate)
+        roof["bound_note"] = ("the kernel (one L2 reduction per endpoint) is bound by the L2 reduction rate, not "
+                              "DRAM: %.3g reductions/s against about 1.9e11/s measured for bare reductions" % rate)
     ws_bytes = {f: rmq.rmq_batch_workspace_bytes(n, q, vcode[f], k=k, k_con=k_con, **xo[f]) for f in forms}
     hbm_plain = None
     if "plain" in form_ms:
@@ -555,6 +567,7 @@ def run_main(args, dist, rmq, torch, np):
                    "parallelism": "replicas" if dist.world > 1 else "single GPU"},
         "forms": {f: {"ms": form_ms[f], "queries_per_s": q / (form_ms[f] * 1e-3),
                       "stages_ms": stages[f], "staged_call_ms": staged_ms[f],
+                      **({"mark_clear_ms": clear_ms} if f == "contracted" else {}),
                       "open_query_work": counts[f]} for f in forms},
         "hbm_plain": hbm_plain,
         "hbm_contracted": hbm_con,

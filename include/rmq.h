@@ -125,7 +125,9 @@ rmq_status rmq_batch_ex(const int32_t *A, int64_t n, const int32_t *l, const int
  * Plain form (Sec. 3.2), 4 events: start | block minima | sparse table |
  *   queries.
  * Contracted form (Sec. 3.1), 6 events: start | step 1 sort | step 1 remap |
- *   step 2 contraction | step 3 block minima and table over A_Q | step 4.
+ *   step 2 contraction | step 3 block minima and table over A_Q | step 4;
+ *   a 7th event, if given, is recorded inside step 1's sort, after the
+ *   clearing of the endpoint bitmap and before the marking of the endpoints.
  * With fewer events only the first n_events boundaries are recorded. */
 rmq_status rmq_batch_timed(const int32_t *A, int64_t n, const int32_t *l, const int32_t *r,
                            int64_t q, int32_t *out, const rmq_opts *opts, void *stream,

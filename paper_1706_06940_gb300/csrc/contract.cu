@@ -879,6 +879,7 @@ cudaError_t endpoint_bitmap(const int32_t *l, const int32_t *r, int64_t q, int64
     // only the bit words need clearing: k_bits_final writes every count
     cudaError_t e = cudaMemsetAsync(BW, 0, (size_t)bitmap_entries(n) * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
+    if (st) st->extra(s, kEventAfterClear);
     const DevInfo di = dev_info();
     const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(cdiv(q, 4), kT), (int64_t)di.sms * 8));
     launch_pdl(k_mark_endpoints, (unsigned)ctas, kT, 0, s, l, r, q, n, BW, err);

@@ -207,7 +207,14 @@ struct Stages {
         if (ev && i < n) cudaEventRecord(ev[i], s);
         ++i;
     }
+    // An event outside the sequence (a boundary inside a stage), at index idx.
+    void extra(cudaStream_t s, int idx) {
+        if (ev && idx < n) cudaEventRecord(ev[idx], s);
+    }
 };
+// Index of the optional event recorded after the clearing of the endpoint
+// bitmap, inside step 1 of the contracted form.
+constexpr int kEventAfterClear = 6;
 
 // Process-wide count of kernel launches issued by this library.
 void note_launches(int count);

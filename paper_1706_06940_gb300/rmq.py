@@ -209,7 +209,8 @@ def rmq_batch_ex(A, l, r, out, variant=0, k=0, k_con=0, stream=None, flags=0, th
 
 def rmq_batch_timed(A, l, r, out, events, variant=0, k=0, k_con=0, stream=None, threads_per_query=0, k1=0):
     """rmq_batch_ex recording torch.cuda.Event objects at the stage boundaries
-    (4 for the plain form, 6 for the contracted form)."""
+    (4 for the plain form, 6 for the contracted form, whose optional 7th is
+    recorded after the bitmap clear inside step 1)."""
     handles = []
     for ev in events:
         if ev.cuda_event == 0:       # torch creates the CUDA event lazily

@@ -127,3 +127,27 @@ def test_batch_above_2_to_the_30_queries(R):
     it = torch.from_numpy(idx).to(DEV)
     ls, rs = l[it].cpu().numpy(), r[it].cpu().numpy()
     assert np.array_equal(out_p[it].cpu().numpy(), oracle.rmq_sparse_table(A_host, ls, rs))
+
+
+@pytest.mark.parametrize("variant,n_events", [(1, 4), (1, 2), (2, 6), (2, 7), (2, 3)])
+def test_stage_events(R, variant, n_events):
+    """rmq_batch_timed records the stage boundaries it is given (the first
+    n_events; the contracted form's 7th lies after the bitmap clear, inside
+    step 1) and answers as the oracle does."""
+    n, q = 300_007, 20_011
+    A = W.uniform_array(n, 610)
+    l, r = W.uniform_queries(n, q, 611)
+    dA = torch.from_numpy(A).to(DEV)
+    dl, dr = torch.from_numpy(l).to(DEV), torch.from_numpy(r).to(DEV)
+    out = torch.full((q,), -7, dtype=torch.int32, device=DEV)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(n_events)]
+    R.rmq_batch_timed(dA, dl, dr, out, evs, variant=variant)
+    torch.cuda.synchronize()
+    assert R.rmq_stream_status() == R.Status.OK
+    assert np.array_equal(out.cpu().numpy(), oracle.rmq_sparse_table(A, l, r))
+    stages = min(n_events, 4 if variant == 1 else 6)
+    spans = [evs[j].elapsed_time(evs[j + 1]) for j in range(stages - 1)]
+    assert all(t >= 0.0 for t in spans)
+    if n_events == 7:
+        clear = evs[0].elapsed_time(evs[6])
+        assert 0.0 <= clear <= evs[0].elapsed_time(evs[1])
