@@ -34,7 +34,7 @@ namespace rmq {
 namespace {
 
 constexpr int kMT = 256;
-constexpr int kLogSlice = 13;             // phase-1 item: 8192 cells (or one block when k is larger)
+constexpr int kLogSlice = 12;             // phase-1 item: 4096 cells (or one block when k is larger)
 constexpr int kMaxLogK = 15;              // block sizes the launch accepts (k <= 32768)
 constexpr int kQueriesPerItem = 1024;     // k_query_handles: queries per CTA item
 constexpr int kWarpQueries = 128;         // k_multi: queries per warp item (4 per lane)
