@@ -855,9 +855,17 @@ def run_config4(args, rmq, torch, np, dev, peak, seed):
     per array on the same stream."""
     import oracle
     ns, qs = W().uneven_batch(args.arrays, seed)
+    # the arrays are views of one device buffer (each starting on a 16-byte
+    # boundary), as a ragged batch is usually held: after the other workloads'
+    # allocations, 512 separate allocations ran the same launch about 20 %
+    # slower (0.93 against 0.78 ms), with the same kernel and inputs
+    starts = np.concatenate([[0], np.cumsum((ns.astype(np.int64) + 3) // 4 * 4)])
+    big = torch.empty(int(starts[-1]), dtype=torch.int32, device=dev)
     dA, ls, rs = [], [], []
     for h, (n, q) in enumerate(zip(ns, qs)):
-        dA.append(torch.from_numpy(W().uniform_array(int(n), seed + 17 * h)).to(dev))
+        a = big[int(starts[h]):int(starts[h]) + int(n)]
+        a.copy_(torch.from_numpy(W().uniform_array(int(n), seed + 17 * h)))
+        dA.append(a)
         l, r = W().uniform_queries(int(n), int(q), seed + 17 * h + 1)
         ls.append(l)
         rs.append(r)
@@ -920,6 +928,7 @@ def run_config4(args, rmq, torch, np, dev, peak, seed):
     return {"workload": "batched uneven: %d int32 arrays, n log-uniform in [1e4,1e7] (sum %d), q log-uniform in "
                         "[10,1e5] (sum %d), uniform values and queries; one persistent launch replayed from a CUDA "
                         "graph" % (len(dA), int(ns.sum()), qtot),
+            "layout": "the arrays are views of one device buffer, each 16-byte aligned",
             "ms": ms_multi, "queries_per_s": qtot / (ms_multi * 1e-3), "kernels_per_replay": kernels_per_replay,
             "per_array_calls": {"ms": ms_seq, "queries_per_s": qtot / (ms_seq * 1e-3),
                                 "speedup_of_one_launch": ms_seq / ms_multi},
