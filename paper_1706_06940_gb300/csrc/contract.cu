@@ -494,6 +494,7 @@ __global__ void __launch_bounds__(kT, 6) k_bits_final(const uint32_t *__restrict
     run += tile_off;
     const int64_t m = m32;
     if (blockIdx.x == 0 && threadIdx.x == 0) *m_dev = m;
+    const uint32_t r0 = run;   // marks before the lane's first word
     // exclusive counts of the lane's words, back in row order
 #pragma unroll
     for (int j = 0; j < kIPT; j += 4) {
@@ -504,7 +505,6 @@ __global__ void __launch_bounds__(kT, 6) k_bits_final(const uint32_t *__restrict
         v.w = run; run += cnt[j + 3];
         *reinterpret_cast<uint4 *>(sx + stage_pos(kIPT * lane + j)) = v;
     }
-    __syncwarp();
     // coarse geometry of the table over A_Q (m - 1 entries)
     const int64_t nbq = m >= 2 ? (m - 2 + (1ll << logk_q)) >> logk_q : 0;
     const bool index = CP != nullptr && nbq > 0;
@@ -514,39 +514,58 @@ __global__ void __launch_bounds__(kT, 6) k_bits_final(const uint32_t *__restrict
     const uint32_t nbc = (uint32_t)g.nbc;
     const uint32_t bmask = (1u << (bs - 5)) - 1u;   // word e starts a bucket iff (e & bmask) == 0
     if (index && blockIdx.x == 0 && threadIdx.x == 0) CB[nbk] = (uint16_t)(nbc - 1);
+    // The lane's kIPT consecutive words e0 .. e0 + kIPT - 1 hold marks r0 .. r0 + s - 1.
+    const uint32_t ue0 = (uint32_t)base + (uint32_t)(kIPT * lane);   // word indices are below 2^27
+    // A_Q entries the contraction combines with atomics: the segment open at
+    // the first word of each contraction tile (32 words); with kIPT = 16 that
+    // word is the first of an even lane
+    if (AQ && (ue0 & 31u) == 0 && (int64_t)ue0 < nbp && (int64_t)(ue0 >> 5) < ntA) {
+        const int64_t sg = (int64_t)r0 - 1;
+        if (sg >= 0 && sg <= m - 2) AQ[sg] = KEY_MAX;
+    }
+    if (index) {
+        // a coarse block of A_Q begins at the (j 2^sh)-th mark: only a lane
+        // whose marks contain a multiple of 2^sh looks at its words (for
+        // r0 = 0, r0 - 1 wraps and mark 0 counts)
+        const bool cp_here = s && ((r0 - 1u) >> sh) != ((r0 + s - 1u) >> sh);
+        // a bucket starts at word e when (e & bmask) == 0 (not the end entry)
+        const uint32_t first_b = (ue0 + bmask) & ~bmask;
+        const bool cb_here = first_b < ue0 + (uint32_t)kIPT && (int64_t)first_b < nbp - 1;
+        if (cp_here || cb_here) {
+            uint32_t ex = r0;
+#pragma unroll
+            for (int j = 0; j < kIPT; ++j) {
+                const uint32_t e = ue0 + (uint32_t)j;
+                const uint32_t word = st[stage_pos(kIPT * lane + j)];
+                const uint32_t c = __popc(word);
+                if (cp_here && c && ((ex + c - 1u) >> sh) != ((ex - 1u) >> sh)) {
+                    // at most one multiple of 2^sh among ex .. ex + c - 1 (2^sh >= 32)
+                    const uint32_t jb = (ex + (1u << sh) - 1u) >> sh;
+                    const uint32_t t = (jb << sh) - ex;
+                    if (jb < nbc) {
+                        uint32_t wd = word;
+                        for (uint32_t d = 0; d < t; ++d) wd &= wd - 1u;   // drop the t lower marks
+                        CP[jb] = e * 32u + (uint32_t)(__ffs(wd) - 1);
+                    }
+                }
+                // bucket start: the last coarse block that begins at or before it
+                if (cb_here && (e & bmask) == 0 && (int64_t)e < nbp - 1) {
+                    const uint32_t upto = ex + (word & 1u);   // marks <= 32e
+                    const uint32_t cb = upto >= 1u ? (upto - 1u) >> sh : 0u;
+                    CB[e >> (bs - 5)] = (uint16_t)(cb < nbc - 1u ? cb : nbc - 1u);
+                }
+                ex += c;
+            }
+        }
+    }
+    __syncwarp();
+    // the counts, stored by rows (coalesced)
     const uint32_t ebase = (uint32_t)base;
-    const bool all_in = base + 32 * kIPT <= nbp - 1;   // no end entry and nothing past it
+    const bool all_in = base + 32 * kIPT <= nbp;
 #pragma unroll
     for (int i = 0; i < kIPT; ++i) {
-        const uint32_t ex = sx[stage_pos(i * 32 + lane)], word = st[stage_pos(i * 32 + lane)];
         const uint32_t e = ebase + (uint32_t)(i * 32 + lane);
-        if (!all_in && (int64_t)e >= nbp) continue;
-        BC[e] = ex;
-        if (lane == 0 && (int64_t)(e >> 5) < ntA) {   // the first word of a contraction tile
-            const int64_t sg = (int64_t)ex - 1;
-            if (sg >= 0 && sg <= m - 2) AQ[sg] = KEY_MAX;
-        }
-        if (index && (all_in || (int64_t)e < nbp - 1)) {
-            // a coarse block of A_Q begins at the (j 2^sh)-th mark: is one of
-            // this word's marks ex .. ex + c - 1 a multiple of 2^sh?  (2^sh >= 32,
-            // so at most one is; for ex = 0, ex - 1 wraps and mark 0 counts)
-            const uint32_t c = __popc(word);
-            if (c && ((ex + c - 1u) >> sh) != ((ex - 1u) >> sh)) {
-                const uint32_t jb = (ex + (1u << sh) - 1u) >> sh;
-                const uint32_t t = (jb << sh) - ex;
-                if (jb < nbc) {
-                    uint32_t wd = word;
-                    for (uint32_t d = 0; d < t; ++d) wd &= wd - 1u;   // drop the t lower marks
-                    CP[jb] = e * 32u + (uint32_t)(__ffs(wd) - 1);
-                }
-            }
-            // bucket start: the last coarse block that begins at or before it
-            if ((e & bmask) == 0) {
-                const uint32_t upto = ex + (word & 1u);   // marks <= 32e
-                const uint32_t cb = upto >= 1u ? (upto - 1u) >> sh : 0u;
-                CB[e >> (bs - 5)] = (uint16_t)(cb < nbc - 1u ? cb : nbc - 1u);
-            }
-        }
+        if (all_in || (int64_t)e < nbp) BC[e] = sx[stage_pos(i * 32 + lane)];
     }
 }
 
