@@ -637,7 +637,8 @@ __device__ __forceinline__ void contract_walk(const int32_t (&vals)[32], uint32_
 template <bool VEC>
 __global__ void __launch_bounds__(kT, 4) k_contract(SrcI32 src, int64_t n, const uint32_t *__restrict__ BW,
                                                  const uint32_t *__restrict__ BC,
-                                                 const int64_t *m_dev, int64_t ntA, uint64_t *__restrict__ H) {
+                                                 const int64_t *m_dev, int64_t t_begin, int64_t ntA,
+                                                 uint64_t *__restrict__ H) {
     pdl_wait();
     extern __shared__ uint64_t csmem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -676,7 +677,7 @@ __global__ void __launch_bounds__(kT, 4) k_contract(SrcI32 src, int64_t n, const
             }
         }
     };
-    for (int64_t t = warp; t < ntA; t += nwarps) {
+    for (int64_t t = t_begin + warp; t < ntA; t += nwarps) {
         const int64_t ts = t * kATile;
         int4 v[8];
         uint2 e;
@@ -753,6 +754,133 @@ __global__ void __launch_bounds__(kT, 4) k_contract(SrcI32 src, int64_t n, const
         }
         if (lane == 0 && s_n >= 0 && s_n <= m - 2) emit_atomic(H, s_n, tail);
     }
+}
+
+// The same contraction for the tiles wholly inside A (16-byte aligned),
+// with the next tile of each warp in flight while the warp walks the
+// current one: a warp's shared memory is a 4 KB tile buffer (swizzled as
+// above) and, apart from it, the slots of at most kSlotsPf segments.  As
+// soon as the lanes hold their cells the buffer is free, and the warp's next
+// tile is requested into it with 16-byte cp.async copies, and its bit words
+// and counts into registers.  6.5 KB per warp keeps 32 warps per SM (an
+// earlier version with two tile buffers had 16).
+constexpr int kSlotsPf = 320;                                            // slots of 8 bytes
+constexpr int kPfWarpBytes = kATile * 4 + kSlotsPf * 8;                  // 6.5 KB per warp
+constexpr int kContractPfSmem = (kT / 32) * kPfWarpBytes;
+
+__global__ void __launch_bounds__(kT, 4) k_contract_pf(SrcI32 src, int64_t nfull, const uint32_t *__restrict__ BW,
+                                                    const uint32_t *__restrict__ BC, const int64_t *m_dev,
+                                                    uint64_t *__restrict__ H) {
+    extern __shared__ __align__(16) uint8_t pfsmem[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int4 *tile = reinterpret_cast<int4 *>(pfsmem + (size_t)w * kPfWarpBytes);
+    uint64_t *slot = reinterpret_cast<uint64_t *>(pfsmem + (size_t)w * kPfWarpBytes + kATile * 4);
+    const uint32_t tile_sh = (uint32_t)__cvta_generic_to_shared(tile);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int4 *A4 = reinterpret_cast<const int4 *>(src.a);
+    // A is read once: its lines go first when L2 needs room, so that A_Q,
+    // written by this kernel and read by the next, stays there longer
+    uint64_t evict_first;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(evict_first));
+    // one commit group per request (empty past the last tile)
+    auto request = [&](int64_t t) {
+        if (t < nfull) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;"
+                             ::"r"(tile_sh + (uint32_t)swz(u * 32 + lane) * 16u),
+                             "l"(A4 + t * (kATile / 4) + u * 32 + lane), "l"(evict_first) : "memory");
+        }
+        cp_async_commit();
+    };
+    // the bit word and count of each lane's 32 cells of tile t
+    auto words_of = [&](int64_t t) {
+        return t < nfull ? make_uint2(__ldg(BW + t * 32 + lane), __ldg(BC + t * 32 + lane)) : make_uint2(0u, 0u);
+    };
+    // A is the caller's: the first tile is requested before the wait for the
+    // kernels that write the bitmap
+    request(warp);
+    pdl_wait();
+    const int32_t m = (int32_t)*m_dev;
+    uint2 e_next = words_of(warp);
+    for (int64_t t = warp; t < nfull; t += nwarps) {
+        const int64_t ts = t * kATile;
+        const uint2 e = e_next;
+        cp_async_wait<0>();
+        __syncwarp();   // every lane's copies of the tile have landed
+        int32_t vals[32];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            const int4 q4 = tile[swz(8 * lane + x)];
+            vals[4 * x] = q4.x; vals[4 * x + 1] = q4.y; vals[4 * x + 2] = q4.z; vals[4 * x + 3] = q4.w;
+        }
+        __syncwarp();   // the tile is read: the buffer takes the next one
+        request(t + nwarps);
+        e_next = words_of(t + nwarps);   // the next tile's words, in flight during this walk
+        const uint32_t word = e.x;
+        const int32_t s_t = (int32_t)__shfl_sync(0xffffffffu, e.y, 0) - 1;      // open before the tile
+        const uint32_t nbits = __popc(word);
+        const int32_t cnt = (int32_t)__reduce_add_sync(0xffffffffu, nbits);     // boundaries in the tile
+        const int32_t s_n = s_t + cnt;                                           // open after the tile
+        const uint32_t cell0 = (uint32_t)(ts + 32 * lane);
+        if (cnt == 0) {
+            if (s_t >= 0 && s_t <= m - 2) {   // no boundary in the tile: one partial minimum of segment s_t
+                int32_t mv = INT_MAX;
+                uint32_t mp = 0;
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const bool lt = vals[c] < mv;
+                    mp = lt ? (uint32_t)c : mp;
+                    mv = lt ? vals[c] : mv;
+                }
+                const uint64_t best = warp_min(make_key(mv, cell0 + mp));
+                if (lane == 0) emit_atomic(H, s_t, best);
+            }
+            continue;
+        }
+        const uint32_t pre = e.y - (uint32_t)(s_t + 1);   // slot of this lane's first boundary
+        int32_t cv;
+        uint32_t cp;
+        uint64_t first = KEY_MAX;
+        const bool direct = cnt > kSlotsPf;   // warp-uniform
+        if (!direct) contract_walk<false>(vals, word, cell0, pre, slot, H, s_t, m, cv, cp, first);
+        else contract_walk<true>(vals, word, cell0, pre, slot, H, s_t, m, cv, cp, first);
+        bool f = nbits != 0;
+        uint64_t val = make_key(cv, cell0 + cp);
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const bool of = __shfl_up_sync(0xffffffffu, f, d);
+            const uint64_t ov = __shfl_up_sync(0xffffffffu, val, d);
+            if (lane >= d) {
+                if (!f) val = kmin(val, ov);
+                f = f || of;
+            }
+        }
+        uint64_t carry_in = __shfl_up_sync(0xffffffffu, val, 1);
+        if (lane == 0) carry_in = KEY_MAX;
+        const uint64_t tail = __shfl_sync(0xffffffffu, val, 31);
+        if (!direct) {
+            if (nbits) slot[pre] = kmin(slot[pre], carry_in);
+            __syncwarp();
+            for (int32_t b = lane; b < cnt; b += 32) {
+                const int32_t sg = s_t + b;
+                if (sg < 0 || sg > m - 2) continue;
+                if (b == 0) emit_atomic(H, sg, slot[0]);
+                else H[sg] = slot[b];
+            }
+            __syncwarp();   // the slots are read before the next walk writes them
+        } else if (nbits) {
+            const int32_t sg = s_t + (int32_t)pre;
+            const uint64_t v0 = kmin(first, carry_in);
+            if (sg >= 0 && sg <= m - 2) {
+                if (pre == 0) emit_atomic(H, sg, v0);
+                else H[sg] = v0;
+            }
+        }
+        if (lane == 0 && s_n >= 0 && s_n <= m - 2) emit_atomic(H, s_n, tail);
+    }
+    cp_async_wait<0>();   // nothing is left in flight (the last request was empty)
 }
 
 int key_bits(int64_t n) { return n > 1 ? ilog2_host((uint64_t)(n - 1)) + 1 : 0; }
@@ -877,11 +1005,35 @@ cudaError_t contract_bitmap(const int32_t *A, int64_t n, const uint32_t *BW, con
         if (di.device >= 0 && di.device < kMaxDev) occ[di.device] = std::max(1, o);
     });
     if (di.device >= 0 && di.device < kMaxDev) per_sm = occ[di.device];
-    const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(ntA, kT / 32), (int64_t)di.sms * per_sm));
+    // the tiles wholly inside a 16-byte aligned A go to the prefetching
+    // kernel; the last, partial tile (and every tile of an unaligned A) to
+    // the register-staged one
+    const int64_t nfull = n / kATile;
+    int64_t t_begin = 0;
+    if (nfull > 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0) {
+        static std::once_flag pf_once[kMaxDev];
+        static int pf_occ[kMaxDev];
+        once_per_device(pf_once, di.device, [&] {
+            cudaFuncSetAttribute(k_contract_pf, cudaFuncAttributeMaxDynamicSharedMemorySize, kContractPfSmem);
+            int o = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_contract_pf, kT, kContractPfSmem);
+            if (di.device >= 0 && di.device < kMaxDev) pf_occ[di.device] = std::max(1, o);
+        });
+        const int per = (di.device >= 0 && di.device < kMaxDev) ? pf_occ[di.device] : 1;
+        const int64_t pctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(nfull, kT / 32), (int64_t)di.sms * per));
+        launch_pdl(k_contract_pf, (unsigned)pctas, kT, kContractPfSmem, s, src, nfull, BW, BC, m_dev, AQ);
+        note_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        t_begin = nfull;
+        if (t_begin >= ntA) return cudaSuccess;
+    }
+    const int64_t ctas =
+        std::max<int64_t>(1, std::min<int64_t>(cdiv(ntA - t_begin, kT / 32), (int64_t)di.sms * per_sm));
     if ((reinterpret_cast<uintptr_t>(A) & 15) == 0)
-        launch_pdl(k_contract<true>, (unsigned)ctas, kT, kContractSmem, s, src, n, BW, BC, m_dev, ntA, AQ);
+        launch_pdl(k_contract<true>, (unsigned)ctas, kT, kContractSmem, s, src, n, BW, BC, m_dev, t_begin, ntA, AQ);
     else
-        launch_pdl(k_contract<false>, (unsigned)ctas, kT, kContractSmem, s, src, n, BW, BC, m_dev, ntA, AQ);
+        launch_pdl(k_contract<false>, (unsigned)ctas, kT, kContractSmem, s, src, n, BW, BC, m_dev, t_begin, ntA, AQ);
     note_launches(1);
     return cudaGetLastError();
 }
