@@ -341,7 +341,7 @@ def form_bytes(n, q, k, k_con, m, counts, k1=0):
         "contracted": {
             "mark": ("k_mark_endpoints", "contract.cu", 8 * q + 4 * W),   # after a memset of the W words
             "rank": ("k_bits_partial + k_bits_final", "contract.cu", 8 * W),
-            "contract": ("k_contract", "contract.cu", 4 * n + 8 * W + 8 * mq),
+            "contract": ("k_contract_pf", "contract.cu", 4 * n + 8 * W + 8 * mq),   # + k_contract for a partial last tile
             "table_AQ": ("k_block_min_warp<SrcU64> + k_st_round", "block_min.cu", 8 * mq + 8 * nbq * (lcq + 1)),
             "queries": ("k_query_two<SrcU64, CON>", "query.cuh",
                         12 * q + 8 * S_c + 4 * cc.get("rank_reads", 0)),

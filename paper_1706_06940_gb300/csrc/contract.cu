@@ -756,9 +756,8 @@ __global__ void __launch_bounds__(kT, 4) k_contract(SrcI32 src, int64_t n, const
     }
 }
 
-// The same contraction for the tiles wholly inside A (16-byte aligned),
-// with the next tile of each warp in flight while the warp walks the
-// current one: a warp's shared memory is a 4 KB tile buffer (swizzled as
+// The same contraction for a 16-byte aligned A, with the next tile of each
+// warp in flight while the warp walks the current one: a warp's shared memory is a 4 KB tile buffer (swizzled as
 // above) and, apart from it, the slots of at most kSlotsPf segments.  As
 // soon as the lanes hold their cells the buffer is free, and the warp's next
 // tile is requested into it with 16-byte cp.async copies, and its bit words
@@ -768,7 +767,8 @@ constexpr int kSlotsPf = 320;                                            // slot
 constexpr int kPfWarpBytes = kATile * 4 + kSlotsPf * 8;                  // 6.5 KB per warp
 constexpr int kContractPfSmem = (kT / 32) * kPfWarpBytes;
 
-__global__ void __launch_bounds__(kT, 4) k_contract_pf(SrcI32 src, int64_t nfull, const uint32_t *__restrict__ BW,
+__global__ void __launch_bounds__(kT, 4) k_contract_pf(SrcI32 src, int64_t n, int64_t ntA,
+                                                    const uint32_t *__restrict__ BW,
                                                     const uint32_t *__restrict__ BC, const int64_t *m_dev,
                                                     uint64_t *__restrict__ H) {
     extern __shared__ __align__(16) uint8_t pfsmem[];
@@ -783,7 +783,12 @@ __global__ void __launch_bounds__(kT, 4) k_contract_pf(SrcI32 src, int64_t nfull
     // written by this kernel and read by the next, stays there longer
     uint64_t evict_first;
     asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(evict_first));
-    // one commit group per request (empty past the last tile)
+    // one commit group per request (empty past the last tile).  In the last,
+    // partial tile a vector copies only its cells below n and the rest of it
+    // is zero-filled: such cells follow the last endpoint, so they only ever
+    // fall in the open segment after it, which is no entry of A_Q.
+    const int64_t nv = (n + 3) >> 2;   // vectors holding at least one cell
+    const int64_t nfull = n / kATile;  // tiles wholly inside [0, n)
     auto request = [&](int64_t t) {
         if (t < nfull) {
 #pragma unroll
@@ -791,12 +796,25 @@ __global__ void __launch_bounds__(kT, 4) k_contract_pf(SrcI32 src, int64_t nfull
                 asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;"
                              ::"r"(tile_sh + (uint32_t)swz(u * 32 + lane) * 16u),
                              "l"(A4 + t * (kATile / 4) + u * 32 + lane), "l"(evict_first) : "memory");
+        } else if (t < ntA) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t vi = t * (kATile / 4) + u * 32 + lane;
+                const int64_t cells = n - 4 * vi;
+                const uint32_t bytes = cells >= 4 ? 16u : (cells > 0 ? (uint32_t)cells * 4u : 0u);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                             ::"r"(tile_sh + (uint32_t)swz(u * 32 + lane) * 16u),
+                             "l"(A4 + (vi < nv ? vi : 0)), "r"(bytes) : "memory");
+            }
         }
         cp_async_commit();
     };
     // the bit word and count of each lane's 32 cells of tile t
+    const int64_t nw = (n + 31) >> 5;   // bitmap words; entry nw is the end entry
     auto words_of = [&](int64_t t) {
-        return t < nfull ? make_uint2(__ldg(BW + t * 32 + lane), __ldg(BC + t * 32 + lane)) : make_uint2(0u, 0u);
+        const int64_t wi = t * 32 + lane;
+        const int64_t ei = wi < nw ? wi : nw;
+        return t < ntA ? make_uint2(__ldg(BW + ei), __ldg(BC + ei)) : make_uint2(0u, 0u);
     };
     // A is the caller's: the first tile is requested before the wait for the
     // kernels that write the bitmap
@@ -804,7 +822,7 @@ __global__ void __launch_bounds__(kT, 4) k_contract_pf(SrcI32 src, int64_t nfull
     pdl_wait();
     const int32_t m = (int32_t)*m_dev;
     uint2 e_next = words_of(warp);
-    for (int64_t t = warp; t < nfull; t += nwarps) {
+    for (int64_t t = warp; t < ntA; t += nwarps) {
         const int64_t ts = t * kATile;
         const uint2 e = e_next;
         cp_async_wait<0>();
@@ -1005,12 +1023,10 @@ cudaError_t contract_bitmap(const int32_t *A, int64_t n, const uint32_t *BW, con
         if (di.device >= 0 && di.device < kMaxDev) occ[di.device] = std::max(1, o);
     });
     if (di.device >= 0 && di.device < kMaxDev) per_sm = occ[di.device];
-    // the tiles wholly inside a 16-byte aligned A go to the prefetching
-    // kernel; the last, partial tile (and every tile of an unaligned A) to
+    // a 16-byte aligned A goes to the prefetching kernel, an unaligned one to
     // the register-staged one
-    const int64_t nfull = n / kATile;
     int64_t t_begin = 0;
-    if (nfull > 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0) {
+    if ((reinterpret_cast<uintptr_t>(A) & 15) == 0) {
         static std::once_flag pf_once[kMaxDev];
         static int pf_occ[kMaxDev];
         once_per_device(pf_once, di.device, [&] {
@@ -1020,13 +1036,10 @@ cudaError_t contract_bitmap(const int32_t *A, int64_t n, const uint32_t *BW, con
             if (di.device >= 0 && di.device < kMaxDev) pf_occ[di.device] = std::max(1, o);
         });
         const int per = (di.device >= 0 && di.device < kMaxDev) ? pf_occ[di.device] : 1;
-        const int64_t pctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(nfull, kT / 32), (int64_t)di.sms * per));
-        launch_pdl(k_contract_pf, (unsigned)pctas, kT, kContractPfSmem, s, src, nfull, BW, BC, m_dev, AQ);
+        const int64_t pctas = std::max<int64_t>(1, std::min<int64_t>(cdiv(ntA, kT / 32), (int64_t)di.sms * per));
+        launch_pdl(k_contract_pf, (unsigned)pctas, kT, kContractPfSmem, s, src, n, ntA, BW, BC, m_dev, AQ);
         note_launches(1);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        t_begin = nfull;
-        if (t_begin >= ntA) return cudaSuccess;
+        return cudaGetLastError();
     }
     const int64_t ctas =
         std::max<int64_t>(1, std::min<int64_t>(cdiv(ntA - t_begin, kT / 32), (int64_t)di.sms * per_sm));
