@@ -341,7 +341,7 @@ def form_bytes(n, q, k, k_con, m, counts, k1=0):
         "contracted": {
             "mark": ("k_mark_endpoints", "contract.cu", 8 * q + 4 * W),   # after a memset of the W words
             "rank": ("k_bits_partial + k_bits_final", "contract.cu", 8 * W),
-            "contract": ("k_contract_pf", "contract.cu", 4 * n + 8 * W + 8 * mq),   # + k_contract for a partial last tile
+            "contract": ("k_contract_pf", "contract.cu", 4 * n + 8 * W + 8 * mq),   # k_contract only where A is not 16-B aligned
             "table_AQ": ("k_block_min_warp<SrcU64> + k_st_round", "block_min.cu", 8 * mq + 8 * nbq * (lcq + 1)),
             "queries": ("k_query_two<SrcU64, CON>", "query.cuh",
                         12 * q + 8 * S_c + 4 * cc.get("rank_reads", 0)),
@@ -856,9 +856,7 @@ def run_config4(args, rmq, torch, np, dev, peak, seed):
     import oracle
     ns, qs = W().uneven_batch(args.arrays, seed)
     # the arrays are views of one device buffer (each starting on a 16-byte
-    # boundary), as a ragged batch is usually held: after the other workloads'
-    # allocations, 512 separate allocations ran the same launch about 20 %
-    # slower (0.93 against 0.78 ms), with the same kernel and inputs
+    # boundary), as a ragged batch is usually held
     starts = np.concatenate([[0], np.cumsum((ns.astype(np.int64) + 3) // 4 * 4)])
     big = torch.empty(int(starts[-1]), dtype=torch.int32, device=dev)
     dA, ls, rs = [], [], []
