@@ -334,7 +334,7 @@ def form_bytes(n, q, k, k_con, m, counts, k1=0):
         "plain": {
             "block_minima": ("k_block_min_warp" if k >= 128 else "k_block_min_group",
                              "block_min.cu", 4 * n + 8 * nb + 8 * m1),
-            "sparse_table": ("k_st_round", "sparse_table.cu", 8 * nb * (lc + 1)),
+            "sparse_table": ("k_st_first", "sparse_table.cu", 8 * nb * (lc + 1)),
             "queries": ("k_query_two<SrcI32>", "query.cuh",
                         12 * q + 4 * S_p + 8 * cp.get("m1_reads", 0)),
         },
@@ -342,7 +342,7 @@ def form_bytes(n, q, k, k_con, m, counts, k1=0):
             "mark": ("k_mark_endpoints", "contract.cu", 8 * q + 4 * W),   # after a memset of the W words
             "rank": ("k_bits_partial + k_bits_final", "contract.cu", 8 * W),
             "contract": ("k_contract_pf", "contract.cu", 4 * n + 8 * W + 8 * mq),   # k_contract only where A is not 16-B aligned
-            "table_AQ": ("k_block_min_warp<SrcU64> + k_st_round", "block_min.cu", 8 * mq + 8 * nbq * (lcq + 1)),
+            "table_AQ": ("k_block_min_warp<SrcU64> + k_st_first", "block_min.cu", 8 * mq + 8 * nbq * (lcq + 1)),
             "queries": ("k_query_two<SrcU64, CON>", "query.cuh",
                         12 * q + 8 * S_c + 4 * cc.get("rank_reads", 0)),
         },

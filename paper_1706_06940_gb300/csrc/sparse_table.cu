@@ -18,8 +18,9 @@ constexpr int kThreads = 256;
 // A CTA owns R residues rho (mod 2^b) and S consecutive strides s, i.e. the
 // entries j = rho0 + rho + (s0 + s) * 2^b; it loads the S + 2^nlev rows it
 // needs once (coalesced along rho for R = 32, along s for R = 1), doubles in
-// ping-pong buffers and writes every level's rows < S.  Round 0 uses R = 1
-// (contiguous tiles); later rounds start at b >= 5, so R = 32 divides 2^b.
+// ping-pong buffers and writes every level's rows < S.  Round 0 (R = 1,
+// contiguous tiles) runs as k_st_first below; later rounds start at b >= 5,
+// so R = 32 divides 2^b.
 // cap > 0: levels up to lc of the two-level layout for that coarse geometry;
 // cap == 0: every level.
 template <int R, int LV>
@@ -63,6 +64,45 @@ __global__ void __launch_bounds__(kThreads) k_st_round(uint64_t *__restrict__ T,
             if (j + span <= nb) Tu[j] = Y[i];
         }
         uint64_t *tmp = X; X = Y; Y = tmp;
+    }
+}
+
+// The first round (levels 1 .. nlev from level 0, contiguous tiles of S
+// outputs): the same doubling as k_st_round with R = 1, b = 0, laid out for a
+// short dependent chain, which is what bounds this kernel (a few hundred
+// bytes per CTA).  The loads of the tile and its halo are issued first: the
+// halo is sized for nlev_max, the host's bound on the level count (from the
+// largest possible block count; the coarse shift grows with it), and the
+// exact count is worked out from the device-side length while they are in
+// flight.  Index arithmetic inside the tile is 32-bit.
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_st_first(uint64_t *__restrict__ T, Len len, int logk, int nlev_max,
+                                                      int cap) {
+    pdl_wait();
+    const int64_t n = len.get();
+    const int64_t nb = (n + (1ll << logk) - 1) >> logk;
+    const int64_t s0 = (int64_t)blockIdx.x * S;
+    if (nb < 2 || s0 >= nb) return;
+    extern __shared__ uint64_t smem[];
+    const int rows = S + (1 << nlev_max);
+    uint64_t *X = smem, *Y = smem + rows;
+    const int64_t left = nb - s0;   // entries of level 0 from the tile's start
+    const unsigned long long *T0 = reinterpret_cast<const unsigned long long *>(T) + s0;
+    for (int i = threadIdx.x; i < rows; i += kThreads) X[i] = i < left ? __ldg(T0 + i) : KEY_MAX;
+    const int top = cap > 0 ? coarse_geom(nb, cap).lc : ilog2_dev((uint64_t)nb);
+    const int nlev = min(nlev_max, top);
+    __syncthreads();
+    uint64_t *Tu = T + s0;
+    for (int u = 1; u <= nlev; ++u) {
+        const int half = 1 << (u - 1);
+        const int cnt = rows - (1 << u) + 1;
+        for (int i = threadIdx.x; i < cnt; i += kThreads) Y[i] = kmin(X[i], X[i + half]);
+        __syncthreads();
+        Tu += nb;
+        const int64_t valid = left - (1ll << u) + 1;   // entries j with j + 2^u <= nb
+        for (int i = threadIdx.x; i < S; i += kThreads)
+            if (i < valid) Tu[i] = Y[i];
+        uint64_t *t = X; X = Y; Y = t;
     }
 }
 
@@ -114,16 +154,18 @@ cudaError_t launch_sparse_table(uint64_t *T, Len len, int logk, int64_t nb_max, 
     const int kcap = two ? cap : 0;
     static std::once_flag once[kMaxDev];
     const DevInfo di = dev_info();
-    const size_t smem0 = 2ull * (kS0 + (1 << kLV0)) * 1 * sizeof(uint64_t);
+    const int nlev0 = std::min(top, kLV0);   // levels of the first round, at most
+    const size_t smem0 = 2ull * (kS0 + (1 << nlev0)) * sizeof(uint64_t);
     const size_t smem1 = 2ull * (kS1 + (1 << kLV1)) * 32 * sizeof(uint64_t);
     once_per_device(once, di.device, [&] {
-        cudaFuncSetAttribute(k_st_round<1, kLV0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem0);
+        cudaFuncSetAttribute(k_st_first<kS0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(2ull * (kS0 + (1 << kLV0)) * sizeof(uint64_t)));
         cudaFuncSetAttribute(k_st_round<32, kLV1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
     });
     {
         const int64_t ctas = cdiv(nb_max, kS0);
         if (top > 0) {
-            launch_pdl(k_st_round<1, kLV0>, (unsigned)ctas, kThreads, smem0, s, T, len, logk, 0, kS0, kcap);
+            launch_pdl(k_st_first<kS0>, (unsigned)ctas, kThreads, smem0, s, T, len, logk, nlev0, kcap);
             note_launches(1);
         }
         cudaError_t e = cudaGetLastError();
