@@ -306,17 +306,19 @@ rmq_status rmq_server_submit(rmq_server s, int32_t id, const int32_t *l_host, co
                              int32_t *out_host, int64_t *ticket_out);
 
 /* Wait until the ticket's answers are in its out buffer; *latency_s = time
- * from submit to answers (seconds, may be NULL).  Each ticket is waited once.
- * Returns RMQ_ERR_QUERY_RANGE when some query of this request had l < 0,
- * r >= n or l > r (checked on the host when the request is batched; those
- * answers are -1, the others are valid), RMQ_ERR_CUDA when its batch
- * failed on the device, RMQ_ERR_INVALID_ARG when the server was destroyed
- * before it ran. */
+ * from submit to answers (seconds, may be NULL).  Each ticket is waited once:
+ * a wait on a ticket that was never issued or has already been collected
+ * returns RMQ_ERR_INVALID_ARG at once.  Returns RMQ_ERR_QUERY_RANGE when some
+ * query of this request had l < 0, r >= n or l > r (checked on the host when
+ * the request is batched; those answers are -1, the others are valid), and
+ * RMQ_ERR_CUDA when its batch failed on the device. */
 rmq_status rmq_server_wait(rmq_server s, int64_t ticket, double *latency_s);
 
 rmq_status rmq_server_stats_get(rmq_server s, rmq_server_stats *out);
 
-/* Stop the threads, finish running batches and free everything. */
+/* Stop the threads, finish running batches and free everything; requests
+ * still queued are not run.  No other thread may be inside an rmq_server_*
+ * call on s (a wait included) while it is destroyed, nor call one after. */
 void rmq_server_destroy(rmq_server s);
 
 /* ----------------------------------------------------------- diagnostics */

@@ -99,6 +99,22 @@ bool stage_and_check(const int32_t *l, const int32_t *r, int64_t q, int64_t n, i
     return ok;
 }
 
+// Whether a ticket is still to complete: queued, or taken into a slot that
+// has not been handed back (a slot's requests are set and cleared under the
+// server lock, in the same critical sections that take it from and return it
+// to free_slots).  The caller holds the lock.
+bool outstanding(const rmq_server_s *S, int64_t t) {
+    for (const Request &rq : S->pending)
+        if (rq.ticket == t) return true;
+    std::vector<char> is_free(S->slots.size(), 0);
+    for (int f : S->free_slots) is_free[f] = 1;
+    for (size_t i = 0; i < S->slots.size(); ++i)
+        if (!is_free[i])
+            for (const Request &rq : S->slots[i].reqs)
+                if (rq.ticket == t) return true;
+    return false;
+}
+
 void scheduler(rmq_server_s *S) {
     cudaSetDevice(S->device);
     for (;;) {
@@ -380,6 +396,9 @@ rmq_status rmq_server_wait(rmq_server S, int64_t ticket, double *latency_s) {
     if (!S || ticket < 0) return RMQ_ERR_INVALID_ARG;
     std::unique_lock<std::mutex> lk(S->mu);
     if (ticket >= S->next_ticket) return RMQ_ERR_INVALID_ARG;
+    // a ticket that is neither done nor outstanding was collected before
+    if (!S->finished.count(ticket) && !S->failed.count(ticket) && !outstanding(S, ticket))
+        return RMQ_ERR_INVALID_ARG;
     S->cv_slot.wait(lk, [&] { return S->finished.count(ticket) || S->failed.count(ticket); });
     auto f = S->failed.find(ticket);
     if (f != S->failed.end()) {

@@ -232,3 +232,26 @@ def test_admit_wait_gets_memory_freed_by_an_eviction(R):
     srv.wait(srv.submit(b, l, r, out))
     assert np.array_equal(out, oracle.rmq_naive(B.cpu().numpy(), l, r))
     srv.close()
+
+
+def test_second_wait_on_a_ticket_is_refused(R):
+    """A ticket is collected once: waiting on it again, or on a ticket never
+    issued, returns RMQ_ERR_INVALID_ARG at once instead of blocking."""
+    n = 200_000
+    A = W.uniform_array(n, 520)
+    srv = R.Server(inflight=2)
+    a = srv.admit(torch.from_numpy(A).to(DEV))
+    l, r = W.uniform_queries(n, 1000, 521)
+    out = np.full(1000, -7, np.int32)
+    t = srv.submit(a, l, r, out)
+    srv.wait(t)
+    assert np.array_equal(out, oracle.rmq_naive(A, l, r))
+    for bad in (t, t + 1000):
+        with pytest.raises(R.RmqError) as ei:
+            srv.wait(bad)
+        assert ei.value.status == R.Status.ERR_INVALID_ARG
+    # the server still serves after the refused waits
+    out2 = np.full(1000, -7, np.int32)
+    srv.wait(srv.submit(a, l, r, out2))
+    assert np.array_equal(out2, out)
+    srv.close()
